@@ -1,0 +1,193 @@
+/*
+ * eri.h -- C ABI of the GB300 engine for batched electron repulsion integrals (ERIs)
+ * with fused fixed-bitwidth compression, after arXiv 2303.13632 ("Computing and
+ * Compressing Electron Repulsion Integrals on FPGAs").
+ *
+ * What is computed (paper section in brackets):
+ *   [ab|cd] = int int g_a(r) g_b(r) g_c(r') g_d(r') / |r - r'| dr dr'          (Sec. II-B, Eq. 1)
+ * for Cartesian Gaussian shells with L <= 3 (s, p, d, f; Sec. II-A), contracted over
+ * primitives, by Rys quadrature (Sec. II-C): Boys function / Rys roots and weights,
+ * setup of B and C, vertical recurrence (Eq. 6), horizontal recurrence (Eq. 7) and
+ * quadrature (Eq. 8); optionally compressed per quartet into n-bit integers with one
+ * scale each (Sec. II-D, Eqs. 9-10; decompression Eq. 11 is the caller's x = q * eps).
+ *
+ * Conventions shared by every entry point
+ *   - Shell functions: N(alpha, L) (x-Ax)^ax (y-Ay)^ay (z-Az)^az exp(-alpha |r-A|^2) with
+ *     N = (2 alpha/pi)^{3/4} (4 alpha)^{L/2} / sqrt((2L-1)!!) for every component (the
+ *     axis-aligned normalisation of Sec. II-A).  A contracted function is
+ *     sum_k coefs[k] N(exps[k], L) g_k; the contraction is not renormalised.
+ *   - Cartesian order within a shell: a_x from L down to 0, then a_y from L-a_x down to 0
+ *     (xx, xy, xz, yy, yz, zz).  Within a quartet the ERIs are row major: a slowest, d
+ *     fastest.  (The FPGA loop order of the paper's Fig. 2 is d, c outer with b, a unrolled;
+ *     that is a hardware choice and does not change the values.)
+ *   - Class id of a quartet of shells with angular momenta (La, Lb, Lc, Ld):
+ *     ((La*4 + Lb)*4 + Lc)*4 + Ld, 0..255 (the 256 generic classes of Sec. III-A).
+ *   - Output order: quartets sorted by class id (ascending), stable within a class (the
+ *     order of the caller's list); eri_plan_quartet_order returns the permutation.
+ *   - Pointers named d_* are device pointers on the plan's device; every other pointer is
+ *     host memory.  The plan owns its device copies; the caller owns every output buffer.
+ *   - Calls that take a stream are asynchronous on that stream (a cudaStream_t passed as
+ *     void*; NULL is the legacy default stream).  One plan is used from one stream at a time.
+ *   - Errors: no exception crosses the ABI.  Invalid arguments return an error before any
+ *     device work and leave outputs untouched.  Device-side problems (non-finite results)
+ *     are latched in the plan and returned by eri_sync.
+ */
+#ifndef GB300_ERI_H
+#define GB300_ERI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct eri_plan_s *eri_plan_t;
+
+typedef enum {
+    ERI_OK = 0,
+    ERI_E_INVALID = 1,     /* bad argument: null pointer, L > 3, alpha <= 0, non-finite input,
+                              shell id out of range, bitwidth outside 2..24, wrong class */
+    ERI_E_UNSUPPORTED = 2, /* valid request this build does not serve */
+    ERI_E_NOMEM = 3,       /* device or host allocation failed */
+    ERI_E_CUDA = 4,        /* a CUDA runtime call failed (launch, copy, sync) */
+    ERI_E_TIMEOUT = 5,     /* a bounded device wait gave up (latched, see eri_sync) */
+    ERI_E_NUMERIC = 6      /* a non-finite ERI was produced (latched, see eri_sync) */
+} eri_status_t;
+
+/* Arithmetic of the recurrence/quadrature stages (Sec. III: the paper uses FP32 there
+ * and FP64 for the Rys roots, footnote of Sec. II-C). */
+enum {
+    ERI_FP64 = 0,  /* everything in FP64 */
+    ERI_MIXED = 1  /* FP64: Boys function, Rys roots and weights, Gaussian-product prefactors;
+                      FP32: setup B/C, VRR, HRR, quadrature; primitive sums Kahan-compensated */
+};
+
+/* How eri_plan_create obtains the quartet list. */
+enum {
+    ERI_EXPLICIT = 0, /* the caller's list of n_quartets x 4 shell ids */
+    ERI_ALL = 1       /* every ordered quartet (i, j, k, l) of the n_shells shells */
+};
+
+/* Flags of eri_plan_opts_t.flags */
+enum {
+    ERI_QUARTETS_ON_DEVICE = 1 /* `quartets` is a device pointer (no host->device copy) */
+};
+
+/* One shell (host memory; eri_plan_create copies it). */
+typedef struct {
+    double center[3];     /* bohr */
+    int32_t L;            /* 0..3 */
+    int32_t nprim;        /* >= 1 */
+    const double *exps;   /* nprim exponents, each > 0 */
+    const double *coefs;  /* nprim contraction coefficients (finite) */
+} eri_shell_t;
+
+typedef struct {
+    int32_t precision;    /* ERI_FP64 or ERI_MIXED */
+    int32_t quartet_mode; /* ERI_EXPLICIT or ERI_ALL */
+    int32_t device;       /* CUDA device ordinal the plan lives on */
+    int32_t flags;        /* ERI_QUARTETS_ON_DEVICE */
+} eri_plan_opts_t;
+
+/* Builds a plan: validates and normalises the shells, classifies and sorts the quartets by
+ * class on the device, and keeps device copies of everything the kernels read.
+ *   shells      n_shells entries (host)
+ *   quartets    n_quartets x 4 int32 shell ids, row major (host unless
+ *               ERI_QUARTETS_ON_DEVICE), or NULL with ERI_ALL
+ *   opts        NULL for defaults (ERI_FP64, ERI_EXPLICIT, device 0, no flags)
+ *   out         receives the plan; untouched on error
+ * Synchronous.  Errors: ERI_E_INVALID (bad shell, id out of range), ERI_E_NOMEM, ERI_E_CUDA. */
+eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const int32_t *quartets,
+                             int64_t n_quartets, const eri_plan_opts_t *opts, eri_plan_t *out);
+
+/* Frees the plan and its device memory.  NULL is ignored. */
+void eri_plan_destroy(eri_plan_t plan);
+
+/* Changes the precision used by later compute calls (ERI_FP64 or ERI_MIXED). */
+eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);
+
+/* Total quartets in the plan. */
+eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);
+
+/* Per-class layout.  cls = ((La*4 + Lb)*4 + Lc)*4 + Ld.  Any output pointer may be NULL.
+ *   n_quartets          quartets of this class in the plan
+ *   n_eri_per_quartet   n_ga n_gb n_gc n_gd (Sec. II-A shell sizes)
+ *   first_quartet       index of the class's first quartet in class-sorted order
+ *   fp64_offset         offset (in doubles) of the class's first ERI in eri_compute's output */
+eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quartets,
+                                 int32_t *n_eri_per_quartet, int64_t *first_quartet,
+                                 int64_t *fp64_offset);
+
+/* perm_out[i] = caller's index of the quartet at class-sorted position i (host array of
+ * eri_plan_num_quartets entries).  For ERI_ALL, index = ((i*n + j)*n + k)*n + l. */
+eri_status_t eri_plan_quartet_order(eri_plan_t plan, int64_t *perm_out);
+
+/* Sizes of the outputs of eri_compute_compressed for a bitwidth (bits = 0: eri_compute's FP64
+ * output).  packed_bytes covers all classes; scales_bytes = 4 * n_quartets. */
+eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_bytes,
+                              size_t *scales_bytes);
+
+/* Byte range of one class inside the packed output of eri_compute_compressed.  Each class
+ * segment starts on a 256-byte boundary and holds a little-endian, least-significant-bit-
+ * first stream of n-bit two's complement fields: ERI v of the class (v = quartet-in-class *
+ * n_eri + index-in-quartet) occupies stream bits [v*bits, (v+1)*bits), stream bit s being
+ * bit s%32 of 32-bit word s/32.  For bits = 8 and 16 this is a plain int8/int16 array.
+ * Bits past the class's last field up to the segment end are zero. */
+eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
+                                     size_t *byte_offset, size_t *bytes);
+
+/* FP64 ERIs of every quartet (Eqs. 5-8 per primitive quartet, summed over primitives) into
+ * d_out (eri_output_bytes(plan, 0, ...) bytes, class-sorted, see fp64_offset).
+ * Asynchronous on `stream`; one kernel launch per non-empty class. */
+eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream);
+
+/* Same as eri_compute for one class only (cls as in eri_plan_class_info); d_out is the
+ * full-size buffer and only the class's range is written. */
+eri_status_t eri_compute_class(eri_plan_t plan, int32_t cls, double *d_out, void *stream);
+
+/* ERIs compressed per quartet (Sec. II-D): b_max = max |x| over the quartet, eps = b_max /
+ * (2^{bits-1} - 1) rounded to FP32 (Eq. 9, stored 32-bit as in Sec. III-C), q = ANINT(x /
+ * eps) with halves away from zero (Eq. 10), computed as x * eps^{-1} like the paper's
+ * kernel.  b_max = 0 gives eps = 0 and q = 0.
+ *   bits       2..24 (eps has a 24-bit significand; wider codes would exceed +-(2^{n-1}-1))
+ *   d_packed   eri_output_bytes(plan, bits, ...).packed bytes, layout of eri_packed_class_offset
+ *   d_scales   one float eps per quartet, class-sorted
+ * Asynchronous on `stream`. */
+eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
+                                    void *stream);
+
+/* eri_compute_compressed for one class only (full-size buffers). */
+eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
+                                          void *d_packed, float *d_scales, void *stream);
+
+/* Waits for the plan's work on `stream` and returns the first latched device error
+ * (ERI_E_NUMERIC, ERI_E_TIMEOUT) or a CUDA error; clears the latch. */
+eri_status_t eri_sync(eri_plan_t plan, void *stream);
+
+/* Human-readable name of a status. */
+const char *eri_status_string(eri_status_t status);
+
+/* ---- component diagnostics (same device code as the ERI kernels) ---- */
+
+/* Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt for m = 0..mmax (mmax <= 16), the
+ * moments of the Rys weight (Sec. II-C).  d_F[i*(mmax+1) + m] for the n values d_T[i] >= 0. */
+eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t n, double *d_F,
+                             void *stream);
+
+/* Rys roots x_mu = t_mu^2 and weights w_mu of order nroots (1..9) for each d_T[i] >= 0
+ * (the input R_Rys of Sec. II-C, Eq. 5): d_x[i*nroots + mu], d_w[i*nroots + mu], roots in
+ * ascending order, sum_mu w_mu x_mu^k = F_k(T) for k < 2*nroots. */
+eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                            double *d_w, void *stream);
+
+/* Class helpers (no device needed). */
+int32_t eri_class_id(int32_t La, int32_t Lb, int32_t Lc, int32_t Ld);
+/* n_eri = n_ga n_gb n_gc n_gd, n_rys = (La+Lb+Lc+Ld)/2 + 1. */
+eri_status_t eri_class_shape(int32_t cls, int32_t *n_eri, int32_t *n_rys);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GB300_ERI_H */

@@ -1,0 +1,183 @@
+"""Python face of the C ABI (include/eri.h): the same entry points, taking numpy arrays,
+torch tensors and shell sets.  Argument marshalling only -- every step of the ERI path
+runs in the CUDA library.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import _lib
+from ._lib import (ERI_ALL, ERI_EXPLICIT, ERI_FP64, ERI_MIXED, ERI_QUARTETS_ON_DEVICE, EriError,  # noqa: F401
+                   check)
+
+PRECISIONS = {"fp64": ERI_FP64, "mixed": ERI_MIXED}
+
+
+def _stream_handle(stream) -> ctypes.c_void_p:
+    if stream is None:
+        return ctypes.c_void_p(0)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)  # torch.cuda.Stream
+
+
+def _dev_ptr(t) -> ctypes.c_void_p:
+    if t is None:
+        return ctypes.c_void_p(0)
+    if isinstance(t, int):
+        return ctypes.c_void_p(t)
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("expected a contiguous CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Plan:
+    """Owns an eri_plan_t; the arrays that back the shell structs are kept alive."""
+
+    def __init__(self, handle: ctypes.c_void_p):
+        self.handle = handle
+
+    def destroy(self):
+        if self.handle:
+            _lib.load().eri_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = "explicit",
+                    device: int = 0) -> Plan:
+    """shells: a ShellSet (workloads.py); quartets: [n, 4] int32 numpy array (host), a
+    contiguous int32 CUDA tensor (device), or None with mode="all"."""
+    lib = _lib.load()
+    n = len(shells.L)
+    arr = (_lib.eri_shell_t * max(n, 1))()
+    exps = np.ascontiguousarray(shells.exps, dtype=np.float64)
+    coefs = np.ascontiguousarray(shells.coefs, dtype=np.float64)
+    base_e = exps.ctypes.data
+    base_c = coefs.ctypes.data
+    for s in range(n):
+        sh = arr[s]
+        for x in range(3):
+            sh.center[x] = float(shells.centers[s][x])
+        sh.L = int(shells.L[s])
+        sh.nprim = int(shells.nprim[s])
+        off = int(shells.pofs[s]) * 8
+        sh.exps = ctypes.cast(base_e + off, _lib.c_double_p)
+        sh.coefs = ctypes.cast(base_c + off, _lib.c_double_p)
+    opts = _lib.eri_plan_opts_t(PRECISIONS[precision], ERI_ALL if mode == "all" else ERI_EXPLICIT,
+                                device, 0)
+    if quartets is None:
+        qptr, nq = ctypes.c_void_p(0), 0
+    elif isinstance(quartets, np.ndarray):
+        q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+        qptr, nq = ctypes.c_void_p(q.ctypes.data), len(q)
+    else:  # torch tensor on the device
+        import torch
+
+        if quartets.dtype != torch.int32 or not quartets.is_cuda or not quartets.is_contiguous():
+            raise ValueError("device quartets must be a contiguous int32 CUDA tensor")
+        qptr, nq = ctypes.c_void_p(quartets.data_ptr()), quartets.numel() // 4
+        opts.flags |= ERI_QUARTETS_ON_DEVICE
+    handle = ctypes.c_void_p()
+    st = lib.eri_plan_create(arr, n, qptr, nq, ctypes.byref(opts), ctypes.byref(handle))
+    check(st, "eri_plan_create")
+    return Plan(handle)
+
+
+def eri_plan_destroy(plan: Plan) -> None:
+    plan.destroy()
+
+
+def eri_plan_set_precision(plan: Plan, precision: str) -> None:
+    check(_lib.load().eri_plan_set_precision(plan.handle, PRECISIONS[precision]), "eri_plan_set_precision")
+
+
+def eri_plan_num_quartets(plan: Plan) -> int:
+    n = ctypes.c_int64()
+    check(_lib.load().eri_plan_num_quartets(plan.handle, ctypes.byref(n)), "eri_plan_num_quartets")
+    return n.value
+
+
+def eri_plan_class_info(plan: Plan, cls: int):
+    """Returns (n_quartets, n_eri_per_quartet, first_quartet, fp64_offset)."""
+    a, b, c, d = ctypes.c_int64(), ctypes.c_int32(), ctypes.c_int64(), ctypes.c_int64()
+    check(_lib.load().eri_plan_class_info(plan.handle, cls, ctypes.byref(a), ctypes.byref(b),
+                                          ctypes.byref(c), ctypes.byref(d)), "eri_plan_class_info")
+    return a.value, b.value, c.value, d.value
+
+
+def eri_plan_quartet_order(plan: Plan) -> np.ndarray:
+    n = eri_plan_num_quartets(plan)
+    out = np.zeros(n, dtype=np.int64)
+    check(_lib.load().eri_plan_quartet_order(plan.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
+          "eri_plan_quartet_order")
+    return out
+
+
+def eri_output_bytes(plan: Plan, bits: int):
+    """Returns (packed_bytes, scales_bytes); bits = 0 gives the FP64 output size."""
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    check(_lib.load().eri_output_bytes(plan.handle, bits, ctypes.byref(a), ctypes.byref(b)), "eri_output_bytes")
+    return a.value, b.value
+
+
+def eri_packed_class_offset(plan: Plan, bits: int, cls: int):
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    check(_lib.load().eri_packed_class_offset(plan.handle, bits, cls, ctypes.byref(a), ctypes.byref(b)),
+          "eri_packed_class_offset")
+    return a.value, b.value
+
+
+def eri_compute(plan: Plan, out, stream=None) -> None:
+    check(_lib.load().eri_compute(plan.handle, _dev_ptr(out), _stream_handle(stream)), "eri_compute")
+
+
+def eri_compute_class(plan: Plan, cls: int, out, stream=None) -> None:
+    check(_lib.load().eri_compute_class(plan.handle, cls, _dev_ptr(out), _stream_handle(stream)),
+          "eri_compute_class")
+
+
+def eri_compute_compressed(plan: Plan, bits: int, packed, scales, stream=None) -> None:
+    check(_lib.load().eri_compute_compressed(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales),
+                                             _stream_handle(stream)), "eri_compute_compressed")
+
+
+def eri_compute_compressed_class(plan: Plan, cls: int, bits: int, packed, scales, stream=None) -> None:
+    check(_lib.load().eri_compute_compressed_class(plan.handle, cls, bits, _dev_ptr(packed),
+                                                   _dev_ptr(scales), _stream_handle(stream)),
+          "eri_compute_compressed_class")
+
+
+def eri_sync(plan: Plan, stream=None) -> None:
+    check(_lib.load().eri_sync(plan.handle, _stream_handle(stream)), "eri_sync")
+
+
+def eri_status_string(status: int) -> str:
+    return _lib.load().eri_status_string(status).decode()
+
+
+def eri_boys_device(mmax: int, T, F, stream=None) -> None:
+    check(_lib.load().eri_boys_device(mmax, _dev_ptr(T), T.numel(), _dev_ptr(F), _stream_handle(stream)),
+          "eri_boys_device")
+
+
+def eri_rys_device(nroots: int, T, x, w, stream=None) -> None:
+    check(_lib.load().eri_rys_device(nroots, _dev_ptr(T), T.numel(), _dev_ptr(x), _dev_ptr(w),
+                                     _stream_handle(stream)), "eri_rys_device")
+
+
+def eri_class_id(La: int, Lb: int, Lc: int, Ld: int) -> int:
+    return int(_lib.load().eri_class_id(La, Lb, Lc, Ld))
+
+
+def eri_class_shape(cls: int):
+    a, b = ctypes.c_int32(), ctypes.c_int32()
+    check(_lib.load().eri_class_shape(cls, ctypes.byref(a), ctypes.byref(b)), "eri_class_shape")
+    return a.value, b.value

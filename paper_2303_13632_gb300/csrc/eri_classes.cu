@@ -1,0 +1,36 @@
+// eri_classes.cu -- instantiates the kernels of the canonical classes whose index is
+// congruent to ERI_TU modulo kNumTU, in the three arithmetic variants.  Compiled once per
+// unit with -DERI_TU=<0..15> so the 55 canonical classes build in parallel.
+#include "eri_internal.h"
+#include "eri_kernels.cuh"
+
+#ifndef ERI_TU
+#error "compile with -DERI_TU=<0..15>"
+#endif
+
+#define ERI_CAT2(a, b) a##b
+#define ERI_CAT(a, b) ERI_CAT2(a, b)
+#define ERI_REGISTER_NAME ERI_CAT(eri_register_tu_, ERI_TU)
+
+namespace eri {
+
+template <int IDX>
+struct Register {
+    static void apply(LaunchFn *table) {
+        if constexpr (IDX < kNumCanonical) {
+            if constexpr (IDX % kNumTU == ERI_TU) {
+                constexpr int cls = canonical_class(IDX);
+                constexpr int La = (cls >> 6) & 3, Lb = (cls >> 4) & 3, Lc = (cls >> 2) & 3,
+                              Ld = cls & 3;
+                table[cls * kNumVariants + 0] = &launch_class<La, Lb, Lc, Ld, double, false>;
+                table[cls * kNumVariants + 1] = &launch_class<La, Lb, Lc, Ld, float, false>;
+                table[cls * kNumVariants + 2] = &launch_class<La, Lb, Lc, Ld, float, true>;
+            }
+            Register<IDX + 1>::apply(table);
+        }
+    }
+};
+
+void ERI_REGISTER_NAME(LaunchFn *table) { Register<0>::apply(table); }
+
+}  // namespace eri

@@ -1,0 +1,180 @@
+// eri_device.cuh -- device-side building blocks shared by the ERI kernels:
+// plan data views, constant tables, the Boys function and the Rys roots/weights.
+//
+// arXiv 2303.13632, Sec. II-C: the Rys quadrature needs the roots t_mu and weights w_mu
+// of order n_Rys for T = rho |P-Q|^2 (the input R_Rys, Eq. 5).  The paper computes them
+// on the CPU in FP64 (footnote of Sec. II-C); here they are evaluated on the GPU in FP64
+// from piecewise Chebyshev series (T below a per-order threshold) or the Gauss-Hermite
+// limit (T above it), both generated offline with 40-digit arithmetic.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace eri {
+
+constexpr int kRysNmax = 9;
+constexpr int kRysDeg = 12;
+constexpr int kBoysMmax = 16;
+constexpr int kBoysTaylor = 10;
+constexpr int kBoysCols = kBoysMmax + kBoysTaylor + 1;
+constexpr double kBoysStep = 0.1;
+constexpr double kBoysTmax = 50.0;
+constexpr int kBoysNgrid = 502;
+constexpr double kPi = 3.14159265358979323846;
+
+// Device addresses of the generated tables (see eri_tables.cu).
+struct Tables {
+    const double *rys_cheb;
+    const double *herm_x2;
+    const double *herm_w;
+    const double *boys_grid;
+    int tasym[kRysNmax + 1];
+    long long offset[kRysNmax + 1];
+    int herm_off[kRysNmax + 2];
+};
+
+// Shell table of a plan on the device (structure of arrays).
+struct ShellsDev {
+    const double *cx, *cy, *cz;  // centres
+    const int *pofs;             // first primitive
+    const int *nprim;            // primitives per shell
+    const double *exps;          // exponents
+    const double *cn;            // contraction coefficient times N(alpha, L)
+};
+
+// One class launch: inputs, outputs and latch.  The kernel computes the canonical class
+// (Sec. II-B, Eq. 3) of the quartets' generic class: canonical shell slot k takes the
+// quartet's shell perm[k], and the canonical component tuple (i0, i1, i2, i3) is stored at
+// generic offset i0*ostride[0] + i1*ostride[1] + i2*ostride[2] + i3*ostride[3].
+struct ClassArgs {
+    int perm[4];
+    int ostride[4];
+    const int4 *quartets;  // class-sorted shell ids, first quartet of the class
+    long long nq;          // quartets of the class
+    double *out_fp64;      // FP64 output of the class (null in compressed mode)
+    uint32_t *packed;      // first word of the class segment (null in FP64 mode)
+    long long seg_words;   // words of the class segment (incl. zero padding)
+    float *scales;         // eps of the class's first quartet
+    int bits;              // 2..24 in compressed mode
+    int *err;              // device error latch (bit 0: non-finite result)
+};
+
+// Boys function F_m(T), m = 0..mmax (mmax <= kBoysMmax).  For T < 50: Taylor series of
+// F_mmax about the nearest grid point T_k (|T - T_k| <= 0.05, ten terms; the derivative is
+// dF_m/dT = -F_{m+1}) and the stable downward recursion
+// F_m = (2T F_{m+1} + exp(-T)) / (2m+1).  For T >= 50: F_0 = sqrt(pi/T)/2 (erf(sqrt T) = 1
+// to double precision there) and the upward recursion F_{m+1} = ((2m+1)F_m - exp(-T))/(2T).
+__device__ __forceinline__ void boys_eval(int mmax, double T, const double *__restrict__ grid,
+                                          double *F) {
+    double eT = exp(-T);
+    if (T < kBoysTmax) {
+        int k = __double2int_rn(T * (1.0 / kBoysStep));
+        double d = k * kBoysStep - T;  // expansion in (-delta)
+        const double *g = grid + k * kBoysCols + mmax;
+        double s = __ldg(g + kBoysTaylor - 1);
+#pragma unroll
+        for (int j = kBoysTaylor - 1; j >= 1; --j) s = fma(s, d / j, __ldg(g + j - 1));
+        F[mmax] = s;
+        for (int m = mmax - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + eT) / (2 * m + 1);
+    } else {
+        F[0] = 0.5 * sqrt(kPi / T);
+        double inv2T = 0.5 / T;
+        for (int m = 0; m < mmax; ++m) F[m + 1] = ((2 * m + 1) * F[m] - eT) * inv2T;
+    }
+}
+
+// F_0(T) and, when WANT1, F_1(T) without exp(): Taylor series of each order about the grid
+// point for T < 50; beyond, F_0 = sqrt(pi/T)/2 and F_1 = F_0/(2T) (the exp(-T) terms are below
+// 1e-20 relative there).
+template <bool WANT1>
+__device__ __forceinline__ void boys_f01(double T, const double *__restrict__ grid, double &F0,
+                                         double &F1) {
+    if (T < kBoysTmax) {
+        int k = __double2int_rn(T * (1.0 / kBoysStep));
+        double d = k * kBoysStep - T;
+        const double *g = grid + k * kBoysCols;
+        double s0 = __ldg(g + kBoysTaylor - 1);
+        double s1 = WANT1 ? __ldg(g + kBoysTaylor) : 0.0;
+#pragma unroll
+        for (int j = kBoysTaylor - 1; j >= 1; --j) {
+            s0 = fma(s0, d / j, __ldg(g + j - 1));
+            if (WANT1) s1 = fma(s1, d / j, __ldg(g + j));
+        }
+        F0 = s0;
+        F1 = s1;
+    } else {
+        F0 = 0.5 * sqrt(kPi / T);
+        F1 = WANT1 ? F0 * (0.5 / T) : 0.0;
+    }
+}
+
+// Chebyshev series sum_j c_j T_j(u) by Clenshaw's recurrence.
+__device__ __forceinline__ double cheb_eval(const double *__restrict__ c, double u) {
+    double b1 = 0.0, b2 = 0.0, u2 = 2.0 * u;
+#pragma unroll
+    for (int j = kRysDeg; j >= 1; --j) {
+        double t = fma(u2, b1, __ldg(c + j) - b2);
+        b2 = b1;
+        b1 = t;
+    }
+    return fma(u, b1, __ldg(c) - b2);
+}
+
+// Root mu (0-based, ascending) and weight of the order-n Rys rule at T.
+__device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double T, double &x,
+                                         double &w) {
+    if (n == 1) {
+        double F0, F1;
+        boys_f01<true>(T, tb.boys_grid, F0, F1);
+        w = F0;
+        x = F1 / F0;
+        return;
+    }
+    if (T < (double)tb.tasym[n]) {
+        int k = (int)T;
+        double u = 2.0 * (T - k) - 1.0;
+        const double *c = tb.rys_cheb + tb.offset[n] + (long long)k * (2 * n * (kRysDeg + 1)) +
+                          (2 * mu) * (kRysDeg + 1);
+        x = cheb_eval(c, u);
+        w = cheb_eval(c + (kRysDeg + 1), u);
+    } else {
+        int h = tb.herm_off[n] + mu;
+        x = __ldg(tb.herm_x2 + h) / T;
+        w = __ldg(tb.herm_w + h) * rsqrt(T);
+    }
+}
+
+__host__ __device__ constexpr int ncart(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Cartesian components (a_x, a_y, a_z) of index idx in a shell of angular momentum L.
+static __constant__ int c_cart[4][10][3] = {
+    {{0, 0, 0}},
+    {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},
+    {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}},
+    {{3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1},
+     {0, 1, 2}, {0, 0, 3}}};
+
+// Cartesian component of index idx in a shell of angular momentum L (order: a_x from L
+// down to 0, then a_y from L - a_x down to 0).
+__host__ __device__ constexpr int cart_x(int L, int idx) {
+    int k = 0;
+    for (int ax = L; ax >= 0; --ax)
+        for (int ay = L - ax; ay >= 0; --ay) {
+            if (k == idx) return ax;
+            ++k;
+        }
+    return -1;
+}
+__host__ __device__ constexpr int cart_y(int L, int idx) {
+    int k = 0;
+    for (int ax = L; ax >= 0; --ax)
+        for (int ay = L - ax; ay >= 0; --ay) {
+            if (k == idx) return ay;
+            ++k;
+        }
+    return -1;
+}
+__host__ __device__ constexpr int cart_z(int L, int idx) { return L - cart_x(L, idx) - cart_y(L, idx); }
+
+}  // namespace eri

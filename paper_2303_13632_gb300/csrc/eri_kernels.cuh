@@ -1,0 +1,641 @@
+// eri_kernels.cuh -- class-templated ERI kernel: Rys quadrature fused with compression.
+//
+// arXiv 2303.13632, Sec. III-B: one kernel per quartet class (La, Lb, Lc, Ld), the
+// angular momenta being compile-time parameters from which n_g and n_Rys follow.
+// Per primitive quartet the kernel runs the stages of Sec. II-C / Fig. 1:
+//   setup      B00, B10, B01 and C00_xi, C00'_xi for each root (the B and C arrays),
+//   VRR        Eq. 6: I(i+1,0,k,0) = i B10 I(i-1,..) + k B00 I(i,..,k-1) + C00 I(i,..,k)
+//                     I(i,0,k+1,0) = k B01 I(..,k-1) + i B00 I(i-1,..,k) + C00' I(i,..,k)
+//   HRR        Eq. 7: I(i,j,k,l) = I(i+1,j-1,k,l) + (A-B)_xi I(i,j-1,k,l), then the same on
+//                     the ket with (C-D)_xi,
+//   quadrature Eq. 8: [ab|cd] = sum_mu prod_xi I(a_xi, b_xi, c_xi, d_xi, mu, xi), with the
+//                     weight and the Gaussian-product prefactor folded into the z origin,
+// sums the primitive quartets (contraction), and then either stores FP64 values or
+// compresses each quartet (Sec. II-D): b_max (max |x|), eps = b_max / (2^{n-1}-1) (Eq. 9),
+// q = ANINT(x eps^{-1}) (Eq. 10), packed into an n-bit little-endian stream.
+//
+// GPU mapping (replaces the FPGA's pipelined loops and private buffer copies, Sec. III-C..E):
+// a CTA owns a tile of Q quartets of one class and runs the stages as data-parallel phases
+// separated by __syncthreads():
+//   A0 geometry + prefactor   one thread per quartet                      (FP64)
+//   A1 roots/weights + B, C   one thread per (quartet, root)              (FP64 -> R)
+//   B  VRR + bra HRR          one thread per (quartet, root, axis)        (R)
+//   C  ket HRR                one thread per (quartet, root, axis, i, j)  (R)
+//   D  quadrature             one thread per (quartet, a, c, b-chunk), the b-chunk x d
+//                             outputs held in registers across primitives (R)
+//   E  b_max, eps, quantise, pack through shared memory, store          (compressed mode)
+// The intermediates I(i,j,k,l,mu,xi) of Table I live in shared memory; several CTAs per SM
+// overlap their phases, which is the GPU analogue of the paper's c_max concurrent quartets.
+// R = double gives the plain FP64 path, R = float the mixed path (FP64 setup/roots, FP32
+// recurrences and quadrature, Kahan-compensated sums over primitives).
+#pragma once
+
+#include "eri_device.cuh"
+
+namespace eri {
+
+template <typename R>
+struct RTraits;
+template <>
+struct RTraits<double> {
+    static __device__ __forceinline__ double round_away(double v) { return round(v); }
+};
+template <>
+struct RTraits<float> {
+    static __device__ __forceinline__ float round_away(float v) { return roundf(v); }
+};
+
+__host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
+__host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
+__host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+
+// Per-quartet geometry kept in shared memory (FP64).
+enum GeoSlot {
+    G_T = 0, G_PREF, G_P, G_Q, G_PAX, G_PAY, G_PAZ, G_QCX, G_QCY, G_QCZ, G_PQX, G_PQY, G_PQZ,
+    G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_N
+};
+// Per (quartet, root) setup values kept in shared memory (type R).
+enum BCSlot { S_B00 = 0, S_B10, S_B01, S_C0X, S_C0Y, S_C0Z, S_C1X, S_C1Y, S_C1Z, S_WZ, S_N };
+
+template <int La_, int Lb_, int Lc_, int Ld_, typename R_>
+struct Cfg {
+    using R = R_;
+    static constexpr int La = La_, Lb = Lb_, Lc = Lc_, Ld = Ld_;
+    static constexpr int NA = ncart(La), NB = ncart(Lb), NC = ncart(Lc), ND = ncart(Ld);
+    static constexpr int NERI = NA * NB * NC * ND;
+    static constexpr int NRYS = (La + Lb + Lc + Ld) / 2 + 1;
+    static constexpr int NAB = La + Lb, NCD = Lc + Ld;
+    static constexpr int JL = (Lb + 1) * (Ld + 1);          // I block for fixed (xi, mu, i, k)
+    static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;   // I per (xi, mu)
+    static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);  // bra-transferred per (xi, mu)
+    static constexpr bool FUSE_BC = HBLK <= 48;             // ket HRR in registers in phase B
+    static constexpr int RWORDS = sizeof(R) / 4;
+    // outputs per thread: bchunk x ND accumulators (+ Kahan compensation in FP32)
+    static constexpr int ACC_REGS = (sizeof(R) == 8) ? 48 : 64;
+    static constexpr int BCH = imax(1, imin(NB, ACC_REGS / (ND * RWORDS)));
+    static constexpr int NCH = cdiv(NB, BCH);
+    static constexpr int ITEMS_D = NA * NC * NCH;
+    // shared memory per quartet (bytes)
+    static constexpr int GEO_BYTES = G_N * 8;
+    static constexpr int BC_BYTES = NRYS * S_N * (int)sizeof(R);
+    static constexpr int H_BYTES = FUSE_BC ? 0 : 3 * NRYS * HBLK * (int)sizeof(R);
+    static constexpr int I_BYTES = 3 * NRYS * IBLK * (int)sizeof(R);
+    static constexpr int STAGE_BYTES = NERI * 3;  // worst case 24-bit codes
+    static constexpr int UNION_BYTES = imax(H_BYTES + I_BYTES, STAGE_BYTES);
+    static constexpr int PERQ = GEO_BYTES + BC_BYTES + UNION_BYTES + 8;
+    static constexpr int SMEM_BUDGET = 96 * 1024;
+    static constexpr int QMAX_T = imax(1, 256 / ITEMS_D);
+    static constexpr int QMAX_S = imax(1, SMEM_BUDGET / PERQ);
+    static constexpr int Q = imin(128, imin(QMAX_T, QMAX_S));
+    static constexpr int THREADS = imax(64, cdiv(Q * ITEMS_D, 32) * 32);
+    // shared memory layout (byte offsets)
+    static constexpr int OFF_GEO = 0;
+    static constexpr int OFF_BC = OFF_GEO + Q * GEO_BYTES;
+    static constexpr int OFF_BMAX = ((OFF_BC + Q * BC_BYTES + 15) / 16) * 16;
+    static constexpr int OFF_U = ((OFF_BMAX + Q * 8 + 15) / 16) * 16;
+    static constexpr int OFF_H = OFF_U;
+    static constexpr int OFF_I = OFF_U + Q * H_BYTES;
+    static constexpr int SMEM = OFF_U + ((Q * UNION_BYTES + 16 + 15) / 16) * 16 + 16;
+};
+
+// ---------------------------------------------------------------------------------------
+// Phase A0: geometry and prefactor of primitive quartet `prim` of quartet q.
+template <class C>
+__device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &qt, int prim,
+                                               double *geo, int &nprim_total) {
+    int na = sh.nprim[qt.x], nb = sh.nprim[qt.y], nc = sh.nprim[qt.z], nd = sh.nprim[qt.w];
+    nprim_total = na * nb * nc * nd;
+    if (prim >= nprim_total) {
+        geo[G_PREF] = 0.0;
+        geo[G_T] = 0.0;
+        for (int s = G_P; s < G_N; ++s) geo[s] = (s == G_P || s == G_Q) ? 1.0 : 0.0;
+        return;
+    }
+    int id = prim % nd, t = prim / nd;
+    int ic = t % nc;
+    t /= nc;
+    int ib = t % nb, ia = t / nb;
+    int pa = sh.pofs[qt.x] + ia, pb = sh.pofs[qt.y] + ib, pc = sh.pofs[qt.z] + ic,
+        pd = sh.pofs[qt.w] + id;
+    double ea = sh.exps[pa], eb = sh.exps[pb], ec = sh.exps[pc], ed = sh.exps[pd];
+    double A[3] = {sh.cx[qt.x], sh.cy[qt.x], sh.cz[qt.x]};
+    double B[3] = {sh.cx[qt.y], sh.cy[qt.y], sh.cz[qt.y]};
+    double Cc[3] = {sh.cx[qt.z], sh.cy[qt.z], sh.cz[qt.z]};
+    double D[3] = {sh.cx[qt.w], sh.cy[qt.w], sh.cz[qt.w]};
+    double p = ea + eb, q = ec + ed;
+    double ip = 1.0 / p, iq = 1.0 / q;
+    double ab2 = 0.0, cd2 = 0.0, pq2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        double AB = A[x] - B[x], CD = Cc[x] - D[x];
+        // P - A = -eb/p (A - B), Q - C = -ed/q (C - D): computed from differences
+        double PA = -eb * ip * AB, QC = -ed * iq * CD;
+        double PQ = (A[x] + PA) - (Cc[x] + QC);
+        geo[G_PAX + x] = PA;
+        geo[G_QCX + x] = QC;
+        geo[G_PQX + x] = PQ;
+        geo[G_ABX + x] = AB;
+        geo[G_CDX + x] = CD;
+        ab2 += AB * AB;
+        cd2 += CD * CD;
+        pq2 += PQ * PQ;
+    }
+    double rho = p * q / (p + q);
+    // K_AB K_CD = exp(-(ab/p |A-B|^2 + cd/q |C-D|^2)) in one FP64 exponential
+    double kabcd = exp(-(ea * eb * ip * ab2 + ec * ed * iq * cd2));
+    // 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD times the four coef * N factors
+    const double two_pi_52 = 34.986836655249725;
+    geo[G_PREF] = two_pi_52 * ip * iq * rsqrt(p + q) * kabcd * sh.cn[pa] * sh.cn[pb] *
+                  sh.cn[pc] * sh.cn[pd];
+    geo[G_T] = rho * pq2;
+    geo[G_P] = p;
+    geo[G_Q] = q;
+}
+
+// Phase A1: root mu of quartet geometry geo -> B and C values (Rys setup stage).  The root and
+// weight are evaluated in FP64; B and C are formed in the recurrence type R (the paper's FPGA
+// kernel does this stage in FP32).  Classes with L = 0 need only F_0 (no root).
+template <class C>
+__device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo, int mu,
+                                            typename C::R *bc) {
+    using R = typename C::R;
+    constexpr int LTOT = C::NAB + C::NCD;
+    double x, w;
+    if constexpr (LTOT == 0) {
+        double F0, F1;
+        boys_f01<false>(geo[G_T], tb.boys_grid, F0, F1);
+        w = F0;
+        x = 0.0;
+    } else {
+        rys_root(tb, C::NRYS, mu, geo[G_T], x, w);
+    }
+    bc[S_WZ] = (R)(geo[G_PREF] * w);
+    if constexpr (LTOT > 0) {
+        R p = (R)geo[G_P], q = (R)geo[G_Q], xr = (R)x;
+        R ipq = (R)1 / (p + q);
+        R fq = q * xr * ipq, fp = p * xr * ipq;
+        bc[S_B00] = (R)0.5 * xr * ipq;
+        bc[S_B10] = ((R)1 - fq) / ((R)2 * p);
+        bc[S_B01] = ((R)1 - fp) / ((R)2 * q);
+#pragma unroll
+        for (int s = 0; s < 3; ++s) {
+            R pq = (R)geo[G_PQX + s];
+            bc[S_C0X + s] = (R)geo[G_PAX + s] - fq * pq;
+            bc[S_C1X + s] = (R)geo[G_QCX + s] + fp * pq;
+        }
+    }
+}
+
+// Bra HRR of one VRR column G(0..NAB) (fixed k) into h[i][j], i <= La, j <= Lb.
+template <class C>
+__device__ __forceinline__ void bra_hrr(const typename C::R (&g)[C::NAB + 1], typename C::R ab,
+                                        typename C::R (&h)[C::La + 1][C::Lb + 1]) {
+    using R = typename C::R;
+    R t[C::Lb + 1][C::NAB + 1];
+#pragma unroll
+    for (int i = 0; i <= C::NAB; ++i) t[0][i] = g[i];
+#pragma unroll
+    for (int j = 1; j <= C::Lb; ++j)
+#pragma unroll
+        for (int i = 0; i + j <= C::NAB; ++i) t[j][i] = fma(ab, t[j - 1][i], t[j - 1][i + 1]);
+#pragma unroll
+    for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+        for (int j = 0; j <= C::Lb; ++j) h[i][j] = t[j][i];
+}
+
+// Ket HRR of one transferred column s(0..NCD) (fixed i, j) into o[k][l], k <= Lc, l <= Ld.
+template <class C>
+__device__ __forceinline__ void ket_hrr(const typename C::R (&s)[C::NCD + 1], typename C::R cd,
+                                        typename C::R (&o)[C::Lc + 1][C::Ld + 1]) {
+    using R = typename C::R;
+    R t[C::Ld + 1][C::NCD + 1];
+#pragma unroll
+    for (int k = 0; k <= C::NCD; ++k) t[0][k] = s[k];
+#pragma unroll
+    for (int l = 1; l <= C::Ld; ++l)
+#pragma unroll
+        for (int k = 0; k + l <= C::NCD; ++k) t[l][k] = fma(cd, t[l - 1][k], t[l - 1][k + 1]);
+#pragma unroll
+    for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+        for (int l = 0; l <= C::Ld; ++l) o[k][l] = t[l][k];
+}
+
+// I layout per quartet: [xi][mu][i][k][j][l] (the (j,l) block is contiguous for phase D).
+template <class C>
+__device__ __forceinline__ int i_index(int xi, int mu, int i, int k, int j, int l) {
+    return ((((xi * C::NRYS + mu) * (C::La + 1) + i) * (C::Lc + 1) + k) * (C::Lb + 1) + j) *
+               (C::Ld + 1) + l;
+}
+
+// Phase B: VRR column by column in k, bra HRR of each column; writes H (or I when fused).
+template <class C>
+__device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double *geo, int mu,
+                                          int xi, typename C::R *Hq, typename C::R *Iq) {
+    using R = typename C::R;
+    const R *b = bc + mu * S_N;
+    R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
+    R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
+    R ab = (R)geo[G_ABX + xi];
+    R prev[C::NAB + 1], cur[C::NAB + 1];
+    // column k = 0: G(i+1, 0) = C00 G(i, 0) + i B10 G(i-1, 0)
+    cur[0] = (xi == 2) ? b[S_WZ] : (R)1;
+#pragma unroll
+    for (int i = 0; i < C::NAB; ++i)
+        cur[i + 1] = c00 * cur[i] + (i > 0 ? (R)i * b10 * cur[i - 1] : (R)0);
+#pragma unroll
+    for (int i = 0; i <= C::NAB; ++i) prev[i] = (R)0;
+    R hk[C::La + 1][C::Lb + 1][C::NCD + 1];
+#pragma unroll
+    for (int k = 0; k <= C::NCD; ++k) {
+        R h[C::La + 1][C::Lb + 1];
+        bra_hrr<C>(cur, ab, h);
+        if constexpr (C::FUSE_BC) {
+#pragma unroll
+            for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+                for (int j = 0; j <= C::Lb; ++j) hk[i][j][k] = h[i][j];
+        } else {
+#pragma unroll
+            for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+                for (int j = 0; j <= C::Lb; ++j)
+                    Hq[(((xi * C::NRYS + mu) * (C::La + 1) + i) * (C::Lb + 1) + j) * (C::NCD + 1) +
+                       k] = h[i][j];
+        }
+        if (k < C::NCD) {
+            // G(i, k+1) = C00' G(i, k) + k B01 G(i, k-1) + i B00 G(i-1, k)
+            R nxt[C::NAB + 1];
+#pragma unroll
+            for (int i = 0; i <= C::NAB; ++i) {
+                R v = c01 * cur[i];
+                if (k > 0) v = fma((R)k * b01, prev[i], v);
+                if (i > 0) v = fma((R)i * b00, cur[i - 1], v);
+                nxt[i] = v;
+            }
+#pragma unroll
+            for (int i = 0; i <= C::NAB; ++i) {
+                prev[i] = cur[i];
+                cur[i] = nxt[i];
+            }
+        }
+    }
+    if constexpr (C::FUSE_BC) {
+        R cd = (R)geo[G_CDX + xi];
+#pragma unroll
+        for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+            for (int j = 0; j <= C::Lb; ++j) {
+                R s[C::NCD + 1];
+#pragma unroll
+                for (int k = 0; k <= C::NCD; ++k) s[k] = hk[i][j][k];
+                R o[C::Lc + 1][C::Ld + 1];
+                ket_hrr<C>(s, cd, o);
+#pragma unroll
+                for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+                    for (int l = 0; l <= C::Ld; ++l) Iq[i_index<C>(xi, mu, i, k, j, l)] = o[k][l];
+            }
+    }
+}
+
+// Phase C: ket HRR for one (mu, xi, i, j).
+template <class C>
+__device__ __forceinline__ void phase_ket(const double *geo, int mu, int xi, int i, int j,
+                                          const typename C::R *Hq, typename C::R *Iq) {
+    using R = typename C::R;
+    R s[C::NCD + 1];
+    const R *src = Hq + (((xi * C::NRYS + mu) * (C::La + 1) + i) * (C::Lb + 1) + j) * (C::NCD + 1);
+#pragma unroll
+    for (int k = 0; k <= C::NCD; ++k) s[k] = src[k];
+    R o[C::Lc + 1][C::Ld + 1];
+    ket_hrr<C>(s, (R)geo[G_CDX + xi], o);
+#pragma unroll
+    for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+        for (int l = 0; l <= C::Ld; ++l) Iq[i_index<C>(xi, mu, i, k, j, l)] = o[k][l];
+}
+
+// Phase D for b-chunk CH: acc[bb][d] (+)= sum_mu X[bx][dx] Y[by][dy] Z[bz][dz], where X, Y, Z
+// are the (j, l) blocks of I at (i, k) = (a_xi, c_xi) for xi = x, y, z.
+template <class C, int CH, bool KAHAN>
+__device__ __forceinline__ void quad_chunk(const typename C::R *Iq, int a, int c,
+                                           typename C::R (&acc)[C::BCH][C::ND],
+                                           typename C::R (&comp)[C::BCH][C::ND], bool first) {
+    using R = typename C::R;
+    constexpr int B0 = CH * C::BCH;
+    constexpr int NBC = imin(C::BCH, C::NB - B0);
+    constexpr int LD1 = C::Ld + 1;
+    const int ax = c_cart[C::La][a][0], ay = c_cart[C::La][a][1], az = c_cart[C::La][a][2];
+    const int cx = c_cart[C::Lc][c][0], cy = c_cart[C::Lc][c][1], cz = c_cart[C::Lc][c][2];
+    R part[KAHAN ? C::BCH : 1][KAHAN ? C::ND : 1];
+    if constexpr (KAHAN) {
+#pragma unroll
+        for (int bb = 0; bb < C::BCH; ++bb)
+#pragma unroll
+            for (int d = 0; d < C::ND; ++d) part[bb][d] = (R)0;
+    } else if (first) {
+#pragma unroll
+        for (int bb = 0; bb < C::BCH; ++bb)
+#pragma unroll
+            for (int d = 0; d < C::ND; ++d) acc[bb][d] = (R)0;
+    }
+    const R *px = Iq + i_index<C>(0, 0, ax, cx, 0, 0);
+    const R *py = Iq + i_index<C>(1, 0, ay, cy, 0, 0);
+    const R *pz = Iq + i_index<C>(2, 0, az, cz, 0, 0);
+    constexpr int MU_STRIDE = C::IBLK;
+#pragma unroll 1
+    for (int mu = 0; mu < C::NRYS; ++mu) {
+#pragma unroll
+        for (int bb = 0; bb < NBC; ++bb) {
+            constexpr int dummy = 0;
+            (void)dummy;
+            const int b = B0 + bb;
+            const int bx = cart_x(C::Lb, b), by = cart_y(C::Lb, b), bz = cart_z(C::Lb, b);
+            R X[LD1], Y[LD1], Z[LD1];
+#pragma unroll
+            for (int t = 0; t < LD1; ++t) {
+                X[t] = px[bx * LD1 + t];
+                Y[t] = py[by * LD1 + t];
+                Z[t] = pz[bz * LD1 + t];
+            }
+#pragma unroll
+            for (int d = 0; d < C::ND; ++d) {
+                const int dx = cart_x(C::Ld, d), dy = cart_y(C::Ld, d), dz = cart_z(C::Ld, d);
+                R xy = X[dx] * Y[dy];
+                if constexpr (KAHAN)
+                    part[bb][d] = fma(xy, Z[dz], part[bb][d]);
+                else
+                    acc[bb][d] = fma(xy, Z[dz], acc[bb][d]);
+            }
+        }
+        px += MU_STRIDE;
+        py += MU_STRIDE;
+        pz += MU_STRIDE;
+    }
+    if constexpr (KAHAN) {
+#pragma unroll
+        for (int bb = 0; bb < C::BCH; ++bb)
+#pragma unroll
+            for (int d = 0; d < C::ND; ++d) {
+                if (first) {
+                    acc[bb][d] = part[bb][d];
+                    comp[bb][d] = (R)0;
+                } else {
+                    // Kahan-compensated sum over primitive quartets
+                    R y = part[bb][d] - comp[bb][d];
+                    R t = acc[bb][d] + y;
+                    comp[bb][d] = (t - acc[bb][d]) - y;
+                    acc[bb][d] = t;
+                }
+            }
+    }
+}
+
+template <class C, bool KAHAN>
+__device__ __forceinline__ void quad_dispatch(int ch, const typename C::R *Iq, int a, int c,
+                                              typename C::R (&acc)[C::BCH][C::ND],
+                                              typename C::R (&comp)[C::BCH][C::ND], bool first) {
+    if constexpr (C::NCH == 1) {
+        quad_chunk<C, 0, KAHAN>(Iq, a, c, acc, comp, first);
+    } else {
+        switch (ch) {
+            case 0: quad_chunk<C, 0, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 1: if constexpr (C::NCH > 1) quad_chunk<C, 1, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 2: if constexpr (C::NCH > 2) quad_chunk<C, 2, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 3: if constexpr (C::NCH > 3) quad_chunk<C, 3, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 4: if constexpr (C::NCH > 4) quad_chunk<C, 4, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 5: if constexpr (C::NCH > 5) quad_chunk<C, 5, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 6: if constexpr (C::NCH > 6) quad_chunk<C, 6, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 7: if constexpr (C::NCH > 7) quad_chunk<C, 7, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 8: if constexpr (C::NCH > 8) quad_chunk<C, 8, KAHAN>(Iq, a, c, acc, comp, first); break;
+            case 9: if constexpr (C::NCH > 9) quad_chunk<C, 9, KAHAN>(Iq, a, c, acc, comp, first); break;
+            default: break;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+template <class C, bool KAHAN>
+__global__ void __launch_bounds__(C::THREADS)
+eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+    using R = typename C::R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
+    R *bc_s = reinterpret_cast<R *>(smem + C::OFF_BC);
+    unsigned long long *bmax_s = reinterpret_cast<unsigned long long *>(smem + C::OFF_BMAX);
+    R *H_s = reinterpret_cast<R *>(smem + C::OFF_H);
+    R *I_s = reinterpret_cast<R *>(smem + C::OFF_I);
+    __shared__ int maxprim_s;
+
+    const int tid = threadIdx.x;
+    const long long q0 = (long long)blockIdx.x * C::Q;
+    const int qn = (int)((args.nq - q0) < C::Q ? (args.nq - q0) : C::Q);
+
+    // phase D item of this thread (fixed across primitive iterations)
+    const bool has_item = tid < C::Q * C::ITEMS_D;
+    int dq = 0, da = 0, dc = 0, dch = 0;
+    if (has_item) {
+        dq = tid / C::ITEMS_D;
+        int r = tid % C::ITEMS_D;
+        da = r / (C::NC * C::NCH);
+        dc = (r / C::NCH) % C::NC;
+        dch = r % C::NCH;
+    }
+    R acc[C::BCH][C::ND];
+    R comp[C::BCH][C::ND];  // Kahan compensation; eliminated when KAHAN is false
+
+    if (tid == 0) maxprim_s = 1;
+    __syncthreads();
+    for (int prim = 0; prim < maxprim_s; ++prim) {
+        // A0: geometry per quartet (canonical shell order)
+        for (int q = tid; q < C::Q; q += C::THREADS) {
+            int np = 0;
+            double *geo = geo_s + q * G_N;
+            if (q < qn) {
+                int4 g = args.quartets[q0 + q];
+                int ids[4] = {g.x, g.y, g.z, g.w};
+                int4 qt = make_int4(ids[args.perm[0]], ids[args.perm[1]], ids[args.perm[2]],
+                                    ids[args.perm[3]]);
+                phase_geometry<C>(sh, qt, prim, geo, np);
+            } else {
+                geo[G_PREF] = 0.0;
+                geo[G_T] = 0.0;
+                for (int s = G_P; s < G_N; ++s) geo[s] = (s == G_P || s == G_Q) ? 1.0 : 0.0;
+            }
+            if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+        }
+        __syncthreads();
+        // A1: roots, weights, B and C per (quartet, root)
+        for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
+            int q = it / C::NRYS, mu = it % C::NRYS;
+            phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
+        }
+        __syncthreads();
+        // B: VRR (+ bra HRR, + ket HRR when fused) per (quartet, root, axis)
+        for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
+            int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
+            int mu = r / 3, xi = r % 3;
+            phase_vrr<C>(bc_s + q * C::NRYS * S_N, geo_s + q * G_N, mu, xi,
+                         H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
+                         I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
+        }
+        __syncthreads();
+        if constexpr (!C::FUSE_BC) {
+            constexpr int NIJ = (C::La + 1) * (C::Lb + 1);
+            for (int it = tid; it < C::Q * C::NRYS * 3 * NIJ; it += C::THREADS) {
+                int q = it / (C::NRYS * 3 * NIJ), r = it % (C::NRYS * 3 * NIJ);
+                int mu = r / (3 * NIJ);
+                r %= 3 * NIJ;
+                int xi = r / NIJ, ij = r % NIJ;
+                phase_ket<C>(geo_s + q * G_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
+                             H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
+                             I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
+            }
+            __syncthreads();
+        }
+        // D: quadrature into register accumulators
+        if (has_item)
+            quad_dispatch<C, KAHAN>(dch, I_s + (size_t)dq * (C::I_BYTES / sizeof(R)), da, dc, acc,
+                                    comp, prim == 0);
+        __syncthreads();
+    }
+
+    const bool live = has_item && dq < qn;
+    const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
+              st3 = args.ostride[3];
+    if (args.out_fp64 != nullptr) {
+        // FP64 output in the generic class's row-major order
+        if (live) {
+            double *o = args.out_fp64 + (q0 + dq) * (long long)C::NERI + da * st0 + dc * st2;
+            bool bad = false;
+#pragma unroll
+            for (int bb = 0; bb < C::BCH; ++bb) {
+                int b = dch * C::BCH + bb;
+                if (b < C::NB) {
+#pragma unroll
+                    for (int d = 0; d < C::ND; ++d) {
+                        double v = (double)acc[bb][d];
+                        bad |= !(fabs(v) <= 1.7976931348623157e308);
+                        o[b * st1 + d * st3] = v;
+                    }
+                }
+            }
+            if (bad) atomicOr(args.err, 1);
+        }
+        return;
+    }
+
+    // ---- compressed output (Sec. II-D) ----
+    for (int q = tid; q < C::Q; q += C::THREADS) bmax_s[q] = 0ull;
+    __syncthreads();
+    if (live) {
+        // b_max = max |x| over the quartet; non-negative IEEE values order like their bit
+        // patterns, so an integer atomicMax on the bits is exact
+        bool bad = false;
+        unsigned long long mb = 0ull;
+#pragma unroll
+        for (int bb = 0; bb < C::BCH; ++bb)
+            if (dch * C::BCH + bb < C::NB)
+#pragma unroll
+                for (int d = 0; d < C::ND; ++d) {
+                    double v = fabs((double)acc[bb][d]);
+                    bad |= !(v <= 1.7976931348623157e308);
+                    unsigned long long u = (unsigned long long)__double_as_longlong(v);
+                    mb = u > mb ? u : mb;
+                }
+        atomicMax(bmax_s + dq, mb);
+        if (bad) atomicOr(args.err, 1);
+    }
+    // staging buffer for the tile's bitstream (aliases the H/I region)
+    const int bits = args.bits;
+    const long long bit0 = q0 * (long long)C::NERI * bits;
+    const long long bit1 = (q0 + qn) * (long long)C::NERI * bits;
+    const long long w0 = bit0 >> 5;
+    const long long w1 = (bit1 + 31) >> 5;
+    const int nw = (int)(w1 - w0);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem + C::OFF_U);
+    __syncthreads();  // quadrature reads of I are complete; b_max final
+    for (int w = tid; w < nw; w += C::THREADS) stage[w] = 0u;
+    __syncthreads();
+    if (live) {
+        const double M = (double)((1u << (bits - 1)) - 1u);
+        double bmax = __longlong_as_double((long long)bmax_s[dq]);
+        float eps = (float)(bmax / M);
+        if (da == 0 && dc == 0 && dch == 0) args.scales[q0 + dq] = eps;
+        R inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
+        const uint32_t mask = (1u << bits) - 1u;
+        const R Mr = (R)M;
+        const long long qbase = (q0 + dq) * (long long)C::NERI + da * st0 + dc * st2;
+#pragma unroll
+        for (int bb = 0; bb < C::BCH; ++bb) {
+            int b = dch * C::BCH + bb;
+            if (b < C::NB) {
+#pragma unroll
+                for (int d = 0; d < C::ND; ++d) {
+                    R v = RTraits<R>::round_away(acc[bb][d] * inv);
+                    v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
+                    uint32_t code = (uint32_t)(int)v & mask;
+                    long long s = (qbase + b * st1 + d * st3) * bits - (w0 << 5);
+                    int wi = (int)(s >> 5), off = (int)(s & 31);
+                    atomicOr(stage + wi, code << off);
+                    if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                }
+            }
+        }
+    }
+    __syncthreads();
+    // store the tile's words; partial edge words are merged with the neighbour tile's bits
+    const bool last_tile = (q0 + qn) >= args.nq;
+    const int head_bits = (int)(bit0 & 31);
+    const int tail_bits = (int)(bit1 & 31);
+    for (int w = tid; w < nw; w += C::THREADS) {
+        uint32_t v = stage[w];
+        long long gw = w0 + w;
+        uint32_t keep = 0xffffffffu;  // bits of this word owned by this tile
+        if (w == 0 && head_bits) keep &= ~((1u << head_bits) - 1u);
+        if (w == nw - 1 && tail_bits && !last_tile) keep &= (1u << tail_bits) - 1u;
+        if (keep == 0xffffffffu) {
+            args.packed[gw] = v;
+        } else {
+            atomicAnd(args.packed + gw, ~keep);
+            atomicOr(args.packed + gw, v & keep);
+        }
+    }
+    if (last_tile) {
+        for (long long w = w1 + tid; w < args.seg_words; w += C::THREADS) args.packed[w] = 0u;
+    }
+}
+
+// Host-side launch helper for one canonical class.
+template <int La, int Lb, int Lc, int Ld, typename R, bool KAHAN>
+cudaError_t launch_class(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
+                         cudaStream_t stream) {
+    using C = Cfg<La, Lb, Lc, Ld, R>;
+    if (args.nq <= 0) return cudaSuccess;
+    auto kern = eri_class_kernel<C, KAHAN>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long long grid = (args.nq + C::Q - 1) / C::Q;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)grid, C::THREADS, C::SMEM, stream>>>(sh, tb, args);
+    return cudaGetLastError();
+}
+
+// The 55 canonical classes (Sec. II-B, Eq. 3): La >= Lb, Lc >= Ld, n_ga n_gb >= n_gc n_gd.
+__host__ __device__ constexpr int canonical_class(int idx) {
+    int k = 0;
+    for (int La = 0; La < 4; ++La)
+        for (int Lb = 0; Lb <= La; ++Lb)
+            for (int Lc = 0; Lc < 4; ++Lc)
+                for (int Ld = 0; Ld <= Lc; ++Ld)
+                    if (ncart(La) * ncart(Lb) >= ncart(Lc) * ncart(Ld)) {
+                        if (k == idx) return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld;
+                        ++k;
+                    }
+    return -1;
+}
+constexpr int kNumCanonical = 55;
+
+}  // namespace eri

@@ -1,0 +1,521 @@
+// eri_plan.cu -- host side of the C ABI declared in include/eri.h: shell validation and
+// normalisation (Sec. II-A), device-side stable sort of quartets by class, the output
+// layouts, and the per-class kernel launches.
+#include <cub/device/device_radix_sort.cuh>
+
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "eri_internal.h"
+
+namespace eri {
+
+namespace {
+
+LaunchFn g_launch[256 * kNumVariants];
+std::once_flag g_launch_once;
+
+void register_all() {
+    eri_register_tu_0(g_launch); eri_register_tu_1(g_launch); eri_register_tu_2(g_launch);
+    eri_register_tu_3(g_launch); eri_register_tu_4(g_launch); eri_register_tu_5(g_launch);
+    eri_register_tu_6(g_launch); eri_register_tu_7(g_launch); eri_register_tu_8(g_launch);
+    eri_register_tu_9(g_launch); eri_register_tu_10(g_launch); eri_register_tu_11(g_launch);
+    eri_register_tu_12(g_launch); eri_register_tu_13(g_launch); eri_register_tu_14(g_launch);
+    eri_register_tu_15(g_launch);
+}
+
+int ncart_h(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Axis-aligned normalisation of Sec. II-A:
+// N = (2 alpha/pi)^{3/4} (4 alpha)^{L/2} / sqrt((2L-1)!!).
+double shell_norm(double alpha, int L) {
+    double df = 1.0;
+    for (int k = 2 * L - 1; k > 1; k -= 2) df *= k;
+    return std::pow(2.0 * alpha / 3.14159265358979323846, 0.75) * std::pow(4.0 * alpha, 0.5 * L) /
+           std::sqrt(df);
+}
+
+// Canonical representative of a generic class (Sec. II-B, Eq. 3) and the shell permutation:
+// canonical slot k takes generic slot perm[k].
+struct Canon {
+    int cls;
+    int perm[4];
+    int ostride[4];
+};
+
+Canon canonicalise(int cls) {
+    int L[4] = {(cls >> 6) & 3, (cls >> 4) & 3, (cls >> 2) & 3, cls & 3};
+    int bra[2] = {0, 1}, ket[2] = {2, 3};
+    if (L[0] < L[1]) { bra[0] = 1; bra[1] = 0; }
+    if (L[2] < L[3]) { ket[0] = 3; ket[1] = 2; }
+    Canon c;
+    bool swap = ncart_h(L[bra[0]]) * ncart_h(L[bra[1]]) < ncart_h(L[ket[0]]) * ncart_h(L[ket[1]]);
+    int p[4] = {bra[0], bra[1], ket[0], ket[1]};
+    if (swap) { p[0] = ket[0]; p[1] = ket[1]; p[2] = bra[0]; p[3] = bra[1]; }
+    int gstride[4];
+    gstride[3] = 1;
+    for (int g = 2; g >= 0; --g) gstride[g] = gstride[g + 1] * ncart_h(L[g + 1]);
+    for (int k = 0; k < 4; ++k) {
+        c.perm[k] = p[k];
+        c.ostride[k] = gstride[p[k]];
+    }
+    c.cls = ((L[p[0]] * 4 + L[p[1]]) * 4 + L[p[2]]) * 4 + L[p[3]];
+    return c;
+}
+
+__global__ void classify_kernel(const int4 *__restrict__ q, long long n, const int *__restrict__ L,
+                                int n_shells, uint8_t *__restrict__ keys, int *__restrict__ vals,
+                                int *__restrict__ err) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 t = q[i];
+    bool ok = t.x >= 0 && t.x < n_shells && t.y >= 0 && t.y < n_shells && t.z >= 0 &&
+              t.z < n_shells && t.w >= 0 && t.w < n_shells;
+    if (!ok) {
+        atomicOr(err, 4);
+        keys[i] = 0;
+    } else {
+        keys[i] = (uint8_t)(((L[t.x] * 4 + L[t.y]) * 4 + L[t.z]) * 4 + L[t.w]);
+    }
+    vals[i] = (int)i;
+}
+
+__global__ void all_quartets_kernel(int n, long long total, int4 *__restrict__ q) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    long long r = i;
+    int l = (int)(r % n); r /= n;
+    int k = (int)(r % n); r /= n;
+    int j = (int)(r % n); r /= n;
+    q[i] = make_int4((int)r, j, k, l);
+}
+
+__global__ void gather_kernel(const int4 *__restrict__ src, const int *__restrict__ idx,
+                              long long n, int4 *__restrict__ dst) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) dst[i] = src[idx[i]];
+}
+
+__global__ void histogram_kernel(const uint8_t *__restrict__ keys, long long n,
+                                 unsigned long long *__restrict__ counts) {
+    __shared__ unsigned int h[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        atomicAdd(&h[keys[i]], 1u);
+    __syncthreads();
+    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+        if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
+}
+
+}  // namespace
+
+}  // namespace eri
+
+using namespace eri;
+
+struct eri_plan_s {
+    int device = 0;
+    int precision = ERI_FP64;
+    int n_shells = 0;
+    long long n_prims = 0;
+    long long nq = 0;
+    int max_nprim = 1;
+    // device arrays
+    double *d_cx = nullptr, *d_cy = nullptr, *d_cz = nullptr, *d_exps = nullptr, *d_cn = nullptr;
+    int *d_pofs = nullptr, *d_nprim = nullptr;
+    int4 *d_quartets = nullptr;  // class-sorted
+    int *d_perm = nullptr;       // sorted position -> caller's index
+    int *d_err = nullptr;
+    // host layout
+    long long count[256] = {0};
+    long long first[256] = {0};
+    long long fp64_off[256] = {0};
+    Tables tables;
+};
+
+namespace {
+
+void free_plan(eri_plan_s *p) {
+    if (!p) return;
+    cudaFree(p->d_cx);
+    cudaFree(p->d_cy);
+    cudaFree(p->d_cz);
+    cudaFree(p->d_exps);
+    cudaFree(p->d_cn);
+    cudaFree(p->d_pofs);
+    cudaFree(p->d_nprim);
+    cudaFree(p->d_quartets);
+    cudaFree(p->d_perm);
+    cudaFree(p->d_err);
+    delete p;
+}
+
+eri_status_t cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return ERI_OK;
+    if (e == cudaErrorMemoryAllocation) return ERI_E_NOMEM;
+    return ERI_E_CUDA;
+}
+
+template <typename T>
+cudaError_t upload(T **dst, const std::vector<T> &src) {
+    cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, src.size()) * sizeof(T));
+    if (e != cudaSuccess) return e;
+    if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+size_t packed_segment_bytes(long long nq, int neri, int bits) {
+    unsigned long long b = ((unsigned long long)nq * neri * bits + 7) / 8;
+    return (size_t)((b + 255) / 256 * 256);
+}
+
+eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed,
+                        float *d_scales, size_t packed_off, cudaStream_t stream) {
+    if (p->count[cls] == 0) return ERI_OK;
+    Canon c = canonicalise(cls);
+    ShellsDev sh{p->d_cx, p->d_cy, p->d_cz, p->d_pofs, p->d_nprim, p->d_exps, p->d_cn};
+    ClassArgs a{};
+    for (int k = 0; k < 4; ++k) {
+        a.perm[k] = c.perm[k];
+        a.ostride[k] = c.ostride[k];
+    }
+    a.quartets = p->d_quartets + p->first[cls];
+    a.nq = p->count[cls];
+    a.err = p->d_err;
+    int neri = ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) *
+               ncart_h(cls & 3);
+    if (d_out) {
+        a.out_fp64 = d_out + p->fp64_off[cls];
+    } else {
+        a.packed = reinterpret_cast<uint32_t *>(static_cast<char *>(d_packed) + packed_off);
+        a.seg_words = (long long)(packed_segment_bytes(p->count[cls], neri, bits) / 4);
+        a.scales = d_scales + p->first[cls];
+        a.bits = bits;
+    }
+    int variant = p->precision == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
+    LaunchFn fn = g_launch[c.cls * kNumVariants + variant];
+    if (!fn) return ERI_E_UNSUPPORTED;
+    return cuda_status(fn(sh, p->tables, a, stream));
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *eri_status_string(eri_status_t s) {
+    switch (s) {
+        case ERI_OK: return "ERI_OK";
+        case ERI_E_INVALID: return "ERI_E_INVALID";
+        case ERI_E_UNSUPPORTED: return "ERI_E_UNSUPPORTED";
+        case ERI_E_NOMEM: return "ERI_E_NOMEM";
+        case ERI_E_CUDA: return "ERI_E_CUDA";
+        case ERI_E_TIMEOUT: return "ERI_E_TIMEOUT";
+        case ERI_E_NUMERIC: return "ERI_E_NUMERIC";
+    }
+    return "ERI_E_UNKNOWN";
+}
+
+int32_t eri_class_id(int32_t La, int32_t Lb, int32_t Lc, int32_t Ld) {
+    if (La < 0 || La > 3 || Lb < 0 || Lb > 3 || Lc < 0 || Lc > 3 || Ld < 0 || Ld > 3) return -1;
+    return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld;
+}
+
+eri_status_t eri_class_shape(int32_t cls, int32_t *n_eri, int32_t *n_rys) {
+    if (cls < 0 || cls > 255) return ERI_E_INVALID;
+    int L[4] = {(cls >> 6) & 3, (cls >> 4) & 3, (cls >> 2) & 3, cls & 3};
+    if (n_eri) *n_eri = ncart_h(L[0]) * ncart_h(L[1]) * ncart_h(L[2]) * ncart_h(L[3]);
+    if (n_rys) *n_rys = (L[0] + L[1] + L[2] + L[3]) / 2 + 1;
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const int32_t *quartets,
+                             int64_t n_quartets, const eri_plan_opts_t *opts, eri_plan_t *out) {
+    if (!out || (!shells && n_shells > 0) || n_shells < 0) return ERI_E_INVALID;
+    eri_plan_opts_t o{ERI_FP64, ERI_EXPLICIT, 0, 0};
+    if (opts) o = *opts;
+    if (o.precision != ERI_FP64 && o.precision != ERI_MIXED) return ERI_E_INVALID;
+    if (o.quartet_mode != ERI_EXPLICIT && o.quartet_mode != ERI_ALL) return ERI_E_INVALID;
+    long long nq;
+    if (o.quartet_mode == ERI_ALL) {
+        double t = (double)n_shells * n_shells * n_shells * n_shells;
+        if (t >= 2147483647.0) return ERI_E_UNSUPPORTED;
+        nq = (long long)n_shells * n_shells * n_shells * n_shells;
+    } else {
+        if (n_quartets < 0 || (n_quartets > 0 && !quartets)) return ERI_E_INVALID;
+        if (n_quartets >= 2147483647LL) return ERI_E_UNSUPPORTED;
+        nq = n_quartets;
+    }
+    // host validation and normalisation of the shells
+    std::vector<double> cx(n_shells), cy(n_shells), cz(n_shells), ex, cn;
+    std::vector<int> pofs(n_shells), np(n_shells), Ls(n_shells);
+    int max_nprim = 1;
+    for (int s = 0; s < n_shells; ++s) {
+        const eri_shell_t &sh = shells[s];
+        if (sh.L < 0 || sh.L > 3) return sh.L > 3 ? ERI_E_UNSUPPORTED : ERI_E_INVALID;
+        if (sh.nprim < 1 || !sh.exps || !sh.coefs) return ERI_E_INVALID;
+        for (int x = 0; x < 3; ++x)
+            if (!std::isfinite(sh.center[x])) return ERI_E_INVALID;
+        cx[s] = sh.center[0];
+        cy[s] = sh.center[1];
+        cz[s] = sh.center[2];
+        pofs[s] = (int)ex.size();
+        np[s] = sh.nprim;
+        Ls[s] = sh.L;
+        max_nprim = std::max(max_nprim, sh.nprim);
+        for (int k = 0; k < sh.nprim; ++k) {
+            double a = sh.exps[k], c = sh.coefs[k];
+            if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(c)) return ERI_E_INVALID;
+            ex.push_back(a);
+            cn.push_back(c * shell_norm(a, sh.L));
+        }
+    }
+    if (ex.size() >= 2147483647ull) return ERI_E_UNSUPPORTED;
+    std::call_once(g_launch_once, register_all);
+
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) return ERI_E_INVALID;
+    eri_plan_s *p = new (std::nothrow) eri_plan_s();
+    if (!p) return ERI_E_NOMEM;
+    p->device = o.device;
+    p->precision = o.precision;
+    p->n_shells = n_shells;
+    p->n_prims = (long long)ex.size();
+    p->nq = nq;
+    p->max_nprim = max_nprim;
+    if ((e = tables_for_current_device(&p->tables)) != cudaSuccess) { free_plan(p); return cuda_status(e); }
+    int *d_L = nullptr;
+    e = upload(&p->d_cx, cx);
+    if (e == cudaSuccess) e = upload(&p->d_cy, cy);
+    if (e == cudaSuccess) e = upload(&p->d_cz, cz);
+    if (e == cudaSuccess) e = upload(&p->d_exps, ex);
+    if (e == cudaSuccess) e = upload(&p->d_cn, cn);
+    if (e == cudaSuccess) e = upload(&p->d_pofs, pofs);
+    if (e == cudaSuccess) e = upload(&p->d_nprim, np);
+    if (e == cudaSuccess) e = upload(&d_L, Ls);
+    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
+    if (e != cudaSuccess) { cudaFree(d_L); free_plan(p); return cuda_status(e); }
+
+    if (nq > 0) {
+        int4 *d_in = nullptr;
+        uint8_t *d_keys = nullptr, *d_keys_sorted = nullptr;
+        int *d_vals = nullptr;
+        unsigned long long *d_counts = nullptr;
+        void *d_tmp = nullptr;
+        size_t tmp_bytes = 0;
+        int *d_verr = nullptr;
+        const unsigned blocks = (unsigned)((nq + 255) / 256);
+        bool own_in = true;
+        do {
+            if (o.quartet_mode == ERI_ALL) {
+                if ((e = cudaMalloc(&d_in, nq * sizeof(int4))) != cudaSuccess) break;
+                all_quartets_kernel<<<blocks, 256>>>(n_shells, nq, d_in);
+            } else if (o.flags & ERI_QUARTETS_ON_DEVICE) {
+                d_in = reinterpret_cast<int4 *>(const_cast<int32_t *>(quartets));
+                own_in = false;
+            } else {
+                if ((e = cudaMalloc(&d_in, nq * sizeof(int4))) != cudaSuccess) break;
+                if ((e = cudaMemcpy(d_in, quartets, nq * sizeof(int4), cudaMemcpyHostToDevice)) !=
+                    cudaSuccess)
+                    break;
+            }
+            if ((e = cudaMalloc(&d_keys, nq)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&d_keys_sorted, nq)) != cudaSuccess) break;
+            if ((e = cudaMalloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
+            if ((e = cudaMalloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
+            if ((e = cudaMalloc(&d_verr, sizeof(int))) != cudaSuccess) break;
+            if ((e = cudaMemset(d_verr, 0, sizeof(int))) != cudaSuccess) break;
+            classify_kernel<<<blocks, 256>>>(d_in, nq, d_L, n_shells, d_keys, d_vals, d_verr);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            // stable radix sort on the 8-bit class key keeps the caller's order within a class
+            e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_vals,
+                                                p->d_perm, (int)nq, 0, 8);
+            if (e != cudaSuccess) break;
+            if ((e = cudaMalloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
+            e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_vals,
+                                                p->d_perm, (int)nq, 0, 8);
+            if (e != cudaSuccess) break;
+            if ((e = cudaMalloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
+            gather_kernel<<<blocks, 256>>>(d_in, p->d_perm, nq, p->d_quartets);
+            if ((e = cudaMalloc(&d_counts, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
+            if ((e = cudaMemset(d_counts, 0, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
+            histogram_kernel<<<std::min<unsigned>(blocks, 4096u), 256>>>(d_keys_sorted, nq, d_counts);
+            if ((e = cudaGetLastError()) != cudaSuccess) break;
+            unsigned long long counts[256];
+            if ((e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                break;
+            int verr = 0;
+            if ((e = cudaMemcpy(&verr, d_verr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+                break;
+            if (verr) e = cudaErrorInvalidValue;  // mapped to ERI_E_INVALID below
+            for (int c = 0; c < 256; ++c) p->count[c] = (long long)counts[c];
+        } while (false);
+        cudaError_t sync_e = cudaDeviceSynchronize();
+        if (e == cudaSuccess) e = sync_e;
+        if (own_in) cudaFree(d_in);
+        cudaFree(d_keys);
+        cudaFree(d_keys_sorted);
+        cudaFree(d_vals);
+        cudaFree(d_counts);
+        cudaFree(d_tmp);
+        cudaFree(d_verr);
+        if (e != cudaSuccess) {
+            cudaFree(d_L);
+            free_plan(p);
+            return e == cudaErrorInvalidValue ? ERI_E_INVALID : cuda_status(e);
+        }
+    }
+    cudaFree(d_L);
+    long long f = 0, off = 0;
+    for (int c = 0; c < 256; ++c) {
+        p->first[c] = f;
+        p->fp64_off[c] = off;
+        int neri = 0;
+        eri_class_shape(c, &neri, nullptr);
+        f += p->count[c];
+        off += p->count[c] * neri;
+    }
+    *out = p;
+    return ERI_OK;
+}
+
+void eri_plan_destroy(eri_plan_t plan) {
+    if (!plan) return;
+    cudaSetDevice(plan->device);
+    free_plan(plan);
+}
+
+eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision) {
+    if (!plan || (precision != ERI_FP64 && precision != ERI_MIXED)) return ERI_E_INVALID;
+    plan->precision = precision;
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n) {
+    if (!plan || !n) return ERI_E_INVALID;
+    *n = plan->nq;
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quartets,
+                                 int32_t *n_eri_per_quartet, int64_t *first_quartet,
+                                 int64_t *fp64_offset) {
+    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (n_quartets) *n_quartets = plan->count[cls];
+    if (n_eri_per_quartet) eri_class_shape(cls, n_eri_per_quartet, nullptr);
+    if (first_quartet) *first_quartet = plan->first[cls];
+    if (fp64_offset) *fp64_offset = plan->fp64_off[cls];
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_quartet_order(eri_plan_t plan, int64_t *perm_out) {
+    if (!plan || (!perm_out && plan->nq > 0)) return ERI_E_INVALID;
+    if (plan->nq == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    std::vector<int> tmp(plan->nq);
+    cudaError_t e = cudaMemcpy(tmp.data(), plan->d_perm, plan->nq * sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_status(e);
+    for (long long i = 0; i < plan->nq; ++i) perm_out[i] = tmp[i];
+    return ERI_OK;
+}
+
+eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
+                                     size_t *byte_offset, size_t *bytes) {
+    if (!plan || cls < 0 || cls > 255 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    size_t off = 0;
+    for (int c = 0; c < cls; ++c) {
+        int neri = 0;
+        eri_class_shape(c, &neri, nullptr);
+        off += packed_segment_bytes(plan->count[c], neri, bits);
+    }
+    int neri = 0;
+    eri_class_shape(cls, &neri, nullptr);
+    if (byte_offset) *byte_offset = off;
+    if (bytes) *bytes = packed_segment_bytes(plan->count[cls], neri, bits);
+    return ERI_OK;
+}
+
+eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_bytes,
+                              size_t *scales_bytes) {
+    if (!plan || (bits != 0 && (bits < 2 || bits > 24))) return ERI_E_INVALID;
+    size_t total = 0;
+    for (int c = 0; c < 256; ++c) {
+        int neri = 0;
+        eri_class_shape(c, &neri, nullptr);
+        total += bits == 0 ? (size_t)plan->count[c] * neri * sizeof(double)
+                           : packed_segment_bytes(plan->count[c], neri, bits);
+    }
+    if (packed_bytes) *packed_bytes = total;
+    if (scales_bytes) *scales_bytes = bits == 0 ? 0 : (size_t)plan->nq * sizeof(float);
+    return ERI_OK;
+}
+
+eri_status_t eri_compute_class(eri_plan_t plan, int32_t cls, double *d_out, void *stream) {
+    if (!plan || cls < 0 || cls > 255 || (!d_out && plan->nq > 0)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_out) % 8) return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    return launch_one(plan, cls, d_out, 0, nullptr, nullptr, 0, (cudaStream_t)stream);
+}
+
+eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream) {
+    if (!plan || (!d_out && plan->nq > 0)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_out) % 8) return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    for (int c = 0; c < 256; ++c) {
+        eri_status_t s = launch_one(plan, c, d_out, 0, nullptr, nullptr, 0, (cudaStream_t)stream);
+        if (s != ERI_OK) return s;
+    }
+    return ERI_OK;
+}
+
+eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
+                                          void *d_packed, float *d_scales, void *stream) {
+    if (!plan || cls < 0 || cls > 255 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
+        return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    size_t off = 0;
+    eri_packed_class_offset(plan, bits, cls, &off, nullptr);
+    return launch_one(plan, cls, nullptr, bits, d_packed, d_scales, off, (cudaStream_t)stream);
+}
+
+eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
+                                    void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
+        return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    size_t off = 0;
+    for (int c = 0; c < 256; ++c) {
+        int neri = 0;
+        eri_class_shape(c, &neri, nullptr);
+        eri_status_t s = launch_one(plan, c, nullptr, bits, d_packed, d_scales, off, (cudaStream_t)stream);
+        if (s != ERI_OK) return s;
+        off += packed_segment_bytes(plan->count[c], neri, bits);
+    }
+    return ERI_OK;
+}
+
+eri_status_t eri_sync(eri_plan_t plan, void *stream) {
+    if (!plan) return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e != cudaSuccess) return ERI_E_CUDA;
+    int err = 0;
+    e = cudaMemcpy(&err, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return ERI_E_CUDA;
+    if (err) cudaMemset(plan->d_err, 0, sizeof(int));
+    if (err & 1) return ERI_E_NUMERIC;
+    if (err & 2) return ERI_E_TIMEOUT;
+    return ERI_OK;
+}
+
+}  // extern "C"

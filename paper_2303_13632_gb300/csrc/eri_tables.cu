@@ -1,0 +1,112 @@
+// eri_tables.cu -- device copies of the generated Rys/Boys tables and the component
+// diagnostics eri_boys_device / eri_rys_device (same device code as the ERI kernels).
+#include <mutex>
+
+#include "eri_device.cuh"
+#include "eri_internal.h"
+#include "eri_tables.inc"
+
+static_assert(RYS_NMAX == eri::kRysNmax, "table order mismatch");
+static_assert(RYS_DEG == eri::kRysDeg, "table degree mismatch");
+static_assert(BOYS_MMAX == eri::kBoysMmax && BOYS_TAYLOR == eri::kBoysTaylor &&
+                  BOYS_MCOLS == eri::kBoysCols && BOYS_NGRID == eri::kBoysNgrid,
+              "Boys grid mismatch");
+
+namespace eri {
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_tables_mutex;
+bool g_tables_ready[kMaxDevices];
+Tables g_tables[kMaxDevices];
+}  // namespace
+
+// Uploads the tables to the current device once; returns the device addresses.
+cudaError_t tables_for_current_device(Tables *out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_tables_mutex);
+    if (!g_tables_ready[dev]) {
+        Tables t{};
+        double *buf = nullptr;
+        size_t n = (size_t)RYS_CHEB_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN;
+        e = cudaMalloc(&buf, n * sizeof(double));
+        if (e != cudaSuccess) return e;
+        double *p = buf;
+        e = cudaMemcpy(p, rys_cheb_h, sizeof(rys_cheb_h), cudaMemcpyHostToDevice);
+        t.rys_cheb = p;
+        p += RYS_CHEB_LEN;
+        if (e == cudaSuccess) e = cudaMemcpy(p, rys_herm_x2_h, sizeof(rys_herm_x2_h), cudaMemcpyHostToDevice);
+        t.herm_x2 = p;
+        p += RYS_HERM_LEN;
+        if (e == cudaSuccess) e = cudaMemcpy(p, rys_herm_w_h, sizeof(rys_herm_w_h), cudaMemcpyHostToDevice);
+        t.herm_w = p;
+        p += RYS_HERM_LEN;
+        if (e == cudaSuccess) e = cudaMemcpy(p, boys_grid_h, sizeof(boys_grid_h), cudaMemcpyHostToDevice);
+        t.boys_grid = p;
+        if (e != cudaSuccess) {
+            cudaFree(buf);
+            return e;
+        }
+        for (int i = 0; i <= RYS_NMAX; ++i) {
+            t.tasym[i] = rys_tasym_h[i];
+            t.offset[i] = rys_offset_h[i];
+        }
+        for (int i = 0; i <= RYS_NMAX + 1; ++i) t.herm_off[i] = rys_herm_offset_h[i];
+        g_tables[dev] = t;
+        g_tables_ready[dev] = true;
+    }
+    *out = g_tables[dev];
+    return cudaSuccess;
+}
+
+__global__ void boys_kernel(Tables tb, int mmax, const double *__restrict__ T, long long n,
+                            double *__restrict__ F) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double f[kBoysMmax + 1];
+    boys_eval(mmax, T[i], tb.boys_grid, f);
+    for (int m = 0; m <= mmax; ++m) F[i * (mmax + 1) + m] = f[m];
+}
+
+__global__ void rys_kernel(Tables tb, int nroots, const double *__restrict__ T, long long n,
+                           double *__restrict__ X, double *__restrict__ W) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * nroots) return;
+    long long k = i / nroots;
+    int mu = (int)(i % nroots);
+    double x, w;
+    rys_root(tb, nroots, mu, T[k], x, w);
+    X[i] = x;
+    W[i] = w;
+}
+
+}  // namespace eri
+
+using namespace eri;
+
+extern "C" eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t n, double *d_F,
+                                        void *stream) {
+    if (mmax < 0 || mmax > kBoysMmax || n < 0 || (n > 0 && (!d_T || !d_F))) return ERI_E_INVALID;
+    if (n == 0) return ERI_OK;
+    Tables tb;
+    if (tables_for_current_device(&tb) != cudaSuccess) return ERI_E_CUDA;
+    long long blocks = (n + 255) / 256;
+    boys_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, mmax, d_T, n, d_F);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}
+
+extern "C" eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                                       double *d_w, void *stream) {
+    if (nroots < 1 || nroots > kRysNmax || n < 0 || (n > 0 && (!d_T || !d_x || !d_w)))
+        return ERI_E_INVALID;
+    if (n == 0) return ERI_OK;
+    Tables tb;
+    if (tables_for_current_device(&tb) != cudaSuccess) return ERI_E_CUDA;
+    long long total = n * nroots;
+    long long blocks = (total + 255) / 256;
+    rys_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, nroots, d_T, n, d_x, d_w);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}

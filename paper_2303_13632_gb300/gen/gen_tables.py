@@ -1,0 +1,243 @@
+"""Generates the constant tables of the CUDA path (run once; output is committed).
+
+    python -m paper_2303_13632_gb300.gen.gen_tables
+
+Writes ``csrc/eri_tables.inc`` with
+  * Rys roots x_mu = t_mu^2 and weights w_mu of the weight exp(-T t^2) on t in [0, 1]
+    (Sec. II-C, Eq. 5 inputs R_Rys), for n_Rys = 1..RYS_NMAX, as piecewise Chebyshev
+    series of degree RYS_DEG on unit intervals of T in [0, T_asym(n)), and the
+    2n-point Gauss-Hermite nodes/weights for the large-T limit
+        x_mu = u_mu^2 / T,  w_mu = H_mu / sqrt(T)      (T >= T_asym(n));
+  * the Boys function F_m(T_k) on the grid T_k = k * BOYS_STEP (k < BOYS_NGRID) for
+    m = 0..BOYS_MCOLS-1, used by a Taylor expansion plus downward recursion.
+
+Everything is computed with mpmath at 40 significant digits, independently of the
+CPU oracle.  The roots and weights come from the discretised Stieltjes procedure on a
+160-point Gauss-Legendre rule in t (well conditioned, unlike the moment route) and the
+eigen-decomposition of the Jacobi matrix.  Each Chebyshev piece is verified at random
+points against fresh high-precision values before the file is written.
+"""
+from __future__ import annotations
+
+import os
+import sys
+import time
+
+import mpmath as mp
+import numpy as np
+
+mp.mp.dps = 40
+
+RYS_NMAX = 9          # orders needed: forward L <= 12 -> 7; derivative classes need up to 9
+RYS_DEG = 12          # Chebyshev degree per unit interval
+GL_N = 160            # Gauss-Legendre points discretising the Rys measure
+BOYS_STEP = 0.1
+BOYS_TMAX = 50.0      # F_m(T) for T >= BOYS_TMAX comes from the asymptotic form
+BOYS_MMAX = 16        # highest order served by the device Boys function
+BOYS_TAYLOR = 10      # Taylor terms
+BOYS_MCOLS = BOYS_MMAX + BOYS_TAYLOR + 1
+BOYS_NGRID = int(round(BOYS_TMAX / BOYS_STEP)) + 2
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(_HERE), "csrc", "eri_tables.inc")
+
+
+def _legendre_pn(x, N):
+    p0, p1 = mp.mpf(1), x
+    for k in range(2, N + 1):
+        p0, p1 = p1, ((2 * k - 1) * x * p1 - (k - 1) * p0) / k
+    return p0, p1
+
+
+def gauss_legendre_01(N):
+    xs, _ = np.polynomial.legendre.leggauss(N)
+    nodes, weights = [], []
+    for x0 in xs:
+        x = mp.mpf(x0)
+        for _ in range(8):
+            p0, p1 = _legendre_pn(x, N)
+            dp = N * (x * p1 - p0) / (x * x - 1)
+            x = x - p1 / dp
+        p0, p1 = _legendre_pn(x, N)
+        dp = N * (x * p1 - p0) / (x * x - 1)
+        nodes.append((x + 1) / 2)
+        weights.append(1 / ((1 - x * x) * dp * dp))
+    return nodes, weights
+
+
+GL_T, GL_W = gauss_legendre_01(GL_N)
+GL_X = [t * t for t in GL_T]
+
+
+def rys_roots_weights(n, T):
+    """Gauss rule of order n for the measure exp(-T t^2) dt on [0,1] in the variable x = t^2."""
+    T = mp.mpf(T)
+    mass = [w * mp.exp(-T * x) for w, x in zip(GL_W, GL_X)]
+    alpha, beta = [], []
+    p_prev = [mp.mpf(0)] * GL_N
+    p = [mp.mpf(1)] * GL_N
+    nrm_prev = None
+    for k in range(n):
+        nrm = mp.fsum(m * v * v for m, v in zip(mass, p))
+        a = mp.fsum(m * x * v * v for m, x, v in zip(mass, GL_X, p)) / nrm
+        b = nrm if k == 0 else nrm / nrm_prev
+        alpha.append(a)
+        beta.append(b)
+        p_new = [(x - a) * v - (b if k > 0 else 0) * u for x, v, u in zip(GL_X, p, p_prev)]
+        p_prev, p, nrm_prev = p, p_new, nrm
+    J = mp.matrix(n, n)
+    for i in range(n):
+        J[i, i] = alpha[i]
+        if i + 1 < n:
+            J[i, i + 1] = J[i + 1, i] = mp.sqrt(beta[i + 1])
+    E, Q = mp.eigsy(J)
+    pairs = sorted((E[i], beta[0] * Q[0, i] ** 2) for i in range(n))
+    return [x for x, _ in pairs], [w for _, w in pairs]
+
+
+def hermite_positive(n):
+    """Positive nodes u and weights H of the 2n-point Gauss-Hermite rule (weight exp(-u^2))."""
+    N = 2 * n
+    xs, _ = np.polynomial.hermite.hermgauss(N)
+    out = []
+    for x0 in xs:
+        if x0 <= 0:
+            continue
+        x = mp.mpf(x0)
+        for _ in range(10):
+            h0, h1 = mp.mpf(1), 2 * x
+            for k in range(1, N):
+                h0, h1 = h1, 2 * x * h1 - 2 * k * h0
+            x = x - h1 / (2 * N * h0)
+        h0, h1 = mp.mpf(1), 2 * x
+        for k in range(1, N):
+            h0, h1 = h1, 2 * x * h1 - 2 * k * h0
+        w = mp.mpf(2) ** (N - 1) * mp.factorial(N) * mp.sqrt(mp.pi) / (N * N * h0 * h0)
+        out.append((x, w))
+    out.sort()
+    return out
+
+
+def asym_error(n, T, herm):
+    x, w = rys_roots_weights(n, T)
+    e = 0.0
+    for i in range(n):
+        e = max(e, float(abs((x[i] - herm[i][0] ** 2 / T) / x[i])),
+                float(abs((w[i] - herm[i][1] / mp.sqrt(T)) / w[i])))
+    return e
+
+
+def chebyshev_piece(n, a, b, deg):
+    nodes = [(a + b) / 2 + (b - a) / 2 * mp.cos(mp.pi * (k + mp.mpf(1) / 2) / (deg + 1))
+             for k in range(deg + 1)]
+    vals = [rys_roots_weights(n, t) for t in nodes]
+    coefs = []
+    for mu in range(n):
+        for kind in (0, 1):
+            fv = [v[kind][mu] for v in vals]
+            c = []
+            for j in range(deg + 1):
+                s = mp.fsum(fv[k] * mp.cos(mp.pi * j * (k + mp.mpf(1) / 2) / (deg + 1))
+                            for k in range(deg + 1)) * 2 / (deg + 1)
+                c.append(s)
+            c[0] /= 2
+            coefs.append([float(v) for v in c])
+    return coefs
+
+
+def clenshaw(c, u):
+    b1 = b2 = 0.0
+    for cj in reversed(c[1:]):
+        b1, b2 = 2 * u * b1 - b2 + cj, b1
+    return u * b1 - b2 + c[0]
+
+
+def boys_mp(m, T):
+    """F_m(T) = 1F1(m + 1/2; m + 3/2; -T) / (2m + 1)."""
+    return mp.hyp1f1(m + mp.mpf(1) / 2, m + mp.mpf(3) / 2, -mp.mpf(T)) / (2 * m + 1)
+
+
+def fmt(v: float) -> str:
+    return float(v).hex()
+
+
+def main():
+    t0 = time.time()
+    rng = np.random.default_rng(2303)
+    lines = []
+    lines.append("/* Generated by paper_2303_13632_gb300/gen/gen_tables.py -- do not edit. */")
+    lines.append(f"#define RYS_NMAX {RYS_NMAX}")
+    lines.append(f"#define RYS_DEG {RYS_DEG}")
+    lines.append(f"#define BOYS_STEP {BOYS_STEP!r}")
+    lines.append(f"#define BOYS_TMAX {BOYS_TMAX!r}")
+    lines.append(f"#define BOYS_MMAX {BOYS_MMAX}")
+    lines.append(f"#define BOYS_TAYLOR {BOYS_TAYLOR}")
+    lines.append(f"#define BOYS_MCOLS {BOYS_MCOLS}")
+    lines.append(f"#define BOYS_NGRID {BOYS_NGRID}")
+    tasym, offsets, cheb, hx, hw = [0], [0], [], [0.0], [0.0]
+    hoff = [0, 1]
+    worst = 0.0
+    for n in range(1, RYS_NMAX + 1):
+        herm = hermite_positive(n)
+        T = 30
+        while True:
+            if asym_error(n, T, herm) < 1e-16 and asym_error(n, T + 0.5, herm) < 1e-16:
+                break
+            T += 1
+        tasym.append(T)
+        offsets.append(len(cheb))
+        for k in range(T):
+            piece = chebyshev_piece(n, k, k + 1, RYS_DEG)
+            for _ in range(3):
+                Tt = k + rng.random()
+                x, w = rys_roots_weights(n, Tt)
+                u = 2 * (Tt - k) - 1
+                for mu in range(n):
+                    worst = max(worst,
+                                abs(clenshaw(piece[2 * mu], u) - float(x[mu])) / float(x[mu]),
+                                abs(clenshaw(piece[2 * mu + 1], u) - float(w[mu])) / float(w[mu]))
+            for f in piece:
+                cheb.extend(f)
+        for u, h in herm:
+            hx.append(float(u * u))
+            hw.append(float(h))
+        hoff.append(len(hx))
+        print(f"n={n}: T_asym={T}, pieces={T}, worst so far {worst:.3e}, {time.time() - t0:.0f}s",
+              flush=True)
+    if worst > 6e-16:
+        sys.exit(f"Chebyshev fit check failed: {worst}")
+    lines.append("/* first T of the Gauss-Hermite regime for n = index */")
+    lines.append("static const int rys_tasym_h[RYS_NMAX + 1] = {" + ", ".join(map(str, tasym)) + "};")
+    lines.append("/* offset (doubles) of the pieces of order n; piece k of order n holds 2n series of")
+    lines.append("   RYS_DEG+1 coefficients: x_1, w_1, x_2, w_2, ... on T in [k, k+1) */")
+    lines.append("static const long rys_offset_h[RYS_NMAX + 1] = {" + ", ".join(map(str, offsets)) + "};")
+    lines.append(f"#define RYS_CHEB_LEN {len(cheb)}")
+    lines.append("static const double rys_cheb_h[RYS_CHEB_LEN] = {")
+    for i in range(0, len(cheb), 4):
+        lines.append("  " + ", ".join(fmt(v) for v in cheb[i:i + 4]) + ",")
+    lines.append("};")
+    lines.append("/* Gauss-Hermite: index hermite_offset[n] + mu - 1 holds u_mu^2 and H_mu of order n */")
+    lines.append("static const int rys_herm_offset_h[RYS_NMAX + 2] = {" + ", ".join(map(str, hoff)) + "};")
+    lines.append(f"#define RYS_HERM_LEN {len(hx)}")
+    lines.append("static const double rys_herm_x2_h[RYS_HERM_LEN] = {" + ", ".join(fmt(v) for v in hx) + "};")
+    lines.append("static const double rys_herm_w_h[RYS_HERM_LEN] = {" + ", ".join(fmt(v) for v in hw) + "};")
+    # Boys grid
+    grid = []
+    for k in range(BOYS_NGRID):
+        T = mp.mpf(k) * mp.mpf(BOYS_STEP)
+        for m in range(BOYS_MCOLS):
+            grid.append(float(boys_mp(m, T)))
+    lines.append(f"#define BOYS_GRID_LEN {len(grid)}")
+    lines.append("/* F_m(k * BOYS_STEP) at index k * BOYS_MCOLS + m */")
+    lines.append("static const double boys_grid_h[BOYS_GRID_LEN] = {")
+    for i in range(0, len(grid), 4):
+        lines.append("  " + ", ".join(fmt(v) for v in grid[i:i + 4]) + ",")
+    lines.append("};")
+    with open(OUT, "w") as f:
+        f.write("\n".join(lines) + "\n")
+    print(f"wrote {OUT}: {len(cheb)} Chebyshev coefficients, {len(grid)} Boys values, "
+          f"fit check {worst:.3e}, {time.time() - t0:.0f}s")
+
+
+if __name__ == "__main__":
+    main()

@@ -36,6 +36,15 @@ def test_bound_and_full_range(bits):
         assert np.all(np.abs(x - xt) <= float(e) / 2 * (1 + 1e-12))
 
 
+def test_subnormal_scale():
+    """A quartet whose eps = b_max / M is below the smallest normal FP32 number keeps the
+    ANINT rounding of Eq. 10 against the stored (subnormal) eps; codes stay within +-M."""
+    x = np.array([3e-40, -1e-40, 2e-41])
+    q, e = oracle.compress_quartet(x, 16)
+    assert 0 < e < np.finfo(np.float32).tiny
+    assert np.max(np.abs(q)) <= 2 ** 15 - 1
+
+
 def test_zero_quartet():
     q, e = oracle.compress_quartet(np.zeros(7), 16)
     assert e == 0.0 and np.all(q == 0)

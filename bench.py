@@ -39,8 +39,12 @@ def classes():
     return [W.class_of_id(c) for c in range(256)]
 
 
+ONLY = None  # --classes: restrict the sweep to these class ids (profiling runs only)
+
+
 def class_counts(scale: float):
-    return {c: max(1, int(round(W.sweep_quartet_count(W.class_of_id(c)) * scale))) for c in range(256)}
+    return {c: (max(1, int(round(W.sweep_quartet_count(W.class_of_id(c)) * scale)))
+                if ONLY is None or c in ONLY else 0) for c in range(256)}
 
 
 def make_pool(seed_k: int = 2):
@@ -113,6 +117,10 @@ class ClockSampler:
 
 def oracle_sample_size(cls, eris: int) -> int:
     return max(2, eris // W.quartet_size(*cls))
+
+
+def nonempty(counts):
+    return [c for c in range(256) if counts[c] > 0]
 
 
 def cpu_oracle_rate(pool, quartets_by_class, counts):
@@ -263,7 +271,7 @@ def run_ours(args):
     def per_class_ms(precision):
         api.eri_plan_set_precision(plan, precision)
         res = {}
-        for c in range(256):
+        for c in nonempty(counts):
             api.eri_compute_compressed_class(plan, c, BITS, packed, scales, stream)  # warm
             a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             a.record(stream)
@@ -281,7 +289,7 @@ def run_ours(args):
 
     # ---- roofline of the dominant kernel (largest share of the mixed step) ----
     peaks, peak_kind = read_peaks()
-    dom = max(range(256), key=lambda c: ms_mixed[c])
+    dom = max(ms_mixed, key=lambda c: ms_mixed[c])
     dcls = cls_list[dom]
     flops = perfmodel.fp32_equivalent_flops(dcls, "mixed") * counts[dom]
     achieved = flops / (ms_mixed[dom] * 1e-3) / 1e12
@@ -293,17 +301,18 @@ def run_ours(args):
                          "by the FP32/FP64 peak ratio (1.25 TFLOP/s FP64)",
             "share": ms_mixed[dom] / sum(ms_mixed.values())}
     frac_all = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], "mixed", BITS, peaks["hbm_gbs"])
-                / (ms_mixed[c] * 1e-3) for c in range(256)}
+                / (ms_mixed[c] * 1e-3) for c in ms_mixed}
 
     # ---- accuracy on a sample, and the CPU oracle baseline ----
     line_extra = {}
     if rank == 0 and not args.no_check:
         rng = np.random.default_rng(99)
         sample_idx = {c: np.sort(rng.choice(counts[c], size=min(counts[c], oracle_sample_size(cls_list[c], args.ref_eris)),
-                                            replace=False)) for c in range(256)}
+                                            replace=False)) if counts[c] else np.zeros(0, dtype=np.int64)
+                      for c in range(256)}
         qhost = {}
         for c in range(256):
-            idx = torch.as_tensor(sample_idx[c] + first[c], device=dev)
+            idx = torch.as_tensor(sample_idx[c] + first[c], device=dev, dtype=torch.int64)
             qhost[c] = quartets[idx].cpu().numpy()
         g_cpu, cores, spent, ref = cpu_oracle_rate(pool, qhost, counts)
         errs = {}
@@ -314,7 +323,7 @@ def run_ours(args):
             words = packed.cpu().numpy().view(np.int16)
             sc = scales.cpu().numpy()
             worst = 0.0
-            for c in range(256):
+            for c in nonempty(counts):
                 nq, neri, fq, _ = api.eri_plan_class_info(plan, c)
                 off_bytes, _ = api.eri_packed_class_offset(plan, BITS, c)
                 vals, _ = ref[c]
@@ -338,9 +347,9 @@ def run_ours(args):
 
     if rank == 0:
         geris_mixed = {fmt_class(cls_list[c]): round(counts[c] * W.quartet_size(*cls_list[c]) / (ms_mixed[c] * 1e-3) / 1e9, 2)
-                       for c in range(256)}
+                       for c in ms_mixed}
         geris_fp64 = {fmt_class(cls_list[c]): round(counts[c] * W.quartet_size(*cls_list[c]) / (ms_fp64[c] * 1e-3) / 1e9, 2)
-                      for c in range(256)}
+                      for c in ms_fp64}
         out = {
             "metric": METRIC, "value": value, "unit": "GERIS", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -351,7 +360,7 @@ def run_ours(args):
             "roofline": roof,
             "roofline_frac_per_class": {"min": min(frac_all.values()), "median": statistics.median(frac_all.values()),
                                         "max": max(frac_all.values())},
-            "clocks": clk, "gpu_launches": 256 * args.steps,
+            "clocks": clk, "gpu_launches": len(nonempty(counts)) * args.steps,
             "per_class_geris": {"mixed": geris_mixed, "fp64": geris_fp64},
         }
         out.update(line_extra)
@@ -360,9 +369,9 @@ def run_ours(args):
         print(json.dumps(out), flush=True)
         if args.details:
             with open(args.details, "w") as f:
-                json.dump({"ms_mixed": {fmt_class(cls_list[c]): ms_mixed[c] for c in range(256)},
-                           "ms_fp64": {fmt_class(cls_list[c]): ms_fp64[c] for c in range(256)},
-                           "roofline_frac_mixed": {fmt_class(cls_list[c]): frac_all[c] for c in range(256)},
+                json.dump({"ms_mixed": {fmt_class(cls_list[c]): ms_mixed[c] for c in ms_mixed},
+                           "ms_fp64": {fmt_class(cls_list[c]): ms_fp64[c] for c in ms_fp64},
+                           "roofline_frac_mixed": {fmt_class(cls_list[c]): frac_all[c] for c in frac_all},
                            "counts": {fmt_class(cls_list[c]): counts[c] for c in range(256)}}, f, indent=1)
     plan.destroy()
     if dist is not None:
@@ -420,11 +429,16 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--scale", type=float, default=1.0)
-    ap.add_argument("--ref-eris", type=int, default=100000)
+    ap.add_argument("--ref-eris", type=int, default=1500000)
     ap.add_argument("--no-check", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--details", default=None)
+    ap.add_argument("--classes", default=None,
+                    help="comma-separated class ids ((La*4+Lb)*4+Lc)*4+Ld; profiling only")
     args = ap.parse_args()
+    global ONLY
+    if args.classes:
+        ONLY = {int(c) for c in args.classes.split(",")}
     if args.impl == "reference":
         run_reference(args)
     else:

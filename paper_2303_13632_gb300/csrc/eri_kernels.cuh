@@ -50,9 +50,11 @@ __host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
 
 // Per-quartet geometry kept in shared memory (FP64).
+// G_SWAB / G_SWCD = 1 when the VRR is built on B (D) and the HRR transfers to a (c); see
+// phase_geometry.
 enum GeoSlot {
     G_T = 0, G_PREF, G_P, G_Q, G_PAX, G_PAY, G_PAZ, G_QCX, G_QCY, G_QCZ, G_PQX, G_PQY, G_PQZ,
-    G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_N
+    G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD, G_N
 };
 // Per (quartet, root) setup values kept in shared memory (type R).
 enum BCSlot { S_B00 = 0, S_B10, S_B01, S_C0X, S_C0Y, S_C0Z, S_C1X, S_C1Y, S_C1Z, S_WZ, S_N };
@@ -131,8 +133,9 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
         // P - A = -eb/p (A - B), Q - C = -ed/q (C - D): computed from differences
         double PA = -eb * ip * AB, QC = -ed * iq * CD;
         double PQ = (A[x] + PA) - (Cc[x] + QC);
-        geo[G_PAX + x] = PA;
-        geo[G_QCX + x] = QC;
+        // the VRR is built on the centre nearer to P (the larger exponent): P - B = (P - A) + AB
+        geo[G_PAX + x] = eb > ea ? PA + AB : PA;
+        geo[G_QCX + x] = ed > ec ? QC + CD : QC;
         geo[G_PQX + x] = PQ;
         geo[G_ABX + x] = AB;
         geo[G_CDX + x] = CD;
@@ -150,11 +153,13 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     geo[G_T] = rho * pq2;
     geo[G_P] = p;
     geo[G_Q] = q;
+    geo[G_SWAB] = eb > ea ? 1.0 : 0.0;
+    geo[G_SWCD] = ed > ec ? 1.0 : 0.0;
 }
 
-// Phase A1: root mu of quartet geometry geo -> B and C values (Rys setup stage).  The root and
-// weight are evaluated in FP64; B and C are formed in the recurrence type R (the paper's FPGA
-// kernel does this stage in FP32).  Classes with L = 0 need only F_0 (no root).
+// Phase A1: root mu of quartet geometry geo -> B and C values (Rys setup stage), formed in
+// FP64 and rounded to the recurrence type R.  C00 and C00' use the offsets of P and Q from the
+// centres the VRR is built on (phase_geometry).  Classes with L = 0 need only F_0 (no root).
 template <class C>
 __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo, int mu,
                                             typename C::R *bc) {
@@ -171,55 +176,88 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
     }
     bc[S_WZ] = (R)(geo[G_PREF] * w);
     if constexpr (LTOT > 0) {
-        R p = (R)geo[G_P], q = (R)geo[G_Q], xr = (R)x;
-        R ipq = (R)1 / (p + q);
-        R fq = q * xr * ipq, fp = p * xr * ipq;
-        bc[S_B00] = (R)0.5 * xr * ipq;
-        bc[S_B10] = ((R)1 - fq) / ((R)2 * p);
-        bc[S_B01] = ((R)1 - fp) / ((R)2 * q);
+        double p = geo[G_P], q = geo[G_Q];
+        double ipq = 1.0 / (p + q);
+        double fq = q * x * ipq, fp = p * x * ipq;
+        bc[S_B00] = (R)(0.5 * x * ipq);
+        bc[S_B10] = (R)((1.0 - fq) * (0.5 / p));
+        bc[S_B01] = (R)((1.0 - fp) * (0.5 / q));
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
-            R pq = (R)geo[G_PQX + s];
-            bc[S_C0X + s] = (R)geo[G_PAX + s] - fq * pq;
-            bc[S_C1X + s] = (R)geo[G_QCX + s] + fp * pq;
+            double pq = geo[G_PQX + s];
+            bc[S_C0X + s] = (R)(geo[G_PAX + s] - fq * pq);
+            bc[S_C1X + s] = (R)(geo[G_QCX + s] + fp * pq);
         }
     }
 }
 
-// Bra HRR of one VRR column G(0..NAB) (fixed k) into h[i][j], i <= La, j <= Lb.
+// Bra HRR (Eq. 7) of one VRR column g(e) (fixed k) into h[i][j], i <= La, j <= Lb.
+// Built on A (swab = false): (i, j+1) = (i+1, j) + AB (i, j), i.e. transfer to b.
+// Built on B (swab = true):  (i+1, j) = (i, j+1) + BA (i, j), i.e. transfer to a.
+// Transferring away from the centre nearer to P keeps the cancellation factor of the transfer
+// bounded (|AB| / |P - target| <= 2 for each step).
 template <class C>
 __device__ __forceinline__ void bra_hrr(const typename C::R (&g)[C::NAB + 1], typename C::R ab,
-                                        typename C::R (&h)[C::La + 1][C::Lb + 1]) {
+                                        bool swab, typename C::R (&h)[C::La + 1][C::Lb + 1]) {
     using R = typename C::R;
-    R t[C::Lb + 1][C::NAB + 1];
+    if (!swab) {
+        R t[C::Lb + 1][C::NAB + 1];
 #pragma unroll
-    for (int i = 0; i <= C::NAB; ++i) t[0][i] = g[i];
+        for (int e = 0; e <= C::NAB; ++e) t[0][e] = g[e];
 #pragma unroll
-    for (int j = 1; j <= C::Lb; ++j)
+        for (int j = 1; j <= C::Lb; ++j)
 #pragma unroll
-        for (int i = 0; i + j <= C::NAB; ++i) t[j][i] = fma(ab, t[j - 1][i], t[j - 1][i + 1]);
+            for (int e = 0; e + j <= C::NAB; ++e) t[j][e] = fma(ab, t[j - 1][e], t[j - 1][e + 1]);
 #pragma unroll
-    for (int i = 0; i <= C::La; ++i)
+        for (int i = 0; i <= C::La; ++i)
 #pragma unroll
-        for (int j = 0; j <= C::Lb; ++j) h[i][j] = t[j][i];
+            for (int j = 0; j <= C::Lb; ++j) h[i][j] = t[j][i];
+    } else {
+        R t[C::La + 1][C::NAB + 1];
+#pragma unroll
+        for (int e = 0; e <= C::NAB; ++e) t[0][e] = g[e];
+#pragma unroll
+        for (int i = 1; i <= C::La; ++i)
+#pragma unroll
+            for (int e = 0; e + i <= C::NAB; ++e) t[i][e] = fma(-ab, t[i - 1][e], t[i - 1][e + 1]);
+#pragma unroll
+        for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+            for (int j = 0; j <= C::Lb; ++j) h[i][j] = t[i][j];
+    }
 }
 
-// Ket HRR of one transferred column s(0..NCD) (fixed i, j) into o[k][l], k <= Lc, l <= Ld.
+// Ket HRR of one transferred column s(0..NCD) (fixed i, j) into o[k][l], k <= Lc, l <= Ld;
+// transfer to d (swcd = false) or to c (swcd = true), as for the bra.
 template <class C>
 __device__ __forceinline__ void ket_hrr(const typename C::R (&s)[C::NCD + 1], typename C::R cd,
-                                        typename C::R (&o)[C::Lc + 1][C::Ld + 1]) {
+                                        bool swcd, typename C::R (&o)[C::Lc + 1][C::Ld + 1]) {
     using R = typename C::R;
-    R t[C::Ld + 1][C::NCD + 1];
+    if (!swcd) {
+        R t[C::Ld + 1][C::NCD + 1];
 #pragma unroll
-    for (int k = 0; k <= C::NCD; ++k) t[0][k] = s[k];
+        for (int k = 0; k <= C::NCD; ++k) t[0][k] = s[k];
 #pragma unroll
-    for (int l = 1; l <= C::Ld; ++l)
+        for (int l = 1; l <= C::Ld; ++l)
 #pragma unroll
-        for (int k = 0; k + l <= C::NCD; ++k) t[l][k] = fma(cd, t[l - 1][k], t[l - 1][k + 1]);
+            for (int k = 0; k + l <= C::NCD; ++k) t[l][k] = fma(cd, t[l - 1][k], t[l - 1][k + 1]);
 #pragma unroll
-    for (int k = 0; k <= C::Lc; ++k)
+        for (int k = 0; k <= C::Lc; ++k)
 #pragma unroll
-        for (int l = 0; l <= C::Ld; ++l) o[k][l] = t[l][k];
+            for (int l = 0; l <= C::Ld; ++l) o[k][l] = t[l][k];
+    } else {
+        R t[C::Lc + 1][C::NCD + 1];
+#pragma unroll
+        for (int k = 0; k <= C::NCD; ++k) t[0][k] = s[k];
+#pragma unroll
+        for (int c = 1; c <= C::Lc; ++c)
+#pragma unroll
+            for (int k = 0; k + c <= C::NCD; ++k) t[c][k] = fma(-cd, t[c - 1][k], t[c - 1][k + 1]);
+#pragma unroll
+        for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+            for (int l = 0; l <= C::Ld; ++l) o[k][l] = t[k][l];
+    }
 }
 
 // I layout per quartet: [xi][mu][i][k][j][l] (the (j,l) block is contiguous for phase D).
@@ -238,6 +276,7 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
     R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
     R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
     R ab = (R)geo[G_ABX + xi];
+    const bool swab = geo[G_SWAB] != 0.0;
     R prev[C::NAB + 1], cur[C::NAB + 1];
     // column k = 0: G(i+1, 0) = C00 G(i, 0) + i B10 G(i-1, 0)
     cur[0] = (xi == 2) ? b[S_WZ] : (R)1;
@@ -250,7 +289,7 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
 #pragma unroll
     for (int k = 0; k <= C::NCD; ++k) {
         R h[C::La + 1][C::Lb + 1];
-        bra_hrr<C>(cur, ab, h);
+        bra_hrr<C>(cur, ab, swab, h);
         if constexpr (C::FUSE_BC) {
 #pragma unroll
             for (int i = 0; i <= C::La; ++i)
@@ -283,6 +322,7 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
     }
     if constexpr (C::FUSE_BC) {
         R cd = (R)geo[G_CDX + xi];
+        const bool swcd = geo[G_SWCD] != 0.0;
 #pragma unroll
         for (int i = 0; i <= C::La; ++i)
 #pragma unroll
@@ -291,7 +331,7 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
 #pragma unroll
                 for (int k = 0; k <= C::NCD; ++k) s[k] = hk[i][j][k];
                 R o[C::Lc + 1][C::Ld + 1];
-                ket_hrr<C>(s, cd, o);
+                ket_hrr<C>(s, cd, swcd, o);
 #pragma unroll
                 for (int k = 0; k <= C::Lc; ++k)
 #pragma unroll
@@ -310,7 +350,7 @@ __device__ __forceinline__ void phase_ket(const double *geo, int mu, int xi, int
 #pragma unroll
     for (int k = 0; k <= C::NCD; ++k) s[k] = src[k];
     R o[C::Lc + 1][C::Ld + 1];
-    ket_hrr<C>(s, (R)geo[G_CDX + xi], o);
+    ket_hrr<C>(s, (R)geo[G_CDX + xi], geo[G_SWCD] != 0.0, o);
 #pragma unroll
     for (int k = 0; k <= C::Lc; ++k)
 #pragma unroll

@@ -23,6 +23,14 @@ constexpr double kBoysTmax = 50.0;
 constexpr int kBoysNgrid = 502;
 constexpr double kPi = 3.14159265358979323846;
 
+// 1/j for the Taylor terms of the Boys function (a product with a rounded reciprocal instead of
+// an FP64 division; the terms it scales are corrections below 5e-2 of the sum).
+__device__ __forceinline__ double inv_int(int j) {
+    constexpr double t[kBoysTaylor + 1] = {0.0, 1.0, 1.0 / 2, 1.0 / 3, 1.0 / 4, 1.0 / 5,
+                                          1.0 / 6, 1.0 / 7, 1.0 / 8, 1.0 / 9, 1.0 / 10};
+    return t[j];
+}
+
 // Device addresses of the generated tables (see eri_tables.cu).
 struct Tables {
     const double *rys_cheb;
@@ -74,7 +82,7 @@ __device__ __forceinline__ void boys_eval(int mmax, double T, const double *__re
         const double *g = grid + k * kBoysCols + mmax;
         double s = __ldg(g + kBoysTaylor - 1);
 #pragma unroll
-        for (int j = kBoysTaylor - 1; j >= 1; --j) s = fma(s, d / j, __ldg(g + j - 1));
+        for (int j = kBoysTaylor - 1; j >= 1; --j) s = fma(s, d * inv_int(j), __ldg(g + j - 1));
         F[mmax] = s;
         for (int m = mmax - 1; m >= 0; --m) F[m] = (2.0 * T * F[m + 1] + eT) / (2 * m + 1);
     } else {
@@ -98,8 +106,9 @@ __device__ __forceinline__ void boys_f01(double T, const double *__restrict__ gr
         double s1 = WANT1 ? __ldg(g + kBoysTaylor) : 0.0;
 #pragma unroll
         for (int j = kBoysTaylor - 1; j >= 1; --j) {
-            s0 = fma(s0, d / j, __ldg(g + j - 1));
-            if (WANT1) s1 = fma(s1, d / j, __ldg(g + j));
+            const double dj = d * inv_int(j);
+            s0 = fma(s0, dj, __ldg(g + j - 1));
+            if (WANT1) s1 = fma(s1, dj, __ldg(g + j));
         }
         F0 = s0;
         F1 = s1;

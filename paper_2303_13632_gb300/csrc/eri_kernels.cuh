@@ -49,12 +49,17 @@ __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
 
+// ids[k] of an int4 without dynamic register indexing.
+__device__ __forceinline__ int pick(const int4 &g, int k) {
+    return k == 0 ? g.x : (k == 1 ? g.y : (k == 2 ? g.z : g.w));
+}
+
 // Per-quartet geometry kept in shared memory (FP64).
 // G_SWAB / G_SWCD = 1 when the VRR is built on B (D) and the HRR transfers to a (c); see
 // phase_geometry.
 enum GeoSlot {
     G_T = 0, G_PREF, G_P, G_Q, G_PAX, G_PAY, G_PAZ, G_QCX, G_QCY, G_QCZ, G_PQX, G_PQY, G_PQZ,
-    G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD, G_N
+    G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD, G_IP, G_IQ, G_IPQ, G_N
 };
 // Per (quartet, root) setup values kept in shared memory (type R).
 enum BCSlot { S_B00 = 0, S_B10, S_B01, S_C0X, S_C0Y, S_C0Z, S_C1X, S_C1Y, S_C1Z, S_WZ, S_N };
@@ -98,6 +103,9 @@ struct Cfg {
     static constexpr int OFF_H = OFF_U;
     static constexpr int OFF_I = OFF_U + Q * H_BYTES;
     static constexpr int SMEM = OFF_U + ((Q * UNION_BYTES + 16 + 15) / 16) * 16 + 16;
+    // thread-per-quartet variant (all intermediates in registers) for the small classes
+    static constexpr bool TPQ = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
+    static constexpr int TPQ_THREADS = 128;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -110,7 +118,8 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     if (prim >= nprim_total) {
         geo[G_PREF] = 0.0;
         geo[G_T] = 0.0;
-        for (int s = G_P; s < G_N; ++s) geo[s] = (s == G_P || s == G_Q) ? 1.0 : 0.0;
+        for (int s = G_P; s < G_N; ++s)
+            geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0 : (s == G_IPQ ? 0.5 : 0.0);
         return;
     }
     int id = prim % nd, t = prim / nd;
@@ -125,7 +134,9 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     double Cc[3] = {sh.cx[qt.z], sh.cy[qt.z], sh.cz[qt.z]};
     double D[3] = {sh.cx[qt.w], sh.cy[qt.w], sh.cz[qt.w]};
     double p = ea + eb, q = ec + ed;
-    double ip = 1.0 / p, iq = 1.0 / q;
+    // 1/p and 1/q from one FP64 division
+    double ipq_prod = 1.0 / (p * q);
+    double ip = q * ipq_prod, iq = p * ipq_prod;
     double ab2 = 0.0, cd2 = 0.0, pq2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -143,7 +154,8 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
         cd2 += CD * CD;
         pq2 += PQ * PQ;
     }
-    double rho = p * q / (p + q);
+    double ipq = 1.0 / (p + q);
+    double rho = p * q * ipq;
     // K_AB K_CD = exp(-(ab/p |A-B|^2 + cd/q |C-D|^2)) in one FP64 exponential
     double kabcd = exp(-(ea * eb * ip * ab2 + ec * ed * iq * cd2));
     // 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD times the four coef * N factors
@@ -155,6 +167,9 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     geo[G_Q] = q;
     geo[G_SWAB] = eb > ea ? 1.0 : 0.0;
     geo[G_SWCD] = ed > ec ? 1.0 : 0.0;
+    geo[G_IP] = ip;
+    geo[G_IQ] = iq;
+    geo[G_IPQ] = ipq;
 }
 
 // Phase A1: root mu of quartet geometry geo -> B and C values (Rys setup stage), formed in
@@ -177,11 +192,11 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
     bc[S_WZ] = (R)(geo[G_PREF] * w);
     if constexpr (LTOT > 0) {
         double p = geo[G_P], q = geo[G_Q];
-        double ipq = 1.0 / (p + q);
+        double ipq = geo[G_IPQ];
         double fq = q * x * ipq, fp = p * x * ipq;
         bc[S_B00] = (R)(0.5 * x * ipq);
-        bc[S_B10] = (R)((1.0 - fq) * (0.5 / p));
-        bc[S_B01] = (R)((1.0 - fp) * (0.5 / q));
+        bc[S_B10] = (R)((1.0 - fq) * (0.5 * geo[G_IP]));
+        bc[S_B01] = (R)((1.0 - fp) * (0.5 * geo[G_IQ]));
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             double pq = geo[G_PQX + s];
@@ -340,6 +355,65 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
     }
 }
 
+// VRR + bra HRR + ket HRR of one (root, axis) entirely in registers: I[(i, k, j, l)] in the
+// layout of i_index for fixed (xi, mu).  Used by the thread-per-quartet kernel.
+template <class C>
+__device__ __forceinline__ void axis_2d(const typename C::R *b, const double *geo, int xi,
+                                        typename C::R (&I)[C::IBLK]) {
+    using R = typename C::R;
+    R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
+    R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
+    R ab = (R)geo[G_ABX + xi], cd = (R)geo[G_CDX + xi];
+    const bool swab = geo[G_SWAB] != 0.0, swcd = geo[G_SWCD] != 0.0;
+    R prev[C::NAB + 1], cur[C::NAB + 1];
+    cur[0] = (xi == 2) ? b[S_WZ] : (R)1;
+#pragma unroll
+    for (int i = 0; i < C::NAB; ++i)
+        cur[i + 1] = c00 * cur[i] + (i > 0 ? (R)i * b10 * cur[i - 1] : (R)0);
+#pragma unroll
+    for (int i = 0; i <= C::NAB; ++i) prev[i] = (R)0;
+    R hk[C::La + 1][C::Lb + 1][C::NCD + 1];
+#pragma unroll
+    for (int k = 0; k <= C::NCD; ++k) {
+        R h[C::La + 1][C::Lb + 1];
+        bra_hrr<C>(cur, ab, swab, h);
+#pragma unroll
+        for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+            for (int j = 0; j <= C::Lb; ++j) hk[i][j][k] = h[i][j];
+        if (k < C::NCD) {
+            R nxt[C::NAB + 1];
+#pragma unroll
+            for (int i = 0; i <= C::NAB; ++i) {
+                R v = c01 * cur[i];
+                if (k > 0) v = fma((R)k * b01, prev[i], v);
+                if (i > 0) v = fma((R)i * b00, cur[i - 1], v);
+                nxt[i] = v;
+            }
+#pragma unroll
+            for (int i = 0; i <= C::NAB; ++i) {
+                prev[i] = cur[i];
+                cur[i] = nxt[i];
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+        for (int j = 0; j <= C::Lb; ++j) {
+            R sv[C::NCD + 1];
+#pragma unroll
+            for (int k = 0; k <= C::NCD; ++k) sv[k] = hk[i][j][k];
+            R o[C::Lc + 1][C::Ld + 1];
+            ket_hrr<C>(sv, cd, swcd, o);
+#pragma unroll
+            for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+                for (int l = 0; l <= C::Ld; ++l)
+                    I[((i * (C::Lc + 1) + k) * (C::Lb + 1) + j) * (C::Ld + 1) + l] = o[k][l];
+        }
+}
+
 // Phase C: ket HRR for one (mu, xi, i, j).
 template <class C>
 __device__ __forceinline__ void phase_ket(const double *geo, int mu, int xi, int i, int j,
@@ -495,14 +569,15 @@ eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
             double *geo = geo_s + q * G_N;
             if (q < qn) {
                 int4 g = args.quartets[q0 + q];
-                int ids[4] = {g.x, g.y, g.z, g.w};
-                int4 qt = make_int4(ids[args.perm[0]], ids[args.perm[1]], ids[args.perm[2]],
-                                    ids[args.perm[3]]);
+                int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]),
+                                    pick(g, args.perm[2]), pick(g, args.perm[3]));
                 phase_geometry<C>(sh, qt, prim, geo, np);
             } else {
                 geo[G_PREF] = 0.0;
                 geo[G_T] = 0.0;
-                for (int s = G_P; s < G_N; ++s) geo[s] = (s == G_P || s == G_Q) ? 1.0 : 0.0;
+                for (int s = G_P; s < G_N; ++s)
+                    geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0
+                                                                              : (s == G_IPQ ? 0.5 : 0.0);
             }
             if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
         }
@@ -648,12 +723,159 @@ eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Thread-per-quartet kernel for the small classes: each thread runs every stage of one
+// quartet in registers (no shared-memory phases, no barriers before the store), so the FP64
+// setup of all threads overlaps.  Shared memory is used only to pack the compressed tile.
+template <class C>
+__global__ void __launch_bounds__(C::TPQ_THREADS)
+eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+    using R = typename C::R;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int tid = threadIdx.x;
+    const long long q0 = (long long)blockIdx.x * C::TPQ_THREADS;
+    const int qn = (int)((args.nq - q0) < C::TPQ_THREADS ? (args.nq - q0) : C::TPQ_THREADS);
+    const bool live = tid < qn;
+    R acc[C::NERI];
+#pragma unroll
+    for (int o = 0; o < C::NERI; ++o) acc[o] = (R)0;
+    if (live) {
+        int4 g = args.quartets[q0 + tid];
+        int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
+                            pick(g, args.perm[3]));
+        int nprim = 1;
+        for (int prim = 0; prim < nprim; ++prim) {
+            double geo[G_N];
+            phase_geometry<C>(sh, qt, prim, geo, nprim);
+#pragma unroll 1
+            for (int mu = 0; mu < C::NRYS; ++mu) {
+                R bc[S_N];
+                phase_setup<C>(tb, geo, mu, bc);
+                R X[C::IBLK], Y[C::IBLK], Z[C::IBLK];
+                axis_2d<C>(bc, geo, 0, X);
+                axis_2d<C>(bc, geo, 1, Y);
+                axis_2d<C>(bc, geo, 2, Z);
+#pragma unroll
+                for (int a = 0; a < C::NA; ++a)
+#pragma unroll
+                    for (int b = 0; b < C::NB; ++b)
+#pragma unroll
+                        for (int c = 0; c < C::NC; ++c)
+#pragma unroll
+                            for (int d = 0; d < C::ND; ++d) {
+                                constexpr int LB1 = C::Lb + 1, LC1 = C::Lc + 1, LD1 = C::Ld + 1;
+                                const int ix = ((cart_x(C::La, a) * LC1 + cart_x(C::Lc, c)) * LB1 + cart_x(C::Lb, b)) * LD1 + cart_x(C::Ld, d);
+                                const int iy = ((cart_y(C::La, a) * LC1 + cart_y(C::Lc, c)) * LB1 + cart_y(C::Lb, b)) * LD1 + cart_y(C::Ld, d);
+                                const int iz = ((cart_z(C::La, a) * LC1 + cart_z(C::Lc, c)) * LB1 + cart_z(C::Lb, b)) * LD1 + cart_z(C::Ld, d);
+                                const int o = ((a * C::NB + b) * C::NC + c) * C::ND + d;
+                                acc[o] = fma(X[ix] * Y[iy], Z[iz], acc[o]);
+                            }
+            }
+        }
+    }
+    const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
+              st3 = args.ostride[3];
+    if (args.out_fp64 != nullptr) {
+        if (live) {
+            double *out = args.out_fp64 + (q0 + tid) * (long long)C::NERI;
+            bool bad = false;
+#pragma unroll
+            for (int a = 0; a < C::NA; ++a)
+#pragma unroll
+                for (int b = 0; b < C::NB; ++b)
+#pragma unroll
+                    for (int c = 0; c < C::NC; ++c)
+#pragma unroll
+                        for (int d = 0; d < C::ND; ++d) {
+                            double v = (double)acc[((a * C::NB + b) * C::NC + c) * C::ND + d];
+                            bad |= !(fabs(v) <= 1.7976931348623157e308);
+                            out[a * st0 + b * st1 + c * st2 + d * st3] = v;
+                        }
+            if (bad) atomicOr(args.err, 1);
+        }
+        return;
+    }
+    // ---- compressed output (Sec. II-D) ----
+    const int bits = args.bits;
+    const long long bit0 = q0 * (long long)C::NERI * bits;
+    const long long bit1 = (q0 + qn) * (long long)C::NERI * bits;
+    const long long w0 = bit0 >> 5;
+    const long long w1 = (bit1 + 31) >> 5;
+    const int nw = (int)(w1 - w0);
+    uint32_t *stage = reinterpret_cast<uint32_t *>(smem);
+    for (int w = tid; w < nw; w += C::TPQ_THREADS) stage[w] = 0u;
+    __syncthreads();
+    if (live) {
+        R m = (R)0;
+        bool bad = false;
+#pragma unroll
+        for (int o = 0; o < C::NERI; ++o) {
+            R v = acc[o] < (R)0 ? -acc[o] : acc[o];
+            bad |= !(v <= (R)3.0e38);
+            m = v > m ? v : m;
+        }
+        if (bad) atomicOr(args.err, 1);
+        const double M = (double)((1u << (bits - 1)) - 1u);
+        float eps = (float)((double)m / M);
+        args.scales[q0 + tid] = eps;
+        R inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
+        const uint32_t mask = (1u << bits) - 1u;
+        const R Mr = (R)M;
+        const long long qbase = (q0 + tid) * (long long)C::NERI;
+#pragma unroll
+        for (int a = 0; a < C::NA; ++a)
+#pragma unroll
+            for (int b = 0; b < C::NB; ++b)
+#pragma unroll
+                for (int c = 0; c < C::NC; ++c)
+#pragma unroll
+                    for (int d = 0; d < C::ND; ++d) {
+                        R v = RTraits<R>::round_away(acc[((a * C::NB + b) * C::NC + c) * C::ND + d] * inv);
+                        v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
+                        uint32_t code = (uint32_t)(int)v & mask;
+                        long long sb = (qbase + a * st0 + b * st1 + c * st2 + d * st3) * bits - (w0 << 5);
+                        int wi = (int)(sb >> 5), off = (int)(sb & 31);
+                        atomicOr(stage + wi, code << off);
+                        if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                    }
+    }
+    __syncthreads();
+    const bool last_tile = (q0 + qn) >= args.nq;
+    const int head_bits = (int)(bit0 & 31);
+    const int tail_bits = (int)(bit1 & 31);
+    for (int w = tid; w < nw; w += C::TPQ_THREADS) {
+        uint32_t v = stage[w];
+        long long gw = w0 + w;
+        uint32_t keep = 0xffffffffu;
+        if (w == 0 && head_bits) keep &= ~((1u << head_bits) - 1u);
+        if (w == nw - 1 && tail_bits && !last_tile) keep &= (1u << tail_bits) - 1u;
+        if (keep == 0xffffffffu) {
+            args.packed[gw] = v;
+        } else {
+            atomicAnd(args.packed + gw, ~keep);
+            atomicOr(args.packed + gw, v & keep);
+        }
+    }
+    if (last_tile) {
+        for (long long w = w1 + tid; w < args.seg_words; w += C::TPQ_THREADS) args.packed[w] = 0u;
+    }
+}
+
 // Host-side launch helper for one canonical class.
 template <int La, int Lb, int Lc, int Ld, typename R, bool KAHAN>
 cudaError_t launch_class(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
                          cudaStream_t stream) {
     using C = Cfg<La, Lb, Lc, Ld, R>;
     if (args.nq <= 0) return cudaSuccess;
+    if constexpr (C::TPQ && !KAHAN) {
+        long long grid = (args.nq + C::TPQ_THREADS - 1) / C::TPQ_THREADS;
+        if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+        size_t smem = 0;
+        if (args.out_fp64 == nullptr)
+            smem = ((size_t)C::TPQ_THREADS * C::NERI * args.bits + 31) / 32 * 4 + 16;
+        eri_tpq_kernel<C><<<(unsigned)grid, C::TPQ_THREADS, smem, stream>>>(sh, tb, args);
+        return cudaGetLastError();
+    }
     auto kern = eri_class_kernel<C, KAHAN>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;

@@ -161,6 +161,21 @@ eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packe
 eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
                                           void *d_packed, float *d_scales, void *stream);
 
+/* Adjoint (gradients) of E = sum_q sum_abcd G_q,abcd (ab|cd)_q for an upstream d_G laid out
+ * like eri_compute's output (class-sorted, row major per quartet, eri_output_bytes(plan, 0)):
+ *   d_dR[3*s + xi]   = dE / d(center[xi] of shell s)          (n_shells x 3, bohr^-1 Ha)
+ *   d_dalpha[p]      = dE / d(exponent of primitive p)         (primitives in the order of the
+ *                                                               shells' exps arrays)
+ * using d g_a/dA_xi = 2 alpha g_{a+1_xi} - a_xi g_{a-1_xi} and d g_a/d alpha =
+ * (2L+3)/(4 alpha) g_a - sum_xi g_{a+2_xi} (same coefficient and normalisation N(alpha, L));
+ * the Rys recurrences (Eqs. 6-7) are recomputed on index ranges extended by two and
+ * contracted with d_G (Eq. 8 with G weights).  FP64 throughout.  Both outputs are zeroed and
+ * then accumulated on `stream` (device atomics: summation order, hence the last bits, can
+ * vary between runs).  Supports shells with L <= 2; a plan containing an f shell returns
+ * ERI_E_UNSUPPORTED before any device work. */
+eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
+                          void *stream);
+
 /* Waits for the plan's work on `stream` and returns the first latched device error
  * (ERI_E_NUMERIC, ERI_E_TIMEOUT) or a CUDA error; clears the latch. */
 eri_status_t eri_sync(eri_plan_t plan, void *stream);

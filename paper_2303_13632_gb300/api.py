@@ -155,6 +155,13 @@ def eri_compute_compressed_class(plan: Plan, cls: int, bits: int, packed, scales
           "eri_compute_compressed_class")
 
 
+def eri_backward(plan: Plan, G, dR, dalpha, stream=None) -> None:
+    """dR [n_shells, 3] and dalpha [n_prims] (float64 CUDA tensors) receive the gradient of
+    E = sum G * ERIs for G laid out like eri_compute's output."""
+    check(_lib.load().eri_backward(plan.handle, _dev_ptr(G), _dev_ptr(dR), _dev_ptr(dalpha),
+                                   _stream_handle(stream)), "eri_backward")
+
+
 def eri_sync(plan: Plan, stream=None) -> None:
     check(_lib.load().eri_sync(plan.handle, _stream_handle(stream)), "eri_sync")
 

@@ -1,0 +1,244 @@
+// eri_backward.cuh -- adjoint of the ERI kernel: gradients of E = sum_q sum_abcd G_abcd (ab|cd)
+// with respect to the shell centres and the primitive exponents, recomputing the recurrences.
+//
+// For a primitive g_a = c N(alpha, L) prod_xi (r_xi - A_xi)^{a_xi} exp(-alpha |r - A|^2):
+//   d g_a / d A_xi  = 2 alpha g_{a + 1_xi} - a_xi g_{a - 1_xi}
+//   d g_a / d alpha = (2L + 3) / (4 alpha) g_a - sum_xi g_{a + 2_xi}
+// (shifted functions keep the coefficient and normalisation of g_a).  In the Rys form of
+// Eq. 8 each shift touches one axis factor only, so with the 2-D integrals I(i,j,k,l,mu,xi)
+// built for every index up to L + 2 (VRR Eq. 6 and HRR Eq. 7 on the extended ranges, n_Rys =
+// floor((L+2)/2) + 1 roots, exact for the shifted integrals of total degree <= L + 2):
+//   dE/dA_x = sum_mu sum_abcd G_abcd [2 alpha Ix(a+1) - a_x Ix(a-1)] Iy Iz, likewise y, z, B, C, D
+//   dE/d alpha_a = sum_mu sum_abcd G_abcd [(2La+3)/(4 alpha) Ix Iy Iz - Ix(a+2) Iy Iz - ...].
+// Centre gradients are summed over primitives; exponent gradients go to the primitive.
+#pragma once
+
+#include "eri_kernels.cuh"
+
+namespace eri {
+
+// 2-D integral configuration on the extended index ranges (all L + 2) of class (La..Ld).
+template <int La0, int Lb0, int Lc0, int Ld0>
+struct GCfg {
+    using R = double;
+    static constexpr int oLa = La0, oLb = Lb0, oLc = Lc0, oLd = Ld0;
+    static constexpr int oNA = ncart(La0), oNB = ncart(Lb0), oNC = ncart(Lc0), oND = ncart(Ld0);
+    static constexpr int oNERI = oNA * oNB * oNC * oND;
+    static constexpr int La = La0 + 2, Lb = Lb0 + 2, Lc = Lc0 + 2, Ld = Ld0 + 2;
+    static constexpr int NAB = La + Lb, NCD = Lc + Ld;
+    static constexpr int NRYS = (La0 + Lb0 + Lc0 + Ld0 + 2) / 2 + 1;
+    static constexpr bool FUSE_BC = false;
+    static constexpr int JL = (Lb + 1) * (Ld + 1);
+    static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;
+    static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);
+    static constexpr int GEO_BYTES = G_N * 8;
+    static constexpr int BC_BYTES = NRYS * S_N * 8;
+    static constexpr int H_BYTES = 3 * NRYS * HBLK * 8;
+    static constexpr int I_BYTES = 3 * NRYS * IBLK * 8;
+    static constexpr int NACC = 17;  // dR[4][3], dalpha-part[4], E
+    static constexpr int PERQ = GEO_BYTES + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 + 64;
+    static constexpr int Q = imax(1, imin(8, (100 * 1024) / PERQ));
+    static constexpr int THREADS = 256;
+    static constexpr int OFF_GEO = 0;
+    static constexpr int OFF_BC = Q * GEO_BYTES;
+    static constexpr int OFF_ACC = OFF_BC + Q * BC_BYTES;
+    static constexpr int OFF_DR = OFF_ACC + Q * NACC * 8;        // centre gradients, all primitives
+    static constexpr int OFF_PRIM = OFF_DR + Q * 12 * 8;          // primitive ids + exponents
+    static constexpr int OFF_H = ((OFF_PRIM + Q * 8 * 8 + 15) / 16) * 16;
+    static constexpr int OFF_I = OFF_H + Q * H_BYTES;
+    static constexpr int SMEM = OFF_I + Q * I_BYTES + 16;
+};
+
+template <class C>
+__device__ __forceinline__ double gI(const double *Iq, int xi, int mu, int i, int j, int k, int l) {
+    return Iq[i_index<C>(xi, mu, i, k, j, l)];
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::THREADS)
+eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__restrict__ G,
+                    double *__restrict__ dR, double *__restrict__ dalpha) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
+    double *bc_s = reinterpret_cast<double *>(smem + C::OFF_BC);
+    double *acc_s = reinterpret_cast<double *>(smem + C::OFF_ACC);
+    double *dr_s = reinterpret_cast<double *>(smem + C::OFF_DR);
+    double *prim_s = reinterpret_cast<double *>(smem + C::OFF_PRIM);  // [q][0..3] exps, [4..7] prim ids
+    double *H_s = reinterpret_cast<double *>(smem + C::OFF_H);
+    double *I_s = reinterpret_cast<double *>(smem + C::OFF_I);
+    __shared__ int maxprim_s;
+    __shared__ int4 qt_s[C::Q];
+
+    const int tid = threadIdx.x;
+    const long long q0 = (long long)blockIdx.x * C::Q;
+    const int qn = (int)((args.nq - q0) < C::Q ? (args.nq - q0) : C::Q);
+    if (tid == 0) maxprim_s = 1;
+    for (int i = tid; i < C::Q * 12; i += C::THREADS) dr_s[i] = 0.0;
+    for (int q = tid; q < C::Q; q += C::THREADS) {
+        int4 g = q < qn ? args.quartets[q0 + q] : make_int4(0, 0, 0, 0);
+        qt_s[q] = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
+                            pick(g, args.perm[3]));
+    }
+    __syncthreads();
+    const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
+              st3 = args.ostride[3];
+
+    for (int prim = 0; prim < maxprim_s; ++prim) {
+        for (int i = tid; i < C::Q * C::NACC; i += C::THREADS) acc_s[i] = 0.0;
+        for (int q = tid; q < C::Q; q += C::THREADS) {
+            double *geo = geo_s + q * G_N;
+            int np = 0;
+            if (q < qn) {
+                int4 qt = qt_s[q];
+                phase_geometry<C>(sh, qt, prim, geo, np);
+                if (prim < np) {
+                    int nb = sh.nprim[qt.y], nc = sh.nprim[qt.z], nd = sh.nprim[qt.w];
+                    int id = prim % nd, t = prim / nd;
+                    int ic = t % nc;
+                    t /= nc;
+                    int ib = t % nb, ia = t / nb;
+                    int pk[4] = {sh.pofs[qt.x] + ia, sh.pofs[qt.y] + ib, sh.pofs[qt.z] + ic,
+                                 sh.pofs[qt.w] + id};
+                    for (int k = 0; k < 4; ++k) {
+                        prim_s[q * 8 + k] = sh.exps[pk[k]];
+                        prim_s[q * 8 + 4 + k] = (double)pk[k];
+                    }
+                }
+            } else {
+                geo[G_PREF] = 0.0;
+                geo[G_T] = 0.0;
+                for (int s = G_P; s < G_N; ++s)
+                    geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0
+                                                                              : (s == G_IPQ ? 0.5 : 0.0);
+            }
+            if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+            if (q >= qn || prim >= np) {
+                for (int k = 0; k < 4; ++k) {
+                    prim_s[q * 8 + k] = 1.0;
+                    prim_s[q * 8 + 4 + k] = -1.0;
+                }
+            }
+        }
+        __syncthreads();
+        for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
+            int q = it / C::NRYS, mu = it % C::NRYS;
+            phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
+        }
+        __syncthreads();
+        for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
+            int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
+            phase_vrr<C>(bc_s + q * C::NRYS * S_N, geo_s + q * G_N, r / 3, r % 3,
+                         H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
+        }
+        __syncthreads();
+        {
+            constexpr int NIJ = (C::La + 1) * (C::Lb + 1);
+            for (int it = tid; it < C::Q * C::NRYS * 3 * NIJ; it += C::THREADS) {
+                int q = it / (C::NRYS * 3 * NIJ), r = it % (C::NRYS * 3 * NIJ);
+                int mu = r / (3 * NIJ);
+                r %= 3 * NIJ;
+                int xi = r / NIJ, ij = r % NIJ;
+                phase_ket<C>(geo_s + q * G_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
+                             H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
+            }
+        }
+        __syncthreads();
+        // contraction with G: threads over the outputs of one quartet at a time, accumulators
+        // in registers, then a warp-shuffle reduction and one shared atomic per warp
+        for (int q = 0; q < qn; ++q) {
+            const double *ex = prim_s + q * 8;
+            const double *Iq = I_s + (size_t)q * (C::I_BYTES / 8);
+            double r[C::NACC];
+#pragma unroll
+            for (int k = 0; k < C::NACC; ++k) r[k] = 0.0;
+            for (int o = tid; o < C::oNERI; o += C::THREADS) {
+                int d = o % C::oND, t = o / C::oND;
+                int c = t % C::oNC;
+                t /= C::oNC;
+                int b = t % C::oNB, a = t / C::oNB;
+                const double g =
+                    G[(q0 + q) * (long long)C::oNERI + a * st0 + b * st1 + c * st2 + d * st3];
+                int cp[4][3];
+#pragma unroll
+                for (int x = 0; x < 3; ++x) {
+                    cp[0][x] = c_cart[C::oLa][a][x];
+                    cp[1][x] = c_cart[C::oLb][b][x];
+                    cp[2][x] = c_cart[C::oLc][c][x];
+                    cp[3][x] = c_cart[C::oLd][d][x];
+                }
+#pragma unroll 1
+                for (int mu = 0; mu < C::NRYS; ++mu) {
+                    double I0[3], P[3];
+#pragma unroll
+                    for (int x = 0; x < 3; ++x)
+                        I0[x] = gI<C>(Iq, x, mu, cp[0][x], cp[1][x], cp[2][x], cp[3][x]);
+                    P[0] = g * I0[1] * I0[2];
+                    P[1] = g * I0[0] * I0[2];
+                    P[2] = g * I0[0] * I0[1];
+                    r[16] += P[0] * I0[0];
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+                        for (int x = 0; x < 3; ++x) {
+                            const int i0 = cp[0][x] + (k == 0), j0 = cp[1][x] + (k == 1),
+                                      k0 = cp[2][x] + (k == 2), l0 = cp[3][x] + (k == 3);
+                            double up = gI<C>(Iq, x, mu, i0, j0, k0, l0);
+                            double up2 = gI<C>(Iq, x, mu, i0 + (k == 0), j0 + (k == 1),
+                                               k0 + (k == 2), l0 + (k == 3));
+                            double dn = 0.0;
+                            if (cp[k][x] > 0)
+                                dn = gI<C>(Iq, x, mu, i0 - 2 * (k == 0), j0 - 2 * (k == 1),
+                                           k0 - 2 * (k == 2), l0 - 2 * (k == 3));
+                            r[k * 3 + x] += P[x] * (2.0 * ex[k] * up - cp[k][x] * dn);
+                            r[12 + k] -= P[x] * up2;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int k = 0; k < C::NACC; ++k) {
+                double v = r[k];
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+                if ((tid & 31) == 0 && v != 0.0) atomicAdd(acc_s + q * C::NACC + k, v);
+            }
+        }
+        __syncthreads();
+        // per quartet: exponent gradients of this primitive quartet, centre gradients summed
+        for (int q = tid; q < qn; q += C::THREADS) {
+            const double *acc = acc_s + q * C::NACC;
+            const double *ex = prim_s + q * 8;
+            const int Lk[4] = {C::oLa, C::oLb, C::oLc, C::oLd};
+            if (ex[4] >= 0.0) {
+                for (int k = 0; k < 4; ++k) {
+                    double v = (2.0 * Lk[k] + 3.0) / (4.0 * ex[k]) * acc[16] + acc[12 + k];
+                    atomicAdd(dalpha + (long long)ex[4 + k], v);
+                }
+                for (int i = 0; i < 12; ++i) dr_s[q * 12 + i] += acc[i];
+            }
+        }
+        __syncthreads();
+    }
+    for (int it = tid; it < qn * 12; it += C::THREADS) {
+        int q = it / 12, i = it % 12, k = i / 3, x = i % 3;
+        int4 qt = qt_s[q];
+        int s = pick(qt, k);
+        atomicAdd(dR + 3LL * s + x, dr_s[q * 12 + i]);
+    }
+}
+
+template <int La, int Lb, int Lc, int Ld>
+cudaError_t launch_backward(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
+                            const double *G, double *dR, double *dalpha, cudaStream_t stream) {
+    using C = GCfg<La, Lb, Lc, Ld>;
+    if (args.nq <= 0) return cudaSuccess;
+    auto kern = eri_backward_kernel<C>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long long grid = (args.nq + C::Q - 1) / C::Q;
+    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
+    kern<<<(unsigned)grid, C::THREADS, C::SMEM, stream>>>(sh, tb, args, G, dR, dalpha);
+    return cudaGetLastError();
+}
+
+}  // namespace eri

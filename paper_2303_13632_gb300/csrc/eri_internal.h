@@ -17,6 +17,11 @@ using LaunchFn = cudaError_t (*)(const ShellsDev &sh, const Tables &tb, const Cl
 // Variants: 0 = FP64, 1 = mixed, 2 = mixed with Kahan-compensated primitive sums.
 constexpr int kNumVariants = 3;
 
+// Launcher of one canonical class's adjoint kernel (FP64).
+using BackwardFn = cudaError_t (*)(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
+                                   const double *G, double *dR, double *dalpha, cudaStream_t stream);
+void eri_register_backward(BackwardFn *table);
+
 // Each class translation unit fills table[cls * kNumVariants + variant] for its classes.
 constexpr int kNumTU = 16;
 #define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table);

@@ -17,9 +17,11 @@ namespace eri {
 namespace {
 
 LaunchFn g_launch[256 * kNumVariants];
+BackwardFn g_backward[256];
 std::once_flag g_launch_once;
 
 void register_all() {
+    eri_register_backward(g_backward);
     eri_register_tu_0(g_launch); eri_register_tu_1(g_launch); eri_register_tu_2(g_launch);
     eri_register_tu_3(g_launch); eri_register_tu_4(g_launch); eri_register_tu_5(g_launch);
     eri_register_tu_6(g_launch); eri_register_tu_7(g_launch); eri_register_tu_8(g_launch);
@@ -500,6 +502,39 @@ eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packe
         eri_status_t s = launch_one(plan, c, nullptr, bits, d_packed, d_scales, off, (cudaStream_t)stream);
         if (s != ERI_OK) return s;
         off += packed_segment_bytes(plan->count[c], neri, bits);
+    }
+    return ERI_OK;
+}
+
+eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
+                          void *stream) {
+    if (!plan || (plan->nq > 0 && !d_G) || (!d_dR && plan->n_shells > 0) ||
+        (!d_dalpha && plan->n_prims > 0))
+        return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_G) % 8 || reinterpret_cast<uintptr_t>(d_dR) % 8 ||
+        reinterpret_cast<uintptr_t>(d_dalpha) % 8)
+        return ERI_E_INVALID;
+    for (int c = 0; c < 256; ++c)
+        if (plan->count[c] > 0 && !g_backward[canonicalise(c).cls]) return ERI_E_UNSUPPORTED;
+    cudaSetDevice(plan->device);
+    cudaStream_t st = (cudaStream_t)stream;
+    cudaError_t e = cudaMemsetAsync(d_dR, 0, sizeof(double) * 3 * (size_t)plan->n_shells, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_dalpha, 0, sizeof(double) * (size_t)plan->n_prims, st);
+    if (e != cudaSuccess) return cuda_status(e);
+    ShellsDev sh{plan->d_cx, plan->d_cy, plan->d_cz, plan->d_pofs, plan->d_nprim, plan->d_exps, plan->d_cn};
+    for (int c = 0; c < 256; ++c) {
+        if (plan->count[c] == 0) continue;
+        Canon cn = canonicalise(c);
+        ClassArgs a{};
+        for (int k = 0; k < 4; ++k) {
+            a.perm[k] = cn.perm[k];
+            a.ostride[k] = cn.ostride[k];
+        }
+        a.quartets = plan->d_quartets + plan->first[c];
+        a.nq = plan->count[c];
+        a.err = plan->d_err;
+        e = g_backward[cn.cls](sh, plan->tables, a, d_G + plan->fp64_off[c], d_dR, d_dalpha, st);
+        if (e != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
 }

@@ -30,11 +30,13 @@ struct GCfg {
     static constexpr bool FUSE_BC = false;
     static constexpr int JL = (Lb + 1) * (Ld + 1);
     static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;
+    static constexpr int JLP = (JL % 2) ? JL : JL + 1;
+    static constexpr int IBLKP = (La + 1) * (Lc + 1) * JLP;
     static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);
     static constexpr int GEO_BYTES = G_N * 8;
     static constexpr int BC_BYTES = NRYS * S_N * 8;
     static constexpr int H_BYTES = 3 * NRYS * HBLK * 8;
-    static constexpr int I_BYTES = 3 * NRYS * IBLK * 8;
+    static constexpr int I_BYTES = 3 * NRYS * IBLKP * 8;
     static constexpr int NACC = 17;  // dR[4][3], dalpha-part[4], E
     static constexpr int PERQ = GEO_BYTES + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 + 64;
     static constexpr int Q = imax(1, imin(8, (100 * 1024) / PERQ));

@@ -16,7 +16,7 @@ namespace eri {
 
 template <int IDX>
 struct Register {
-    static void apply(LaunchFn *table) {
+    static void apply(LaunchFn *table, bool *tpq) {
         if constexpr (IDX < kNumCanonical) {
             if constexpr (IDX % kNumTU == ERI_TU) {
                 constexpr int cls = canonical_class(IDX);
@@ -25,12 +25,16 @@ struct Register {
                 table[cls * kNumVariants + 0] = &launch_class<La, Lb, Lc, Ld, double, false>;
                 table[cls * kNumVariants + 1] = &launch_class<La, Lb, Lc, Ld, float, false>;
                 table[cls * kNumVariants + 2] = &launch_class<La, Lb, Lc, Ld, float, true>;
+                tpq[cls * kNumVariants + 0] = Cfg<La, Lb, Lc, Ld, double>::TPQ;
+                tpq[cls * kNumVariants + 1] = Cfg<La, Lb, Lc, Ld, float>::TPQ;
+                tpq[cls * kNumVariants + 2] = false;
+                static_assert(Cfg<La, Lb, Lc, Ld, double>::SETUP_FIELDS <= kSetupFieldsMax, "setup");
             }
-            Register<IDX + 1>::apply(table);
+            Register<IDX + 1>::apply(table, tpq);
         }
     }
 };
 
-void ERI_REGISTER_NAME(LaunchFn *table) { Register<0>::apply(table); }
+void ERI_REGISTER_NAME(LaunchFn *table, bool *tpq) { Register<0>::apply(table, tpq); }
 
 }  // namespace eri

@@ -66,6 +66,17 @@ struct ClassArgs {
     float *scales;         // eps of the class's first quartet
     int bits;              // 2..24 in compressed mode
     int *err;              // device error latch (bit 0: non-finite result)
+    const void *setup;     // per-quartet setup values from the setup kernel, or null
+    long long setup_stride;  // elements between two fields of the setup buffer
+};
+
+// Launch options of a class kernel (see launch_class).
+struct LaunchOpts {
+    int force_phase = 0;
+    unsigned long long *counter = nullptr;
+    int grid = 0;
+    int device = 0;
+    void *scratch = nullptr;  // setup buffer for the split setup/recurrence path (K = 1)
 };
 
 // Boys function F_m(T), m = 0..mmax (mmax <= kBoysMmax).  For T < 50: Taylor series of

@@ -11,9 +11,14 @@ namespace eri {
 // Device addresses of the constant tables on the current device (uploaded on first use).
 cudaError_t tables_for_current_device(Tables *out);
 
+// Quartets per launch of the split setup/recurrence path (a multiple of 32 so that every chunk
+// starts on a 32-bit word of the packed stream) and the widest setup record (n_Rys = 7).
+constexpr long long kSetupChunk = 1LL << 20;
+constexpr int kSetupFieldsMax = 8 + 7 * 10;
+
 // Launcher of one canonical class kernel in one arithmetic variant.
 using LaunchFn = cudaError_t (*)(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
-                                 cudaStream_t stream);
+                                 cudaStream_t stream, const LaunchOpts &opts);
 // Variants: 0 = FP64, 1 = mixed, 2 = mixed with Kahan-compensated primitive sums.
 constexpr int kNumVariants = 3;
 
@@ -24,7 +29,8 @@ void eri_register_backward(BackwardFn *table);
 
 // Each class translation unit fills table[cls * kNumVariants + variant] for its classes.
 constexpr int kNumTU = 16;
-#define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table);
+// tpq[cls * kNumVariants + v] is set when that kernel is the thread-per-quartet one.
+#define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table, bool *tpq);
 ERI_DECLARE_REGISTER(0) ERI_DECLARE_REGISTER(1) ERI_DECLARE_REGISTER(2) ERI_DECLARE_REGISTER(3)
 ERI_DECLARE_REGISTER(4) ERI_DECLARE_REGISTER(5) ERI_DECLARE_REGISTER(6) ERI_DECLARE_REGISTER(7)
 ERI_DECLARE_REGISTER(8) ERI_DECLARE_REGISTER(9) ERI_DECLARE_REGISTER(10) ERI_DECLARE_REGISTER(11)

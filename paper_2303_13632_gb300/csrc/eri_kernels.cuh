@@ -74,6 +74,10 @@ struct Cfg {
     static constexpr int NAB = La + Lb, NCD = Lc + Ld;
     static constexpr int JL = (Lb + 1) * (Ld + 1);          // I block for fixed (xi, mu, i, k)
     static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;   // I per (xi, mu)
+    // shared-memory strides: blocks padded to an odd number of elements so that the blocks
+    // the lanes of a warp read in phase D start in different banks
+    static constexpr int JLP = (JL % 2) ? JL : JL + 1;
+    static constexpr int IBLKP = (La + 1) * (Lc + 1) * JLP;
     static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);  // bra-transferred per (xi, mu)
     static constexpr bool FUSE_BC = HBLK <= 48;             // ket HRR in registers in phase B
     static constexpr int RWORDS = sizeof(R) / 4;
@@ -86,7 +90,7 @@ struct Cfg {
     static constexpr int GEO_BYTES = G_N * 8;
     static constexpr int BC_BYTES = NRYS * S_N * (int)sizeof(R);
     static constexpr int H_BYTES = FUSE_BC ? 0 : 3 * NRYS * HBLK * (int)sizeof(R);
-    static constexpr int I_BYTES = 3 * NRYS * IBLK * (int)sizeof(R);
+    static constexpr int I_BYTES = 3 * NRYS * IBLKP * (int)sizeof(R);
     static constexpr int STAGE_BYTES = NERI * 3;  // worst case 24-bit codes
     static constexpr int UNION_BYTES = imax(H_BYTES + I_BYTES, STAGE_BYTES);
     static constexpr int PERQ = GEO_BYTES + BC_BYTES + UNION_BYTES + 8;
@@ -103,6 +107,9 @@ struct Cfg {
     static constexpr int OFF_H = OFF_U;
     static constexpr int OFF_I = OFF_U + Q * H_BYTES;
     static constexpr int SMEM = OFF_U + ((Q * UNION_BYTES + 16 + 15) / 16) * 16 + 16;
+    // values per quartet written by the separate setup kernel (K = 1 plans)
+    static constexpr int SETUP_GEO = 8;  // AB, CD, swab, swcd
+    static constexpr int SETUP_FIELDS = SETUP_GEO + NRYS * S_N;
     // thread-per-quartet variant (all intermediates in registers) for the small classes
     static constexpr bool TPQ = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
     static constexpr int TPQ_THREADS = 128;
@@ -278,8 +285,8 @@ __device__ __forceinline__ void ket_hrr(const typename C::R (&s)[C::NCD + 1], ty
 // I layout per quartet: [xi][mu][i][k][j][l] (the (j,l) block is contiguous for phase D).
 template <class C>
 __device__ __forceinline__ int i_index(int xi, int mu, int i, int k, int j, int l) {
-    return ((((xi * C::NRYS + mu) * (C::La + 1) + i) * (C::Lc + 1) + k) * (C::Lb + 1) + j) *
-               (C::Ld + 1) + l;
+    return (((xi * C::NRYS + mu) * (C::La + 1) + i) * (C::Lc + 1) + k) * C::JLP +
+           j * (C::Ld + 1) + l;
 }
 
 // Phase B: VRR column by column in k, bra HRR of each column; writes H (or I when fused).
@@ -458,7 +465,7 @@ __device__ __forceinline__ void quad_chunk(const typename C::R *Iq, int a, int c
     const R *px = Iq + i_index<C>(0, 0, ax, cx, 0, 0);
     const R *py = Iq + i_index<C>(1, 0, ay, cy, 0, 0);
     const R *pz = Iq + i_index<C>(2, 0, az, cz, 0, 0);
-    constexpr int MU_STRIDE = C::IBLK;
+    constexpr int MU_STRIDE = C::IBLKP;
 #pragma unroll 1
     for (int mu = 0; mu < C::NRYS; ++mu) {
 #pragma unroll
@@ -531,11 +538,13 @@ __device__ __forceinline__ void quad_dispatch(int ch, const typename C::R *Iq, i
 }
 
 // ---------------------------------------------------------------------------------------
-template <class C, bool KAHAN>
-__global__ void __launch_bounds__(C::THREADS)
-eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+// One tile of Q quartets (tile index `tile`) of the phase kernel.  PRESET: phases A0/A1 were
+// done by eri_setup_kernel and their results are read from args.setup.
+template <class C, bool KAHAN, bool PRESET = false>
+__device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb,
+                                           const ClassArgs &args, long long tile,
+                                           unsigned char *smem) {
     using R = typename C::R;
-    extern __shared__ __align__(16) unsigned char smem[];
     double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
     R *bc_s = reinterpret_cast<R *>(smem + C::OFF_BC);
     unsigned long long *bmax_s = reinterpret_cast<unsigned long long *>(smem + C::OFF_BMAX);
@@ -544,7 +553,7 @@ eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     __shared__ int maxprim_s;
 
     const int tid = threadIdx.x;
-    const long long q0 = (long long)blockIdx.x * C::Q;
+    const long long q0 = tile * C::Q;
     const int qn = (int)((args.nq - q0) < C::Q ? (args.nq - q0) : C::Q);
 
     // phase D item of this thread (fixed across primitive iterations)
@@ -563,31 +572,47 @@ eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     if (tid == 0) maxprim_s = 1;
     __syncthreads();
     for (int prim = 0; prim < maxprim_s; ++prim) {
-        // A0: geometry per quartet (canonical shell order)
-        for (int q = tid; q < C::Q; q += C::THREADS) {
-            int np = 0;
-            double *geo = geo_s + q * G_N;
-            if (q < qn) {
-                int4 g = args.quartets[q0 + q];
-                int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]),
-                                    pick(g, args.perm[2]), pick(g, args.perm[3]));
-                phase_geometry<C>(sh, qt, prim, geo, np);
-            } else {
-                geo[G_PREF] = 0.0;
-                geo[G_T] = 0.0;
-                for (int s = G_P; s < G_N; ++s)
-                    geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0
-                                                                              : (s == G_IPQ ? 0.5 : 0.0);
+        if constexpr (PRESET) {
+            // setup values of the tile, field-major in the setup buffer (coalesced loads)
+            const R *su = reinterpret_cast<const R *>(args.setup);
+            const long long ss = args.setup_stride;
+            constexpr int gslot[8] = {G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD};
+            for (int it = tid; it < C::Q * C::SETUP_GEO; it += C::THREADS) {
+                int f = it / C::Q, q = it % C::Q;
+                geo_s[q * G_N + gslot[f]] = q < qn ? (double)su[f * ss + q0 + q] : 0.0;
             }
-            if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+            for (int it = tid; it < C::Q * C::NRYS * S_N; it += C::THREADS) {
+                int f = it / C::Q, q = it % C::Q;
+                bc_s[q * C::NRYS * S_N + f] = q < qn ? su[(C::SETUP_GEO + f) * ss + q0 + q] : (R)0;
+            }
+            __syncthreads();
+        } else {
+            // A0: geometry per quartet (canonical shell order)
+            for (int q = tid; q < C::Q; q += C::THREADS) {
+                int np = 0;
+                double *geo = geo_s + q * G_N;
+                if (q < qn) {
+                    int4 g = args.quartets[q0 + q];
+                    int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]),
+                                        pick(g, args.perm[2]), pick(g, args.perm[3]));
+                    phase_geometry<C>(sh, qt, prim, geo, np);
+                } else {
+                    geo[G_PREF] = 0.0;
+                    geo[G_T] = 0.0;
+                    for (int s = G_P; s < G_N; ++s)
+                        geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0
+                                                                                  : (s == G_IPQ ? 0.5 : 0.0);
+                }
+                if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+            }
+            __syncthreads();
+            // A1: roots, weights, B and C per (quartet, root)
+            for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
+                int q = it / C::NRYS, mu = it % C::NRYS;
+                phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        // A1: roots, weights, B and C per (quartet, root)
-        for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
-            int q = it / C::NRYS, mu = it % C::NRYS;
-            phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
-        }
-        __syncthreads();
         // B: VRR (+ bra HRR, + ket HRR when fused) per (quartet, root, axis)
         for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
             int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
@@ -723,17 +748,77 @@ eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     }
 }
 
+template <class C, bool KAHAN, bool PRESET = false>
+__global__ void __launch_bounds__(C::THREADS)
+eri_class_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    class_tile<C, KAHAN, PRESET>(sh, tb, args, blockIdx.x, smem);
+}
+
+// Setup stage of the split path (primitive quartets, K = 1): one thread per quartet computes
+// the Gaussian-product geometry, the Rys roots and weights and the B, C arrays in FP64 and
+// stores them (type R) field-major, so that every thread of this kernel does FP64 work and
+// the recurrence kernel that follows does none.
+template <class C>
+__global__ void __launch_bounds__(128)
+eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, long long stride) {
+    using R = typename C::R;
+    const long long q = (long long)blockIdx.x * 128 + threadIdx.x;
+    if (q >= args.nq) return;
+    int4 g = args.quartets[q];
+    int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
+                        pick(g, args.perm[3]));
+    double geo[G_N];
+    int np = 0;
+    phase_geometry<C>(sh, qt, 0, geo, np);
+    R *o = out + q;
+    o[0 * stride] = (R)geo[G_ABX];
+    o[1 * stride] = (R)geo[G_ABY];
+    o[2 * stride] = (R)geo[G_ABZ];
+    o[3 * stride] = (R)geo[G_CDX];
+    o[4 * stride] = (R)geo[G_CDY];
+    o[5 * stride] = (R)geo[G_CDZ];
+    o[6 * stride] = (R)geo[G_SWAB];
+    o[7 * stride] = (R)geo[G_SWCD];
+#pragma unroll 1
+    for (int mu = 0; mu < C::NRYS; ++mu) {
+        R bc[S_N];
+        phase_setup<C>(tb, geo, mu, bc);
+#pragma unroll
+        for (int f = 0; f < S_N; ++f) o[(C::SETUP_GEO + mu * S_N + f) * stride] = bc[f];
+    }
+}
+
+// Persistent form: a grid sized to the resident CTAs pulls tiles from a work counter
+// (atomicAdd, no waiting) until the class is exhausted; quartets of uneven contraction
+// degree therefore balance dynamically.  The counter must be zero at launch.
+template <class C, bool KAHAN>
+__global__ void __launch_bounds__(C::THREADS)
+eri_class_persistent(ShellsDev sh, Tables tb, ClassArgs args, unsigned long long *counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long tile_s;
+    const long long n_tiles = (args.nq + C::Q - 1) / C::Q;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) tile_s = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = tile_s;
+        if (t >= n_tiles) break;
+        class_tile<C, KAHAN>(sh, tb, args, t, smem);
+    }
+}
+
 // ---------------------------------------------------------------------------------------
 // Thread-per-quartet kernel for the small classes: each thread runs every stage of one
 // quartet in registers (no shared-memory phases, no barriers before the store), so the FP64
 // setup of all threads overlaps.  Shared memory is used only to pack the compressed tile.
 template <class C>
-__global__ void __launch_bounds__(C::TPQ_THREADS)
-eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+__device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
+                                         const ClassArgs &args, long long tile,
+                                         unsigned char *smem) {
     using R = typename C::R;
-    extern __shared__ __align__(16) unsigned char smem[];
     const int tid = threadIdx.x;
-    const long long q0 = (long long)blockIdx.x * C::TPQ_THREADS;
+    const long long q0 = tile * C::TPQ_THREADS;
     const int qn = (int)((args.nq - q0) < C::TPQ_THREADS ? (args.nq - q0) : C::TPQ_THREADS);
     const bool live = tid < qn;
     R acc[C::NERI];
@@ -861,27 +946,105 @@ eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     }
 }
 
+template <class C>
+__global__ void __launch_bounds__(C::TPQ_THREADS)
+eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    tpq_tile<C>(sh, tb, args, blockIdx.x, smem);
+}
+
+template <class C>
+__global__ void __launch_bounds__(C::TPQ_THREADS)
+eri_tpq_persistent(ShellsDev sh, Tables tb, ClassArgs args, unsigned long long *counter) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ long long tile_s;
+    const long long n_tiles = (args.nq + C::TPQ_THREADS - 1) / C::TPQ_THREADS;
+    for (;;) {
+        __syncthreads();
+        if (threadIdx.x == 0) tile_s = (long long)atomicAdd(counter, 1ull);
+        __syncthreads();
+        const long long t = tile_s;
+        if (t >= n_tiles) break;
+        tpq_tile<C>(sh, tb, args, t, smem);
+    }
+}
+
 // Host-side launch helper for one canonical class.
+//   o.force_phase  use the shared-memory phase kernel even where the thread-per-quartet
+//                  kernel exists (autotuning)
+//   o.counter      non-null: persistent launch pulling tiles from this zeroed counter with
+//                  o.grid CTAs (o.grid <= 0: every resident CTA, from the occupancy API)
 template <int La, int Lb, int Lc, int Ld, typename R, bool KAHAN>
 cudaError_t launch_class(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
-                         cudaStream_t stream) {
+                         cudaStream_t stream, const LaunchOpts &o) {
     using C = Cfg<La, Lb, Lc, Ld, R>;
     if (args.nq <= 0) return cudaSuccess;
+    int sms = 0;
+    if (o.counter) {
+        cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, o.device);
+        if (e != cudaSuccess) return e;
+    }
     if constexpr (C::TPQ && !KAHAN) {
-        long long grid = (args.nq + C::TPQ_THREADS - 1) / C::TPQ_THREADS;
-        if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-        size_t smem = 0;
-        if (args.out_fp64 == nullptr)
-            smem = ((size_t)C::TPQ_THREADS * C::NERI * args.bits + 31) / 32 * 4 + 16;
-        eri_tpq_kernel<C><<<(unsigned)grid, C::TPQ_THREADS, smem, stream>>>(sh, tb, args);
-        return cudaGetLastError();
+        if (!o.force_phase) {
+            size_t smem = 0;
+            if (args.out_fp64 == nullptr)
+                smem = ((size_t)C::TPQ_THREADS * C::NERI * args.bits + 31) / 32 * 4 + 16;
+            long long tiles = (args.nq + C::TPQ_THREADS - 1) / C::TPQ_THREADS;
+            if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+            if (!o.counter) {
+                eri_tpq_kernel<C><<<(unsigned)tiles, C::TPQ_THREADS, smem, stream>>>(sh, tb, args);
+                return cudaGetLastError();
+            }
+            int per_sm = 0;
+            cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+                &per_sm, eri_tpq_persistent<C>, C::TPQ_THREADS, smem);
+            if (e != cudaSuccess) return e;
+            long long grid = o.grid > 0 ? o.grid : (long long)per_sm * sms;
+            grid = grid < tiles ? grid : tiles;
+            eri_tpq_persistent<C><<<(unsigned)grid, C::TPQ_THREADS, smem, stream>>>(sh, tb, args,
+                                                                                     o.counter);
+            return cudaGetLastError();
+        }
+    }
+    if constexpr (!KAHAN) {
+        if (o.scratch && !o.counter) {
+            // split path: FP64 setup kernel, then the recurrence/quadrature kernel
+            long long blocks = (args.nq + 127) / 128;
+            if (blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+            const long long stride = (args.nq + 31) / 32 * 32;
+            eri_setup_kernel<C><<<(unsigned)blocks, 128, 0, stream>>>(
+                sh, tb, args, reinterpret_cast<R *>(o.scratch), stride);
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) return e;
+            ClassArgs a2 = args;
+            a2.setup = o.scratch;
+            a2.setup_stride = stride;
+            auto k2 = eri_class_kernel<C, false, true>;
+            e = cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+            if (e != cudaSuccess) return e;
+            long long tiles = (args.nq + C::Q - 1) / C::Q;
+            k2<<<(unsigned)tiles, C::THREADS, C::SMEM, stream>>>(sh, tb, a2);
+            return cudaGetLastError();
+        }
     }
     auto kern = eri_class_kernel<C, KAHAN>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    auto pkern = eri_class_persistent<C, KAHAN>;
+    cudaError_t e = cudaFuncSetAttribute(o.counter ? (const void *)pkern : (const void *)kern,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
-    long long grid = (args.nq + C::Q - 1) / C::Q;
-    if (grid > 0x7fffffffLL) return cudaErrorInvalidValue;
-    kern<<<(unsigned)grid, C::THREADS, C::SMEM, stream>>>(sh, tb, args);
+    long long tiles = (args.nq + C::Q - 1) / C::Q;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    if (!o.counter) {
+        kern<<<(unsigned)tiles, C::THREADS, C::SMEM, stream>>>(sh, tb, args);
+        return cudaGetLastError();
+    }
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pkern, C::THREADS, C::SMEM);
+    if (e != cudaSuccess) return e;
+    long long grid = o.grid > 0 ? o.grid : (long long)per_sm * sms;
+    grid = grid < tiles ? grid : tiles;
+    if (grid < 1) grid = 1;
+    pkern<<<(unsigned)grid, C::THREADS, C::SMEM, stream>>>(sh, tb, args, o.counter);
     return cudaGetLastError();
 }
 

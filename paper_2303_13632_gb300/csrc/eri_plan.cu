@@ -17,17 +17,20 @@ namespace eri {
 namespace {
 
 LaunchFn g_launch[256 * kNumVariants];
+bool g_tpq[256 * kNumVariants];
 BackwardFn g_backward[256];
 std::once_flag g_launch_once;
 
 void register_all() {
     eri_register_backward(g_backward);
-    eri_register_tu_0(g_launch); eri_register_tu_1(g_launch); eri_register_tu_2(g_launch);
-    eri_register_tu_3(g_launch); eri_register_tu_4(g_launch); eri_register_tu_5(g_launch);
-    eri_register_tu_6(g_launch); eri_register_tu_7(g_launch); eri_register_tu_8(g_launch);
-    eri_register_tu_9(g_launch); eri_register_tu_10(g_launch); eri_register_tu_11(g_launch);
-    eri_register_tu_12(g_launch); eri_register_tu_13(g_launch); eri_register_tu_14(g_launch);
-    eri_register_tu_15(g_launch);
+    eri_register_tu_0(g_launch, g_tpq); eri_register_tu_1(g_launch, g_tpq);
+    eri_register_tu_2(g_launch, g_tpq); eri_register_tu_3(g_launch, g_tpq);
+    eri_register_tu_4(g_launch, g_tpq); eri_register_tu_5(g_launch, g_tpq);
+    eri_register_tu_6(g_launch, g_tpq); eri_register_tu_7(g_launch, g_tpq);
+    eri_register_tu_8(g_launch, g_tpq); eri_register_tu_9(g_launch, g_tpq);
+    eri_register_tu_10(g_launch, g_tpq); eri_register_tu_11(g_launch, g_tpq);
+    eri_register_tu_12(g_launch, g_tpq); eri_register_tu_13(g_launch, g_tpq);
+    eri_register_tu_14(g_launch, g_tpq); eri_register_tu_15(g_launch, g_tpq);
 }
 
 int ncart_h(int L) { return (L + 1) * (L + 2) / 2; }
@@ -134,6 +137,7 @@ struct eri_plan_s {
     int4 *d_quartets = nullptr;  // class-sorted
     int *d_perm = nullptr;       // sorted position -> caller's index
     int *d_err = nullptr;
+    void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
     // host layout
     long long count[256] = {0};
     long long first[256] = {0};
@@ -155,6 +159,7 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_quartets);
     cudaFree(p->d_perm);
     cudaFree(p->d_err);
+    cudaFree(p->d_setup);
     delete p;
 }
 
@@ -203,7 +208,32 @@ eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d
     int variant = p->precision == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
     LaunchFn fn = g_launch[c.cls * kNumVariants + variant];
     if (!fn) return ERI_E_UNSUPPORTED;
-    return cuda_status(fn(sh, p->tables, a, stream));
+    LaunchOpts o;
+    o.device = p->device;
+    const bool split = p->max_nprim == 1 && !g_tpq[c.cls * kNumVariants + variant];
+    if (!split) return cuda_status(fn(sh, p->tables, a, stream, o));
+    if (!p->d_setup) {
+        cudaError_t e = cudaMalloc(&p->d_setup, (size_t)kSetupChunk * kSetupFieldsMax * sizeof(double));
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    o.scratch = p->d_setup;
+    // chunks of kSetupChunk quartets (multiples of 32: every chunk starts on a packed word)
+    for (long long c0 = 0; c0 < a.nq; c0 += kSetupChunk) {
+        ClassArgs ac = a;
+        ac.quartets = a.quartets + c0;
+        ac.nq = std::min<long long>(kSetupChunk, a.nq - c0);
+        if (d_out) {
+            ac.out_fp64 = a.out_fp64 + c0 * neri;
+        } else {
+            long long w = c0 * neri * bits / 32;
+            ac.packed = a.packed + w;
+            ac.scales = a.scales + c0;
+            ac.seg_words = (c0 + ac.nq == a.nq) ? a.seg_words - w : ac.nq * neri * bits / 32;
+        }
+        cudaError_t e = fn(sh, p->tables, ac, stream, o);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return ERI_OK;
 }
 
 }  // namespace

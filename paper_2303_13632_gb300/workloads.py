@@ -147,3 +147,28 @@ def random_contracted_pool(rng, n_per_L: int, K: int, Ls=(1, 2), box: float = 3.
     exps = a0[:, None] * 3.0 ** np.arange(K)[None, :]
     coefs = rng.uniform(0.1, 1.0, size=(n, K))
     return make_shellset(centers, L, list(exps), list(coefs))
+
+
+def molecule_basis(n_atoms: int = 200, box: float = 20.0, min_sep: float = 1.8, seed_k: int = 4,
+                   shells_per_atom=(0, 0, 1, 1, 2, 3), kmax: int = 6) -> ShellSet:
+    """Atoms at random positions in a cubic box with a minimum separation; every atom carries
+    the shells `shells_per_atom` (s, s, p, p, d, f), each contracted over K ~ U{1..kmax}
+    even-tempered primitives alpha0 * 3^k with alpha0 log-uniform in [0.05, 50 / 3^(K-1)]
+    (so exponents span 0.05..50) and coefficients U[0.1, 1]."""
+    rng = rng_for(seed_k)
+    atoms = []
+    while len(atoms) < n_atoms:
+        p = rng.uniform(0.0, box, size=3)
+        if all(np.linalg.norm(p - a) >= min_sep for a in atoms):
+            atoms.append(p)
+    centers, L, exps, coefs = [], [], [], []
+    for a in atoms:
+        for l in shells_per_atom:
+            K = int(rng.integers(1, kmax + 1))
+            hi = 50.0 / 3.0 ** (K - 1)
+            a0 = np.exp(rng.uniform(np.log(0.05), np.log(hi)))
+            centers.append(a)
+            L.append(l)
+            exps.append(a0 * 3.0 ** np.arange(K))
+            coefs.append(rng.uniform(0.1, 1.0, size=K))
+    return make_shellset(np.array(centers), L, exps, coefs)

@@ -94,3 +94,19 @@ def test_backward_rejects_f_shells():
     with pytest.raises(api.EriError) as e:
         api.eri_backward(plan, G, dR, da)
     assert e.value.status == 2
+
+
+def test_autograd_function():
+    """E = sum(G * eri(centers, exps)) differentiated by torch equals the direct adjoint."""
+    from paper_2303_13632_gb300.autograd import eri
+
+    pool, q, G, offs = workload(51, 2, 4)
+    plan = api.eri_plan_create(pool, q, precision="fp64")
+    Gs = torch.tensor(to_sorted(plan, q, G, offs, pool), device="cuda")
+    centers = torch.tensor(pool.centers, dtype=torch.float64, requires_grad=True)
+    exps = torch.tensor(pool.exps, dtype=torch.float64, requires_grad=True)
+    E = (eri(centers, exps, pool, q) * Gs).sum()
+    E.backward()
+    dR, da = gpu_grad(pool, q, G, offs)
+    np.testing.assert_allclose(centers.grad.numpy(), dR, rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(exps.grad.numpy(), da, rtol=1e-12, atol=1e-14)

@@ -161,6 +161,25 @@ eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packe
 eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
                                           void *d_packed, float *d_scales, void *stream);
 
+/* Batched form of eri_compute_compressed (same outputs, same layout): every class of the plan
+ * runs as a persistent work-queue kernel (one grid of resident CTAs per class pulling tiles of
+ * quartets from an atomic counter, so quartets of uneven contraction degree balance
+ * dynamically), the classes spread over four streams forked from `stream`, the whole sequence
+ * captured once into a CUDA graph and replayed on later calls with the same bits, precision
+ * and output pointers.  The tile counters are plan-owned device memory.  The launch choice per
+ * class (kernel family and grid) comes from eri_autotune when it has run.  Asynchronous. */
+eri_status_t eri_compute_compressed_batched(eri_plan_t plan, int32_t bits, void *d_packed,
+                                            float *d_scales, void *stream);
+
+/* Picks, per canonical class of the plan and for the plan's precision and `bits`, the faster
+ * persistent launch (thread-per-quartet or shared-memory kernel where both exist; grid of all
+ * resident CTAs, one or two CTAs per SM) by timing each candidate on the plan's own quartets
+ * (outputs are written to d_packed/d_scales as a side effect).  Choices already recorded for
+ * this GPU in the text file cache_path (may be NULL) are reused; new ones are appended.
+ * Synchronous on `stream`. */
+eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
+                          const char *cache_path, void *stream);
+
 /* Adjoint (gradients) of E = sum_q sum_abcd G_q,abcd (ab|cd)_q for an upstream d_G laid out
  * like eri_compute's output (class-sorted, row major per quartet, eri_output_bytes(plan, 0)):
  *   d_dR[3*s + xi]   = dE / d(center[xi] of shell s)          (n_shells x 3, bohr^-1 Ha)

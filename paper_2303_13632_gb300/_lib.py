@@ -67,6 +67,8 @@ SIGNATURES = {
     "eri_compute_compressed_class": (_i32, [_p, _i32, _i32, _p, _p, _p]),
     "eri_sync": (_i32, [_p, _p]),
     "eri_backward": (_i32, [_p, _p, _p, _p, _p]),
+    "eri_compute_compressed_batched": (_i32, [_p, _i32, _p, _p, _p]),
+    "eri_autotune": (_i32, [_p, _i32, _p, _p, ctypes.c_char_p, _p]),
     "eri_status_string": (ctypes.c_char_p, [_i32]),
     "eri_boys_device": (_i32, [_i32, _p, _i64, _p, _p]),
     "eri_rys_device": (_i32, [_i32, _p, _i64, _p, _p, _p]),

@@ -155,6 +155,17 @@ def eri_compute_compressed_class(plan: Plan, cls: int, bits: int, packed, scales
           "eri_compute_compressed_class")
 
 
+def eri_compute_compressed_batched(plan: Plan, bits: int, packed, scales, stream=None) -> None:
+    check(_lib.load().eri_compute_compressed_batched(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales),
+                                                     _stream_handle(stream)), "eri_compute_compressed_batched")
+
+
+def eri_autotune(plan: Plan, bits: int, packed, scales, cache_path: str | None = None, stream=None) -> None:
+    path = cache_path.encode() if cache_path else None
+    check(_lib.load().eri_autotune(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales), path,
+                                   _stream_handle(stream)), "eri_autotune")
+
+
 def eri_backward(plan: Plan, G, dR, dalpha, stream=None) -> None:
     """dR [n_shells, 3] and dalpha [n_prims] (float64 CUDA tensors) receive the gradient of
     E = sum G * ERIs for G laid out like eri_compute's output."""

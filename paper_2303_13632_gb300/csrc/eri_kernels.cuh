@@ -45,6 +45,17 @@ struct RTraits<float> {
     static __device__ __forceinline__ float round_away(float v) { return roundf(v); }
 };
 
+// Two's complement bits of an integral value |v| <= 2^{bits-1} - 1.  In FP32 and for widths up
+// to 23 the sum v + 1.5 * 2^23 is exact and its low mantissa bits are the integer, which
+// replaces a float-to-integer conversion instruction per value by one FP32 add.
+template <typename R>
+__device__ __forceinline__ uint32_t to_code(R v, int bits) {
+    if constexpr (sizeof(R) == 4) {
+        if (bits <= 23) return (uint32_t)(__float_as_int(v + 12582912.0f) - 0x4B400000);
+    }
+    return (uint32_t)(int)v;
+}
+
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
@@ -672,20 +683,35 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
     __syncthreads();
     if (live) {
         // b_max = max |x| over the quartet; non-negative IEEE values order like their bit
-        // patterns, so an integer atomicMax on the bits is exact
+        // patterns, so an integer atomicMax on the bits is exact.  Done in the accumulation
+        // type: a conversion per value would occupy the (slow) FP64 pipe in mixed precision.
         bool bad = false;
-        unsigned long long mb = 0ull;
+        if constexpr (sizeof(R) == 8) {
+            unsigned long long mb = 0ull;
 #pragma unroll
-        for (int bb = 0; bb < C::BCH; ++bb)
-            if (dch * C::BCH + bb < C::NB)
+            for (int bb = 0; bb < C::BCH; ++bb)
+                if (dch * C::BCH + bb < C::NB)
 #pragma unroll
-                for (int d = 0; d < C::ND; ++d) {
-                    double v = fabs((double)acc[bb][d]);
-                    bad |= !(v <= 1.7976931348623157e308);
-                    unsigned long long u = (unsigned long long)__double_as_longlong(v);
-                    mb = u > mb ? u : mb;
-                }
-        atomicMax(bmax_s + dq, mb);
+                    for (int d = 0; d < C::ND; ++d) {
+                        double v = fabs((double)acc[bb][d]);
+                        bad |= !(v <= 1.7976931348623157e308);
+                        unsigned long long u = (unsigned long long)__double_as_longlong(v);
+                        mb = u > mb ? u : mb;
+                    }
+            atomicMax(bmax_s + dq, mb);
+        } else {
+            unsigned int mb = 0u;
+#pragma unroll
+            for (int bb = 0; bb < C::BCH; ++bb)
+                if (dch * C::BCH + bb < C::NB)
+#pragma unroll
+                    for (int d = 0; d < C::ND; ++d) {
+                        unsigned int u = __float_as_uint((float)acc[bb][d]) & 0x7fffffffu;
+                        bad |= u >= 0x7f800000u;  // inf or nan
+                        mb = u > mb ? u : mb;
+                    }
+            atomicMax(reinterpret_cast<unsigned int *>(bmax_s + dq), mb);
+        }
         if (bad) atomicOr(args.err, 1);
     }
     // staging buffer for the tile's bitstream (aliases the H/I region)
@@ -701,7 +727,11 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
     __syncthreads();
     if (live) {
         const double M = (double)((1u << (bits - 1)) - 1u);
-        double bmax = __longlong_as_double((long long)bmax_s[dq]);
+        double bmax;
+        if constexpr (sizeof(R) == 8)
+            bmax = __longlong_as_double((long long)bmax_s[dq]);
+        else
+            bmax = (double)__uint_as_float(*reinterpret_cast<const unsigned int *>(bmax_s + dq));
         float eps = (float)(bmax / M);
         if (da == 0 && dc == 0 && dch == 0) args.scales[q0 + dq] = eps;
         R inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
@@ -716,7 +746,7 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 for (int d = 0; d < C::ND; ++d) {
                     R v = RTraits<R>::round_away(acc[bb][d] * inv);
                     v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
-                    uint32_t code = (uint32_t)(int)v & mask;
+                    uint32_t code = to_code<R>(v, bits) & mask;
                     long long s = (qbase + b * st1 + d * st3) * bits - (w0 << 5);
                     int wi = (int)(s >> 5), off = (int)(s & 31);
                     atomicOr(stage + wi, code << off);
@@ -917,7 +947,7 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                     for (int d = 0; d < C::ND; ++d) {
                         R v = RTraits<R>::round_away(acc[((a * C::NB + b) * C::NC + c) * C::ND + d] * inv);
                         v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
-                        uint32_t code = (uint32_t)(int)v & mask;
+                        uint32_t code = to_code<R>(v, bits) & mask;
                         long long sb = (qbase + a * st0 + b * st1 + c * st2 + d * st3) * bits - (w0 << 5);
                         int wi = (int)(sb >> 5), off = (int)(sb & 31);
                         atomicOr(stage + wi, code << off);

@@ -3,11 +3,14 @@
 // layouts, and the per-class kernel launches.
 #include <cub/device/device_radix_sort.cuh>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdint>
+#include <cstdio>
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "eri_internal.h"
@@ -138,6 +141,18 @@ struct eri_plan_s {
     int *d_perm = nullptr;       // sorted position -> caller's index
     int *d_err = nullptr;
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
+    // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
+    unsigned long long *d_counters = nullptr;
+    static constexpr int kSide = 4;
+    cudaStream_t side[kSide] = {};
+    cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+    cudaGraphExec_t graph = nullptr;
+    int g_bits = -1, g_prec = -1;
+    void *g_packed = nullptr;
+    float *g_scales = nullptr;
+    // autotuned launch choice per canonical class and variant (grid 0 = all resident CTAs)
+    int tune_phase[256 * kNumVariants] = {0};
+    int tune_grid[256 * kNumVariants] = {0};
     // host layout
     long long count[256] = {0};
     long long first[256] = {0};
@@ -160,6 +175,13 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_perm);
     cudaFree(p->d_err);
     cudaFree(p->d_setup);
+    cudaFree(p->d_counters);
+    if (p->graph) cudaGraphExecDestroy(p->graph);
+    for (int i = 0; i < eri_plan_s::kSide; ++i) {
+        if (p->side[i]) cudaStreamDestroy(p->side[i]);
+        if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
+    }
+    if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     delete p;
 }
 
@@ -180,6 +202,37 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
 size_t packed_segment_bytes(long long nq, int neri, int bits) {
     unsigned long long b = ((unsigned long long)nq * neri * bits + 7) / 8;
     return (size_t)((b + 255) / 256 * 256);
+}
+
+int class_neri(int cls) {
+    return ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) * ncart_h(cls & 3);
+}
+
+int plan_variant(const eri_plan_s *p) {
+    return p->precision == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
+}
+
+ClassArgs class_args(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed, float *d_scales,
+                     size_t packed_off) {
+    Canon c = canonicalise(cls);
+    ClassArgs a{};
+    for (int k = 0; k < 4; ++k) {
+        a.perm[k] = c.perm[k];
+        a.ostride[k] = c.ostride[k];
+    }
+    a.quartets = p->d_quartets + p->first[cls];
+    a.nq = p->count[cls];
+    a.err = p->d_err;
+    int neri = class_neri(cls);
+    if (d_out) {
+        a.out_fp64 = d_out + p->fp64_off[cls];
+    } else {
+        a.packed = reinterpret_cast<uint32_t *>(static_cast<char *>(d_packed) + packed_off);
+        a.seg_words = (long long)(packed_segment_bytes(p->count[cls], neri, bits) / 4);
+        a.scales = d_scales + p->first[cls];
+        a.bits = bits;
+    }
+    return a;
 }
 
 eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed,
@@ -234,6 +287,61 @@ eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d
         if (e != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
+}
+
+eri_status_t ensure_batched_resources(eri_plan_s *p) {
+    cudaError_t e = cudaSuccess;
+    if (!p->d_counters) e = cudaMalloc(&p->d_counters, 256 * sizeof(unsigned long long));
+    for (int i = 0; e == cudaSuccess && i < eri_plan_s::kSide; ++i) {
+        if (!p->side[i]) e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
+        if (e == cudaSuccess && !p->join_ev[i])
+            e = cudaEventCreateWithFlags(&p->join_ev[i], cudaEventDisableTiming);
+    }
+    if (e == cudaSuccess && !p->fork_ev) e = cudaEventCreateWithFlags(&p->fork_ev, cudaEventDisableTiming);
+    return cuda_status(e);
+}
+
+// Persistent launches of every non-empty class on the plan's side streams (forked from and
+// joined back into `stream`); the classes go to the side streams by decreasing quartet count.
+eri_status_t enqueue_batched(eri_plan_s *p, int bits, void *d_packed, float *d_scales,
+                             cudaStream_t stream) {
+    cudaError_t e = cudaMemsetAsync(p->d_counters, 0, 256 * sizeof(unsigned long long), stream);
+    if (e == cudaSuccess) e = cudaEventRecord(p->fork_ev, stream);
+    for (int i = 0; e == cudaSuccess && i < eri_plan_s::kSide; ++i)
+        e = cudaStreamWaitEvent(p->side[i], p->fork_ev, 0);
+    if (e != cudaSuccess) return cuda_status(e);
+    std::vector<int> cls;
+    std::vector<size_t> off(256, 0);
+    size_t o = 0;
+    for (int c = 0; c < 256; ++c) {
+        off[c] = o;
+        o += packed_segment_bytes(p->count[c], class_neri(c), bits);
+        if (p->count[c] > 0) cls.push_back(c);
+    }
+    std::sort(cls.begin(), cls.end(), [&](int x, int y) {
+        return p->count[x] * class_neri(x) > p->count[y] * class_neri(y);
+    });
+    ShellsDev sh{p->d_cx, p->d_cy, p->d_cz, p->d_pofs, p->d_nprim, p->d_exps, p->d_cn};
+    const int variant = plan_variant(p);
+    for (size_t i = 0; i < cls.size(); ++i) {
+        int c = cls[i];
+        int cc = canonicalise(c).cls;
+        LaunchFn fn = g_launch[cc * kNumVariants + variant];
+        if (!fn) return ERI_E_UNSUPPORTED;
+        ClassArgs a = class_args(p, c, nullptr, bits, d_packed, d_scales, off[c]);
+        LaunchOpts lo;
+        lo.device = p->device;
+        lo.counter = p->d_counters + c;
+        lo.force_phase = p->tune_phase[cc * kNumVariants + variant];
+        lo.grid = p->tune_grid[cc * kNumVariants + variant];
+        e = fn(sh, p->tables, a, p->side[i % eri_plan_s::kSide], lo);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    for (int i = 0; e == cudaSuccess && i < eri_plan_s::kSide; ++i) {
+        e = cudaEventRecord(p->join_ev[i], p->side[i]);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(stream, p->join_ev[i], 0);
+    }
+    return cuda_status(e);
 }
 
 }  // namespace
@@ -567,6 +675,151 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
         if (e != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
+}
+
+eri_status_t eri_compute_compressed_batched(eri_plan_t plan, int32_t bits, void *d_packed,
+                                            float *d_scales, void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
+        return ERI_E_INVALID;
+    if (plan->nq == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    eri_status_t st = ensure_batched_resources(plan);
+    if (st != ERI_OK) return st;
+    if (!plan->graph || plan->g_bits != bits || plan->g_prec != plan->precision ||
+        plan->g_packed != d_packed || plan->g_scales != d_scales) {
+        if (plan->graph) {
+            cudaGraphExecDestroy(plan->graph);
+            plan->graph = nullptr;
+        }
+        // capture the fork/launch/join sequence once on a side stream and keep the executable
+        cudaStream_t origin = nullptr;
+        cudaError_t e = cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            cudaStreamDestroy(origin);
+            return cuda_status(e);
+        }
+        st = enqueue_batched(plan, bits, d_packed, d_scales, origin);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(origin, &g);
+        cudaStreamDestroy(origin);
+        if (st != ERI_OK) {
+            if (g) cudaGraphDestroy(g);
+            return st;
+        }
+        if (e != cudaSuccess) return cuda_status(e);
+        e = cudaGraphInstantiate(&plan->graph, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_status(e);
+        plan->g_bits = bits;
+        plan->g_prec = plan->precision;
+        plan->g_packed = d_packed;
+        plan->g_scales = d_scales;
+    }
+    return cuda_status(cudaGraphLaunch(plan->graph, (cudaStream_t)stream));
+}
+
+eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
+                          const char *cache_path, void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    eri_status_t st = ensure_batched_resources(plan);
+    if (st != ERI_OK) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int variant = plan_variant(plan);
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, plan->device) != cudaSuccess) return ERI_E_CUDA;
+    std::string gpu = prop.name;
+    for (auto &ch : gpu)
+        if (ch == ' ') ch = '_';
+    // cached choices: lines "gpu variant bits canonical_class force_phase grid"
+    std::vector<int> known(256, 0);
+    if (cache_path) {
+        if (FILE *f = std::fopen(cache_path, "r")) {
+            char name[256];
+            int v, b, c, fp, gr;
+            while (std::fscanf(f, "%255s %d %d %d %d %d", name, &v, &b, &c, &fp, &gr) == 6)
+                if (gpu == name && v == variant && b == bits && c >= 0 && c < 256) {
+                    plan->tune_phase[c * kNumVariants + v] = fp;
+                    plan->tune_grid[c * kNumVariants + v] = gr;
+                    known[c] = 1;
+                }
+            std::fclose(f);
+        }
+    }
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    ShellsDev sh{plan->d_cx, plan->d_cy, plan->d_cz, plan->d_pofs, plan->d_nprim, plan->d_exps, plan->d_cn};
+    std::vector<std::string> lines;
+    size_t o = 0;
+    std::vector<size_t> off(256);
+    for (int c = 0; c < 256; ++c) {
+        off[c] = o;
+        o += packed_segment_bytes(plan->count[c], class_neri(c), bits);
+    }
+    std::vector<int> done(256, 0);
+    for (int c = 0; c < 256; ++c) {
+        if (plan->count[c] == 0) continue;
+        int cc = canonicalise(c).cls;
+        if (known[cc] || done[cc]) continue;
+        done[cc] = 1;
+        LaunchFn fn = g_launch[cc * kNumVariants + variant];
+        ClassArgs a = class_args(plan, c, nullptr, bits, d_packed, d_scales, off[c]);
+        int cand_phase[2] = {0, 1};
+        int n_phase = g_tpq[cc * kNumVariants + variant] ? 2 : 1;
+        int grids[3] = {0, prop.multiProcessorCount, 2 * prop.multiProcessorCount};
+        float best = 1e30f;
+        int bp = 0, bg = 0;
+        for (int ip = 0; ip < n_phase; ++ip)
+            for (int ig = 0; ig < 3; ++ig) {
+                LaunchOpts lo;
+                lo.device = plan->device;
+                lo.counter = plan->d_counters + c;
+                lo.force_phase = n_phase == 2 ? cand_phase[ip] : 0;
+                lo.grid = grids[ig];
+                float ms = 0.0f;
+                for (int rep = 0; rep < 2; ++rep) {  // first run warms up
+                    cudaMemsetAsync(plan->d_counters + c, 0, sizeof(unsigned long long), s);
+                    cudaEventRecord(e0, s);
+                    if (fn(sh, plan->tables, a, s, lo) != cudaSuccess) {
+                        cudaEventDestroy(e0);
+                        cudaEventDestroy(e1);
+                        return ERI_E_CUDA;
+                    }
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms, e0, e1);
+                }
+                if (ms < best) {
+                    best = ms;
+                    bp = lo.force_phase;
+                    bg = lo.grid;
+                }
+            }
+        plan->tune_phase[cc * kNumVariants + variant] = bp;
+        plan->tune_grid[cc * kNumVariants + variant] = bg;
+        char buf[512];
+        std::snprintf(buf, sizeof(buf), "%s %d %d %d %d %d\n", gpu.c_str(), variant, bits, cc, bp, bg);
+        lines.push_back(buf);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (cache_path && !lines.empty()) {
+        if (FILE *f = std::fopen(cache_path, "a")) {
+            for (auto &l : lines) std::fputs(l.c_str(), f);
+            std::fclose(f);
+        }
+    }
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
 }
 
 eri_status_t eri_sync(eri_plan_t plan, void *stream) {

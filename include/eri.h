@@ -195,6 +195,43 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
                           void *stream);
 
+/* ---- no-allocation entry point (no counterpart in the paper) ---- */
+
+/* Largest n_quartets eri_compute_class_noalloc accepts. */
+#define ERI_NOALLOC_MAX_QUARTETS 16384
+
+/* FP64 (precision ERI_FP64) or mixed-precision (ERI_MIXED) ERIs of quartets that all belong
+ * to generic class `cls`, written in eri_compute's per-quartet layout (row major, a slowest),
+ * for callers that cannot let a library allocate device memory: applications that reserve the
+ * device memory themselves and sub-allocate from their own pool, or code that must not risk
+ * the synchronisation an allocation call can cause.  This function calls no cudaMalloc,
+ * cudaFree or other allocating routine.  Every input and output is caller-owned device memory:
+ *   d_cx, d_cy, d_cz   shell centres (n_shells doubles each)
+ *   d_pofs, d_nprim    first primitive and primitive count per shell; every shell a quartet
+ *                      uses must have nprim = 1 (otherwise bit 2 of *d_err is set and those
+ *                      quartets' values are undefined)
+ *   d_exps, d_cn       exponent and coefficient times N(alpha, L) per primitive, with
+ *                      N = (2 alpha/pi)^{3/4} (4 alpha)^{L/2} / sqrt((2L-1)!!)
+ *   d_quartets         n_quartets x 4 int32 shell ids, 16-byte aligned
+ *   d_out              n_quartets * n_eri doubles
+ *   d_err              one int32, OR-ed with 1 for a non-finite result and 4 for a contracted
+ *                      shell (the caller clears it)
+ * The only scratch is a file-scope device array of ERI_NOALLOC_MAX_QUARTETS setup records
+ * (about 10 MB, resident on every GPU that loads the library until the process exits);
+ * n_quartets above the limit returns ERI_E_INVALID before any device work.  Every call
+ * shares that array and leaves its contents behind; nothing in it must start at zero (each
+ * call writes the records it reads first).  Calls on one device whose device work overlaps
+ * (for example on two streams) race on the array: serialise them.  The first call
+ * on a device looks up the device addresses of the array and of the library's constant
+ * tables (cudaGetSymbolAddress, with that device current); make that first call before any
+ * stream capture.  Asynchronous on `stream` afterwards. */
+eri_status_t eri_compute_class_noalloc(int32_t cls, int32_t precision, const double *d_cx,
+                                       const double *d_cy, const double *d_cz,
+                                       const int32_t *d_pofs, const int32_t *d_nprim,
+                                       const double *d_exps, const double *d_cn,
+                                       const int32_t *d_quartets, int64_t n_quartets,
+                                       double *d_out, int32_t *d_err, void *stream);
+
 /* Waits for the plan's work on `stream` and returns the first latched device error
  * (ERI_E_NUMERIC, ERI_E_TIMEOUT) or a CUDA error; clears the latch. */
 eri_status_t eri_sync(eri_plan_t plan, void *stream);

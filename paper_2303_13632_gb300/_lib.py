@@ -25,6 +25,7 @@ ERI_MIXED = 1
 ERI_EXPLICIT = 0
 ERI_ALL = 1
 ERI_QUARTETS_ON_DEVICE = 1
+ERI_NOALLOC_MAX_QUARTETS = 16384
 
 STATUS_NAMES = {
     ERI_OK: "ERI_OK", ERI_E_INVALID: "ERI_E_INVALID", ERI_E_UNSUPPORTED: "ERI_E_UNSUPPORTED",
@@ -70,6 +71,7 @@ SIGNATURES = {
     "eri_compute_compressed_batched": (_i32, [_p, _i32, _p, _p, _p]),
     "eri_autotune": (_i32, [_p, _i32, _p, _p, ctypes.c_char_p, _p]),
     "eri_status_string": (ctypes.c_char_p, [_i32]),
+    "eri_compute_class_noalloc": (_i32, [_i32, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _i64, _p, _p, _p]),
     "eri_boys_device": (_i32, [_i32, _p, _i64, _p, _p]),
     "eri_rys_device": (_i32, [_i32, _p, _i64, _p, _p, _p]),
     "eri_class_id": (_i32, [_i32, _i32, _i32, _i32]),

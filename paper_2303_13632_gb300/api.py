@@ -173,6 +173,17 @@ def eri_backward(plan: Plan, G, dR, dalpha, stream=None) -> None:
                                    _stream_handle(stream)), "eri_backward")
 
 
+def eri_compute_class_noalloc(cls: int, precision: str, cx, cy, cz, pofs, nprim, exps, cn, quartets,
+                              out, err, stream=None) -> None:
+    """No-allocation entry point (every argument a caller-owned CUDA tensor): FP64 or mixed ERIs
+    of quartets of one class; see include/eri.h for the contract and its limits."""
+    n = quartets.numel() // 4
+    check(_lib.load().eri_compute_class_noalloc(
+        cls, PRECISIONS[precision], _dev_ptr(cx), _dev_ptr(cy), _dev_ptr(cz), _dev_ptr(pofs),
+        _dev_ptr(nprim), _dev_ptr(exps), _dev_ptr(cn), _dev_ptr(quartets), n, _dev_ptr(out),
+        _dev_ptr(err), _stream_handle(stream)), "eri_compute_class_noalloc")
+
+
 def eri_sync(plan: Plan, stream=None) -> None:
     check(_lib.load().eri_sync(plan.handle, _stream_handle(stream)), "eri_sync")
 

@@ -51,7 +51,11 @@ def test_autotune_cache(tmp_path):
     assert len(lines) == 55  # one choice per canonical class present in the plan
     api.eri_autotune(plan, 16, packed, scales, cache)  # everything known: nothing appended
     assert len([l for l in open(cache).read().split("\n") if l]) == 55
+    # the tuned launch may use the other kernel family of a class, whose FP32 rounding differs:
+    # codes within +-1, scales within the mixed path's relative error
     ref = run(plan, 16, False)
     got = run(plan, 16, True)
-    np.testing.assert_array_equal(ref[0], got[0])
-    np.testing.assert_array_equal(ref[1], got[1])
+    a = ref[0].view(np.int16).astype(np.int64)
+    b = got[0].view(np.int16).astype(np.int64)
+    assert np.max(np.abs(a - b)) <= 1
+    np.testing.assert_allclose(got[1], ref[1], rtol=2e-5, atol=0)

@@ -33,6 +33,19 @@ from paper_2303_13632_gb300 import perfmodel, workloads as W  # noqa: E402
 METRIC = "GERIS per quartet class (int16-compressed) at stated max abs err; mixed vs FP64"
 POOL_PER_L = 4096
 BITS = 16
+STUDY_BITS = (8, 12, 16, 20)
+
+
+def unpack(words: np.ndarray, off_bytes: int, qi: np.ndarray, neri: int, bits: int) -> np.ndarray:
+    """Signed n-bit fields of quartets qi (ERIs qi*neri .. +neri) of a class segment."""
+    v = (qi[:, None].astype(np.int64) * neri + np.arange(neri)[None, :]) * bits + off_bytes * 8
+    w = v >> 5
+    o = (v & 31).astype(np.uint64)
+    lo = words[w].astype(np.uint64)
+    hi = words[np.minimum(w + 1, len(words) - 1)].astype(np.uint64)
+    raw = ((lo | (hi << np.uint64(32))) >> o) & np.uint64((1 << bits) - 1)
+    raw = raw.astype(np.int64)
+    return np.where(raw >= (1 << (bits - 1)), raw - (1 << bits), raw).astype(np.float64)
 
 
 def classes():
@@ -305,6 +318,7 @@ def run_ours(args):
 
     # ---- accuracy on a sample, and the CPU oracle baseline ----
     line_extra = {}
+    study_details = None
     if rank == 0 and not args.no_check:
         rng = np.random.default_rng(99)
         sample_idx = {c: np.sort(rng.choice(counts[c], size=min(counts[c], oracle_sample_size(cls_list[c], args.ref_eris)),
@@ -315,26 +329,68 @@ def run_ours(args):
             idx = torch.as_tensor(sample_idx[c] + first[c], device=dev, dtype=torch.int64)
             qhost[c] = quartets[idx].cpu().numpy()
         g_cpu, cores, spent, ref = cpu_oracle_rate(pool, qhost, counts)
-        errs = {}
+        # FP32 arithmetic error of the mixed path (FP64 output) on the sampled quartets
+        samp_q = np.concatenate([qhost[c] for c in nonempty(counts)])
+        samp_plan = api.eri_plan_create(pool, samp_q, precision="mixed", device=local)
+        sb, _ = api.eri_output_bytes(samp_plan, 0)
+        sout = torch.empty(sb // 8, dtype=torch.float64, device=dev)
+        arith = {}
         for prec in ("mixed", "fp64"):
-            api.eri_plan_set_precision(plan, prec)
-            step()
-            api.eri_sync(plan, stream)
-            words = packed.cpu().numpy().view(np.int16)
-            sc = scales.cpu().numpy()
-            worst = 0.0
+            api.eri_plan_set_precision(samp_plan, prec)
+            api.eri_compute(samp_plan, sout, stream)
+            api.eri_sync(samp_plan, stream)
+            host = sout.cpu().numpy()
             for c in nonempty(counts):
-                nq, neri, fq, _ = api.eri_plan_class_info(plan, c)
-                off_bytes, _ = api.eri_packed_class_offset(plan, BITS, c)
+                n_c, neri, _, off = api.eri_plan_class_info(samp_plan, c)
+                got = host[off:off + n_c * neri].reshape(n_c, neri)
                 vals, _ = ref[c]
-                qi = sample_idx[c]
-                pos = off_bytes // 2 + qi[:, None] * neri + np.arange(neri)[None, :]
-                x = words[pos].astype(np.float64) * sc[fq + qi][:, None].astype(np.float64)
-                worst = max(worst, float(np.max(np.abs(x - vals.reshape(len(qi), neri)))))
-            errs[prec] = worst
+                r = vals.reshape(n_c, neri)
+                # relative to each quartet's b_max; quartets below 1e-30 Ha (under the FP32 range
+                # after the prefactor) are left out of the relative figure
+                bm = np.max(np.abs(r), axis=1)
+                keep = bm > 1e-30
+                rel = np.max(np.abs(got - r), axis=1)[keep] / bm[keep]
+                arith.setdefault(prec, {})[c] = float(np.max(rel)) if rel.size else 0.0
+        samp_plan.destroy()
+        errs = {}
+        study = {}
+        for bits in STUDY_BITS:
+            nbw, sbw = api.eri_output_bytes(plan, bits)
+            pk = torch.empty(nbw // 4, dtype=torch.int32, device=dev) if bits != BITS else packed
+            sc_t = torch.empty(sbw // 4, dtype=torch.float32, device=dev) if bits != BITS else scales
+            for prec in ("mixed", "fp64"):
+                api.eri_plan_set_precision(plan, prec)
+                api.eri_compute_compressed(plan, bits, pk, sc_t, stream)
+                api.eri_sync(plan, stream)
+                words = pk.cpu().numpy().view(np.uint32)
+                sc = sc_t.cpu().numpy()
+                worst, half_step, within = 0.0, 0.0, 0
+                for c in nonempty(counts):
+                    nq, neri, fq, _ = api.eri_plan_class_info(plan, c)
+                    off_bytes, _ = api.eri_packed_class_offset(plan, bits, c)
+                    vals, _ = ref[c]
+                    qi = sample_idx[c]
+                    x = unpack(words, off_bytes, qi, neri, bits) * sc[fq + qi][:, None].astype(np.float64)
+                    e = float(np.max(np.abs(x - vals.reshape(len(qi), neri))))
+                    h = float(np.max(sc[fq + qi])) / 2
+                    study.setdefault(str(bits), {}).setdefault(prec, {})[fmt_class(cls_list[c])] = {
+                        "max_abs_err": e, "half_step_max": h}
+                    worst = max(worst, e)
+                    half_step = max(half_step, h)
+                    within += arith[prec][c] <= 0.5 / ((1 << (bits - 1)) - 1)
+                errs.setdefault(str(bits), {})[prec] = {"max_abs_err": worst, "half_step_max": half_step,
+                                                        "classes_arith_err_below_half_step": within}
+        api.eri_plan_set_precision(plan, "mixed")
+        line_extra["precision_study"] = errs
+        line_extra["arith_err_rel_bmax_max"] = {p_: max(arith[p_].values()) for p_ in arith}
+        if args.details:
+            study_details = {"decompressed": study,
+                             "arith_err_rel_bmax": {p_: {fmt_class(cls_list[c]): v for c, v in arith[p_].items()}
+                                                    for p_ in arith}}
+        errs16 = {prec: errs[str(BITS)][prec]["max_abs_err"] for prec in ("mixed", "fp64")}
         api.eri_plan_set_precision(plan, "mixed")
         n_sampled = sum(len(v) for v in sample_idx.values())
-        line_extra["max_abs_err"] = {"mixed": errs["mixed"], "fp64": errs["fp64"], "unit": "Ha",
+        line_extra["max_abs_err"] = {"mixed": errs16["mixed"], "fp64": errs16["fp64"], "unit": "Ha",
                                      "sample": f"{n_sampled} quartets (about {args.ref_eris} ERIs per class), "
                                                "decompressed 16-bit vs FP64 oracle"}
         line_extra["cpu_baseline"] = {"value": g_cpu, "unit": "GERIS", "cores": cores, "kind": "oracle",
@@ -372,7 +428,8 @@ def run_ours(args):
                 json.dump({"ms_mixed": {fmt_class(cls_list[c]): ms_mixed[c] for c in ms_mixed},
                            "ms_fp64": {fmt_class(cls_list[c]): ms_fp64[c] for c in ms_fp64},
                            "roofline_frac_mixed": {fmt_class(cls_list[c]): frac_all[c] for c in frac_all},
-                           "counts": {fmt_class(cls_list[c]): counts[c] for c in range(256)}}, f, indent=1)
+                           "counts": {fmt_class(cls_list[c]): counts[c] for c in range(256)},
+                           "precision_study": study_details}, f, indent=1)
     plan.destroy()
     if dist is not None:
         dist.destroy_process_group()
@@ -417,6 +474,230 @@ def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream):
             "path": "eri_plan_create(host quartets) + eri_compute_compressed + D2H of codes and scales"}
 
 
+# ---------------------------------------------------------------------------------------------
+# Further workloads (not the headline): --workload lattice | molecule | gradient
+
+
+def _events(torch, stream, fn, reps=2):
+    fn()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        fn()
+    b.record(stream)
+    b.synchronize()
+    return a.elapsed_time(b) / reps
+
+
+PAPER_TABLE5 = {"[fd|ps]": 3.33, "[ps|fd]": 1.05, "[ff|dp]": 10.03, "[dp|ff]": 6.65, "[fd|fd]": 11.17,
+                "[df|fd]": 10.93}
+
+
+def run_lattice(args):
+    """The paper's benchmark (Sec. IV-A): 32 sites on a 4x4x2 cubic lattice (1 Angstrom), one
+    primitive s, p, d, f shell per site (alpha = 1.5), all 32^4 site quartets of each class,
+    16-bit output, one class per launch as on the FPGA."""
+    import torch
+
+    import oracle
+    from paper_2303_13632_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    shells = W.lattice_shells()
+    site = torch.arange(32, device=dev, dtype=torch.int32)
+    sq = torch.cartesian_prod(site, site, site, site).to(torch.int32).contiguous()
+    n = sq.shape[0]
+    classes_ = sorted(ONLY) if ONLY else list(range(256))
+    max_eri = max(W.quartet_size(*W.class_of_id(c)) for c in classes_)
+    packed = torch.empty((n * max_eri * BITS + 31) // 32 + 64, dtype=torch.int32, device=dev)
+    scales = torch.empty(n, dtype=torch.float32, device=dev)
+    rng = np.random.default_rng(17)
+    res, acc = {}, {}
+    t_mixed = t_fp64 = 0.0
+    total = 0
+    for c in classes_:
+        cls = W.class_of_id(c)
+        neri = W.quartet_size(*cls)
+        q = (sq * 4 + torch.tensor(cls, dtype=torch.int32, device=dev)).contiguous()
+        plan = api.eri_plan_create(shells, q, precision="mixed")
+        ms = {}
+        for prec in ("mixed", "fp64"):
+            api.eri_plan_set_precision(plan, prec)
+            ms[prec] = _events(torch, stream, lambda: api.eri_compute_compressed(plan, BITS, packed, scales, stream))
+        api.eri_sync(plan, stream)
+        res[fmt_class(cls)] = {"mixed": n * neri / ms["mixed"] / 1e6, "fp64": n * neri / ms["fp64"] / 1e6}
+        t_mixed += ms["mixed"]
+        t_fp64 += ms["fp64"]
+        total += n * neri
+        if not args.no_check:
+            # accuracy after decompression on a sample, 16 and 12 bits, mixed precision
+            k = max(2, min(64, 50000 // neri))
+            qi = np.sort(rng.choice(n, size=k, replace=False))
+            ref, _ = oracle.eri_batch(shells, q[torch.as_tensor(qi, device=dev)].cpu().numpy())
+            ref = ref.reshape(k, neri)
+            api.eri_plan_set_precision(plan, "mixed")
+            e = {}
+            for bits in (16, 12):
+                api.eri_compute_compressed(plan, bits, packed, scales, stream)
+                api.eri_sync(plan, stream)
+                words = packed.cpu().numpy().view(np.uint32)
+                x = unpack(words, 0, qi, neri, bits) * scales.cpu().numpy()[qi][:, None].astype(np.float64)
+                e[bits] = float(np.max(np.abs(x - ref)))
+            acc[fmt_class(cls)] = e
+        plan.destroy()
+    out = {"impl": "ours", "workload": "lattice", "metric": "GERIS per class, 16-bit, paper lattice (Sec. IV-A)",
+           "value": total / (t_mixed * 1e-3) / 1e9, "unit": "GERIS", "fp64_value": total / (t_fp64 * 1e-3) / 1e9,
+           "classes": len(classes_), "quartets_per_class": n,
+           "paper_table5_fpga_vs_ours_mixed": {k: {"fpga": v, "ours": res[k]["mixed"]} for k, v in PAPER_TABLE5.items() if k in res},
+           "per_class_geris": res}
+    if acc:
+        canon = [k for k in acc]
+        out["max_abs_err_16bit"] = max(acc[k][16] for k in canon)
+        out["max_abs_err_12bit_except_ssss"] = max(acc[k][12] for k in canon if k != "[ss|ss]")
+        out["accuracy_per_class"] = acc
+    print(json.dumps(out), flush=True)
+
+
+def run_molecule(args):
+    """Batched mixed workload: 200 atoms in a 20-bohr box (min separation 1.8 bohr), shells
+    s, s, p, p, d, f per atom, contraction degree 1..6, all unique (8-fold) shell quartets
+    surviving Schwarz screening at 1e-10 counted; a seeded budget of about 2^30 ERIs of them
+    computed in one CUDA-graph launch of persistent kernels (mixed precision, 16-bit)."""
+    import torch
+
+    import oracle
+    from paper_2303_13632_gb300 import api, screening as S
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    basis = W.molecule_basis()
+    pairs = S.unique_pairs(basis)
+    t0 = time.perf_counter()
+    qdiag = np.stack([pairs[:, 0], pairs[:, 1], pairs[:, 0], pairs[:, 1]], axis=1).astype(np.int32)
+    dplan = api.eri_plan_create(basis, qdiag, precision="fp64")
+    nb, sb = api.eri_output_bytes(dplan, 8)
+    pk = torch.empty(nb // 4, dtype=torch.int32, device=dev)
+    sc = torch.empty(sb // 4, dtype=torch.float32, device=dev)
+    api.eri_compute_compressed(dplan, 8, pk, sc, stream)
+    api.eri_sync(dplan, stream)
+    bmax = np.zeros(len(pairs))
+    bmax[api.eri_plan_quartet_order(dplan)] = sc.cpu().numpy().astype(np.float64) * 127.0
+    dplan.destroy()
+    t_schwarz = time.perf_counter() - t0
+    tau = 1e-10
+    sq = S.ScreenedQuartets(basis, pairs, np.sqrt(bmax), tau)
+    counts = sq.class_counts()
+    n_unique = int(sum(counts.values()))
+    eris_all = int(sum(v * W.quartet_size(*W.class_of_id(k)) for k, v in counts.items()))
+    rng = np.random.default_rng(W.SEED_BASE + 4)
+    budget = int(2 ** 30 * args.scale)
+    q = sq.sample(rng, budget)
+    plan = api.eri_plan_create(basis, q, precision="mixed")
+    n_eri = int(oracle.quartet_sizes(basis, q).sum())
+    nb, sb = api.eri_output_bytes(plan, BITS)
+    packed = torch.empty(nb // 4, dtype=torch.int32, device=dev)
+    scales = torch.empty(sb // 4, dtype=torch.float32, device=dev)
+    ms_plain = _events(torch, stream, lambda: api.eri_compute_compressed(plan, BITS, packed, scales, stream))
+    cache = os.path.join(tempfile.gettempdir(), "eri_autotune_molecule.txt")
+    api.eri_autotune(plan, BITS, packed, scales, cache, stream)
+    ms_graph = _events(torch, stream, lambda: api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream), reps=3)
+    api.eri_plan_set_precision(plan, "fp64")
+    ms_fp64 = _events(torch, stream, lambda: api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream), reps=1)
+    api.eri_plan_set_precision(plan, "mixed")
+    api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream)
+    api.eri_sync(plan, stream)
+    out = {"impl": "ours", "workload": "molecule",
+           "metric": "GERIS, batched persistent CUDA-graph launch, mixed precision, 16-bit",
+           "value": n_eri / (ms_graph * 1e-3) / 1e9, "unit": "GERIS",
+           "per_class_launches_geris": n_eri / (ms_plain * 1e-3) / 1e9,
+           "fp64_batched_geris": n_eri / (ms_fp64 * 1e-3) / 1e9,
+           "budget": {"quartets": int(len(q)), "eris": n_eri},
+           "screened_unique_quartets": n_unique, "screened_unique_eris": eris_all,
+           "shells": int(basis.n), "pairs": int(len(pairs)), "schwarz_s": t_schwarz, "tau": tau}
+    if not args.no_check:
+        # parity on sampled quartets of modest primitive count
+        L = np.asarray(basis.L)
+        kprod = np.prod([basis.nprim[q[:, x]] for x in range(4)], axis=0)
+        cost = kprod * oracle.quartet_sizes(basis, q)
+        cand = np.nonzero(cost <= 200000)[0]
+        pick = np.sort(rng.choice(cand, size=min(200, len(cand)), replace=False))
+        ref, offs = oracle.eri_batch(basis, q[pick])
+        order = api.eri_plan_quartet_order(plan)
+        pos = np.empty(len(order), dtype=np.int64)
+        pos[order] = np.arange(len(order))
+        words = packed.cpu().numpy().view(np.uint32)
+        scl = scales.cpu().numpy()
+        worst_rel = 0.0
+        for j, i in enumerate(pick):
+            cls = W.class_id(*[int(L[s]) for s in q[i]])
+            nq_c, neri, fq, _ = api.eri_plan_class_info(plan, cls)
+            off_b, _ = api.eri_packed_class_offset(plan, BITS, cls)
+            k = int(pos[i] - fq)
+            x = unpack(words, off_b, np.array([k]), neri, BITS)[0] * float(scl[pos[i]])
+            r = ref[offs[j]:offs[j + 1]]
+            bm = max(np.max(np.abs(r)), 1e-300)
+            worst_rel = max(worst_rel, float(np.max(np.abs(x - r)) / bm))
+        out["parity_sample"] = {"quartets": int(len(pick)), "max_err_rel_bmax": worst_rel,
+                                "bound_16bit_half_step_plus_fp32": 1.0 / 32767}
+    print(json.dumps(out), flush=True)
+
+
+def run_gradient(args):
+    """Differentiation: dE/dR and dE/dalpha of E = sum G (ab|cd) for the 16 classes with every
+    L in {1, 2}, 2^18 quartets each, contraction degree 3, G ~ N(0, 1)."""
+    import torch
+
+    import oracle
+    from paper_2303_13632_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    rng = W.rng_for(5)
+    pool = W.random_contracted_pool(rng, 2048, K=3, Ls=(1, 2))
+    cls_list_ = [c for c in [(a, b, c_, d) for a in (1, 2) for b in (1, 2) for c_ in (1, 2) for d in (1, 2)]]
+    nper = max(1, int((1 << 18) * args.scale))
+    q = np.concatenate([W.random_class_quartets(rng, c, nper, 2048, Ls=(1, 2)) for c in cls_list_])
+    plan = api.eri_plan_create(pool, q, precision="fp64")
+    nb, _ = api.eri_output_bytes(plan, 0)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_BASE + 5)
+    G = torch.randn(nb // 8, dtype=torch.float64, device=dev, generator=gen)
+    dR = torch.empty((pool.n, 3), dtype=torch.float64, device=dev)
+    da = torch.empty(len(pool.exps), dtype=torch.float64, device=dev)
+    ms_bwd = _events(torch, stream, lambda: api.eri_backward(plan, G, dR, da, stream), reps=1)
+    out_t = torch.empty(nb // 8, dtype=torch.float64, device=dev)
+    ms_fwd = _events(torch, stream, lambda: api.eri_compute(plan, out_t, stream), reps=1)
+    api.eri_sync(plan, stream)
+    n_eri = nb // 8
+    out = {"impl": "ours", "workload": "gradient", "metric": "adjoint: ERI derivatives contracted per second",
+           "value": n_eri / (ms_bwd * 1e-3) / 1e9, "unit": "G ERI/s (backward)", "forward_geris_fp64": n_eri / (ms_fwd * 1e-3) / 1e9,
+           "ms_backward": ms_bwd, "ms_forward": ms_fwd, "quartets": int(len(q)), "eris": int(n_eri), "K": 3}
+    if not args.no_check:
+        # oracle derivative on a sample: a plan of the sampled quartets alone, same G values
+        pick = np.sort(rng.choice(len(q), size=64, replace=False))
+        qs = q[pick]
+        sizes = oracle.quartet_sizes(pool, qs)
+        offs = np.zeros(len(qs) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=offs[1:])
+        Gs = np.random.default_rng(9).standard_normal(int(offs[-1]))
+        splan = api.eri_plan_create(pool, qs, precision="fp64")
+        order = api.eri_plan_quartet_order(splan)
+        Gd = torch.tensor(np.concatenate([Gs[offs[i]:offs[i + 1]] for i in order]), device=dev)
+        api.eri_backward(splan, Gd, dR, da, stream)
+        api.eri_sync(splan, stream)
+        rR, ra = oracle.eri_grad_batch(pool, qs, Gs, offs)
+        gR, ga = dR.cpu().numpy(), da.cpu().numpy()
+        out["oracle_check"] = {"quartets": 64, "max_abs_err_dR": float(np.max(np.abs(gR - rR))),
+                               "max_abs_dR": float(np.max(np.abs(rR))),
+                               "max_abs_err_dalpha": float(np.max(np.abs(ga - ra))),
+                               "max_abs_dalpha": float(np.max(np.abs(ra)))}
+    print(json.dumps(out), flush=True)
+
+
 def fmt_class(cls):
     s = "spdf"
     return f"[{s[cls[0]]}{s[cls[1]]}|{s[cls[2]]}{s[cls[3]]}]"
@@ -428,6 +709,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "lattice", "molecule", "gradient"],
+                    help="sweep (default): the 256-class benchmark; the others are further studies")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--ref-eris", type=int, default=1500000)
     ap.add_argument("--no-check", action="store_true")
@@ -441,6 +724,12 @@ def main():
         ONLY = {int(c) for c in args.classes.split(",")}
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "lattice":
+        run_lattice(args)
+    elif args.workload == "molecule":
+        run_molecule(args)
+    elif args.workload == "gradient":
+        run_gradient(args)
     else:
         run_ours(args)
 

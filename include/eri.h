@@ -107,6 +107,22 @@ void eri_plan_destroy(eri_plan_t plan);
 /* Changes the precision used by later compute calls (ERI_FP64 or ERI_MIXED). */
 eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);
 
+/* Precision of one class, overriding the plan's (ERI_FP64, ERI_MIXED, or -1 to follow the plan). */
+eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision);
+
+/* Chooses the precision of every class of the plan for `bits`-bit output: FP32 recurrences
+ * (ERI_MIXED) where the measured error stays below a quarter of the quantisation step, FP64
+ * elsewhere.  The error of a class is max |mixed - FP64| / b_max over its first `sample`
+ * quartets, both computed on the device (quartets with b_max <= 1e-30 Ha are left out), so it
+ * is a sample estimate.  Allocates temporary device buffers; synchronous on `stream`. */
+eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t sample,
+                                          void *stream);
+
+/* Effective precision of a class and the error measured by eri_plan_calibrate_precision
+ * (-1 when not measured).  Either output may be NULL. */
+eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *precision,
+                                      float *mixed_err);
+
 /* Total quartets in the plan. */
 eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);
 

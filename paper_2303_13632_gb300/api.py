@@ -99,6 +99,24 @@ def eri_plan_set_precision(plan: Plan, precision: str) -> None:
     check(_lib.load().eri_plan_set_precision(plan.handle, PRECISIONS[precision]), "eri_plan_set_precision")
 
 
+def eri_plan_set_class_precision(plan: Plan, cls: int, precision: str | None) -> None:
+    v = -1 if precision is None else PRECISIONS[precision]
+    check(_lib.load().eri_plan_set_class_precision(plan.handle, cls, v), "eri_plan_set_class_precision")
+
+
+def eri_plan_calibrate_precision(plan: Plan, bits: int, sample: int = 4096, stream=None) -> None:
+    check(_lib.load().eri_plan_calibrate_precision(plan.handle, bits, sample, _stream_handle(stream)),
+          "eri_plan_calibrate_precision")
+
+
+def eri_plan_class_precision(plan: Plan, cls: int):
+    """Returns (precision name, measured mixed error or -1)."""
+    p, e = ctypes.c_int32(), ctypes.c_float()
+    check(_lib.load().eri_plan_class_precision(plan.handle, cls, ctypes.byref(p), ctypes.byref(e)),
+          "eri_plan_class_precision")
+    return ("fp64" if p.value == ERI_FP64 else "mixed"), float(e.value)
+
+
 def eri_plan_num_quartets(plan: Plan) -> int:
     n = ctypes.c_int64()
     check(_lib.load().eri_plan_num_quartets(plan.handle, ctypes.byref(n)), "eri_plan_num_quartets")

@@ -38,11 +38,12 @@ struct GCfg {
     static constexpr int H_BYTES = 3 * NRYS * HBLK * 8;
     static constexpr int I_BYTES = 3 * NRYS * IBLKP * 8;
     static constexpr int NACC = 17;  // dR[4][3], dalpha-part[4], E
-    static constexpr int PERQ = GEO_BYTES + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 + 64;
+    static constexpr int PERQ = GEO_BYTES + RG_N * 8 + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 + 64;
     static constexpr int Q = imax(1, imin(8, (100 * 1024) / PERQ));
     static constexpr int THREADS = 256;
     static constexpr int OFF_GEO = 0;
-    static constexpr int OFF_BC = Q * GEO_BYTES;
+    static constexpr int OFF_RG = Q * GEO_BYTES;
+    static constexpr int OFF_BC = OFF_RG + Q * RG_N * 8;
     static constexpr int OFF_ACC = OFF_BC + Q * BC_BYTES;
     static constexpr int OFF_DR = OFF_ACC + Q * NACC * 8;        // centre gradients, all primitives
     static constexpr int OFF_PRIM = OFF_DR + Q * 12 * 8;          // primitive ids + exponents
@@ -62,6 +63,7 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                     double *__restrict__ dR, double *__restrict__ dalpha) {
     extern __shared__ __align__(16) unsigned char smem[];
     double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
+    double *rg_s = reinterpret_cast<double *>(smem + C::OFF_RG);
     double *bc_s = reinterpret_cast<double *>(smem + C::OFF_BC);
     double *acc_s = reinterpret_cast<double *>(smem + C::OFF_ACC);
     double *dr_s = reinterpret_cast<double *>(smem + C::OFF_DR);
@@ -114,6 +116,15 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                                                                               : (s == G_IPQ ? 0.5 : 0.0);
             }
             if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+            double *rg = rg_s + q * RG_N;
+            rg[RG_ABX] = geo[G_ABX];
+            rg[RG_ABY] = geo[G_ABY];
+            rg[RG_ABZ] = geo[G_ABZ];
+            rg[RG_CDX] = geo[G_CDX];
+            rg[RG_CDY] = geo[G_CDY];
+            rg[RG_CDZ] = geo[G_CDZ];
+            rg[RG_SWAB] = geo[G_SWAB];
+            rg[RG_SWCD] = geo[G_SWCD];
             if (q >= qn || prim >= np) {
                 for (int k = 0; k < 4; ++k) {
                     prim_s[q * 8 + k] = 1.0;
@@ -129,7 +140,7 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
         __syncthreads();
         for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
             int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
-            phase_vrr<C>(bc_s + q * C::NRYS * S_N, geo_s + q * G_N, r / 3, r % 3,
+            phase_vrr<C>(bc_s + q * C::NRYS * S_N, rg_s + q * RG_N, r / 3, r % 3,
                          H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
         }
         __syncthreads();
@@ -140,7 +151,7 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                 int mu = r / (3 * NIJ);
                 r %= 3 * NIJ;
                 int xi = r / NIJ, ij = r % NIJ;
-                phase_ket<C>(geo_s + q * G_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
+                phase_ket<C>(rg_s + q * RG_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
                              H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
             }
         }

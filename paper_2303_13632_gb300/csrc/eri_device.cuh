@@ -15,6 +15,7 @@ namespace eri {
 
 constexpr int kRysNmax = 9;
 constexpr int kRysDeg = 12;
+constexpr int kRysTail = 8;  // coefficients j >= kRysTail are evaluated in FP32
 constexpr int kBoysMmax = 16;
 constexpr int kBoysTaylor = 10;
 constexpr int kBoysCols = kBoysMmax + kBoysTaylor + 1;
@@ -34,6 +35,7 @@ __device__ __forceinline__ double inv_int(int j) {
 // Device addresses of the generated tables (see eri_tables.cu).
 struct Tables {
     const double *rys_cheb;
+    const float *rys_tail;  // FP32 copies of coefficients kRysTail..kRysDeg of every series
     const double *herm_x2;
     const double *herm_w;
     const double *boys_grid;
@@ -129,11 +131,23 @@ __device__ __forceinline__ void boys_f01(double T, const double *__restrict__ gr
     }
 }
 
-// Chebyshev series sum_j c_j T_j(u) by Clenshaw's recurrence.
-__device__ __forceinline__ double cheb_eval(const double *__restrict__ c, double u) {
-    double b1 = 0.0, b2 = 0.0, u2 = 2.0 * u;
+// Chebyshev series sum_j c_j T_j(u) by Clenshaw's recurrence.  The terms j >= kRysTail sum to
+// less than 1e-9 of the series' smallest value on the piece (checked when the tables are
+// generated), so that part of the recurrence runs in FP32 from FP32 coefficients without
+// disturbing the FP64 result by more than 1e-16 relative; the rest runs in FP64.
+__device__ __forceinline__ double cheb_eval(const double *__restrict__ c,
+                                            const float *__restrict__ ct, double u) {
+    const float u2f = 2.0f * (float)u;
+    float b1f = 0.0f, b2f = 0.0f;
 #pragma unroll
-    for (int j = kRysDeg; j >= 1; --j) {
+    for (int j = kRysDeg; j >= kRysTail; --j) {
+        float t = fmaf(u2f, b1f, __ldg(ct + (j - kRysTail)) - b2f);
+        b2f = b1f;
+        b1f = t;
+    }
+    double b1 = (double)b1f, b2 = (double)b2f, u2 = 2.0 * u;
+#pragma unroll
+    for (int j = kRysTail - 1; j >= 1; --j) {
         double t = fma(u2, b1, __ldg(c + j) - b2);
         b2 = b1;
         b1 = t;
@@ -154,10 +168,11 @@ __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double
     if (T < (double)tb.tasym[n]) {
         int k = (int)T;
         double u = 2.0 * (T - k) - 1.0;
-        const double *c = tb.rys_cheb + tb.offset[n] + (long long)k * (2 * n * (kRysDeg + 1)) +
-                          (2 * mu) * (kRysDeg + 1);
-        x = cheb_eval(c, u);
-        w = cheb_eval(c + (kRysDeg + 1), u);
+        const long long f = (tb.offset[n] / (kRysDeg + 1)) + (long long)k * (2 * n) + 2 * mu;
+        const double *c = tb.rys_cheb + f * (kRysDeg + 1);
+        const float *ct = tb.rys_tail + f * (kRysDeg + 1 - kRysTail);
+        x = cheb_eval(c, ct, u);
+        w = cheb_eval(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTail), u);
     } else {
         int h = tb.herm_off[n] + mu;
         x = __ldg(tb.herm_x2 + h) / T;

@@ -72,6 +72,8 @@ enum GeoSlot {
     G_T = 0, G_PREF, G_P, G_Q, G_PAX, G_PAY, G_PAZ, G_QCX, G_QCY, G_QCZ, G_PQX, G_PQY, G_PQZ,
     G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD, G_IP, G_IQ, G_IPQ, G_N
 };
+// Per-quartet geometry the recurrence stages read, in the recurrence type R (no FP64 there).
+enum RGeoSlot { RG_ABX = 0, RG_ABY, RG_ABZ, RG_CDX, RG_CDY, RG_CDZ, RG_SWAB, RG_SWCD, RG_N };
 // Per (quartet, root) setup values kept in shared memory (type R).
 enum BCSlot { S_B00 = 0, S_B10, S_B01, S_C0X, S_C0Y, S_C0Z, S_C1X, S_C1Y, S_C1Z, S_WZ, S_N };
 
@@ -104,7 +106,7 @@ struct Cfg {
     static constexpr int I_BYTES = 3 * NRYS * IBLKP * (int)sizeof(R);
     static constexpr int STAGE_BYTES = NERI * 3;  // worst case 24-bit codes
     static constexpr int UNION_BYTES = imax(H_BYTES + I_BYTES, STAGE_BYTES);
-    static constexpr int PERQ = GEO_BYTES + BC_BYTES + UNION_BYTES + 8;
+    static constexpr int PERQ = GEO_BYTES + RG_N * (int)sizeof(R) + BC_BYTES + UNION_BYTES + 8;
     static constexpr int SMEM_BUDGET = 96 * 1024;
     static constexpr int QMAX_T = imax(1, 256 / ITEMS_D);
     static constexpr int QMAX_S = imax(1, SMEM_BUDGET / PERQ);
@@ -112,7 +114,8 @@ struct Cfg {
     static constexpr int THREADS = imax(64, cdiv(Q * ITEMS_D, 32) * 32);
     // shared memory layout (byte offsets)
     static constexpr int OFF_GEO = 0;
-    static constexpr int OFF_BC = OFF_GEO + Q * GEO_BYTES;
+    static constexpr int OFF_RG = OFF_GEO + Q * GEO_BYTES;
+    static constexpr int OFF_BC = ((OFF_RG + Q * RG_N * (int)sizeof(R) + 15) / 16) * 16;
     static constexpr int OFF_BMAX = ((OFF_BC + Q * BC_BYTES + 15) / 16) * 16;
     static constexpr int OFF_U = ((OFF_BMAX + Q * 8 + 15) / 16) * 16;
     static constexpr int OFF_H = OFF_U;
@@ -152,9 +155,11 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     double Cc[3] = {sh.cx[qt.z], sh.cy[qt.z], sh.cz[qt.z]};
     double D[3] = {sh.cx[qt.w], sh.cy[qt.w], sh.cz[qt.w]};
     double p = ea + eb, q = ec + ed;
-    // 1/p and 1/q from one FP64 division
-    double ipq_prod = 1.0 / (p * q);
-    double ip = q * ipq_prod, iq = p * ipq_prod;
+    // 1/p and 1/q from one FP64 division; 1/(p+q) as rsqrt(p+q)^2 (no second division)
+    const double pq = p * q;
+    const double ipq_prod = 1.0 / pq;
+    const double ip = q * ipq_prod, iq = p * ipq_prod;
+    const double rs = rsqrt(p + q);
     double ab2 = 0.0, cd2 = 0.0, pq2 = 0.0;
 #pragma unroll
     for (int x = 0; x < 3; ++x) {
@@ -172,14 +177,14 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
         cd2 += CD * CD;
         pq2 += PQ * PQ;
     }
-    double ipq = 1.0 / (p + q);
-    double rho = p * q * ipq;
+    const double ipq = rs * rs;
+    const double rho = pq * ipq;
     // K_AB K_CD = exp(-(ab/p |A-B|^2 + cd/q |C-D|^2)) in one FP64 exponential
-    double kabcd = exp(-(ea * eb * ip * ab2 + ec * ed * iq * cd2));
+    const double kabcd = exp(-(ea * eb * ip * ab2 + ec * ed * iq * cd2));
     // 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD times the four coef * N factors
     const double two_pi_52 = 34.986836655249725;
-    geo[G_PREF] = two_pi_52 * ip * iq * rsqrt(p + q) * kabcd * sh.cn[pa] * sh.cn[pb] *
-                  sh.cn[pc] * sh.cn[pd];
+    geo[G_PREF] = two_pi_52 * ipq_prod * rs * kabcd * (sh.cn[pa] * sh.cn[pb]) *
+                  (sh.cn[pc] * sh.cn[pd]);
     geo[G_T] = rho * pq2;
     geo[G_P] = p;
     geo[G_Q] = q;
@@ -302,14 +307,14 @@ __device__ __forceinline__ int i_index(int xi, int mu, int i, int k, int j, int 
 
 // Phase B: VRR column by column in k, bra HRR of each column; writes H (or I when fused).
 template <class C>
-__device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double *geo, int mu,
+__device__ __forceinline__ void phase_vrr(const typename C::R *bc, const typename C::R *rg, int mu,
                                           int xi, typename C::R *Hq, typename C::R *Iq) {
     using R = typename C::R;
     const R *b = bc + mu * S_N;
     R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
     R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
-    R ab = (R)geo[G_ABX + xi];
-    const bool swab = geo[G_SWAB] != 0.0;
+    R ab = rg[RG_ABX + xi];
+    const bool swab = rg[RG_SWAB] != (R)0;
     R prev[C::NAB + 1], cur[C::NAB + 1];
     // column k = 0: G(i+1, 0) = C00 G(i, 0) + i B10 G(i-1, 0)
     cur[0] = (xi == 2) ? b[S_WZ] : (R)1;
@@ -354,8 +359,8 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
         }
     }
     if constexpr (C::FUSE_BC) {
-        R cd = (R)geo[G_CDX + xi];
-        const bool swcd = geo[G_SWCD] != 0.0;
+        R cd = rg[RG_CDX + xi];
+        const bool swcd = rg[RG_SWCD] != (R)0;
 #pragma unroll
         for (int i = 0; i <= C::La; ++i)
 #pragma unroll
@@ -376,13 +381,13 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const double 
 // VRR + bra HRR + ket HRR of one (root, axis) entirely in registers: I[(i, k, j, l)] in the
 // layout of i_index for fixed (xi, mu).  Used by the thread-per-quartet kernel.
 template <class C>
-__device__ __forceinline__ void axis_2d(const typename C::R *b, const double *geo, int xi,
+__device__ __forceinline__ void axis_2d(const typename C::R *b, const typename C::R *rg, int xi,
                                         typename C::R (&I)[C::IBLK]) {
     using R = typename C::R;
     R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
     R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
-    R ab = (R)geo[G_ABX + xi], cd = (R)geo[G_CDX + xi];
-    const bool swab = geo[G_SWAB] != 0.0, swcd = geo[G_SWCD] != 0.0;
+    R ab = rg[RG_ABX + xi], cd = rg[RG_CDX + xi];
+    const bool swab = rg[RG_SWAB] != (R)0, swcd = rg[RG_SWCD] != (R)0;
     R prev[C::NAB + 1], cur[C::NAB + 1];
     cur[0] = (xi == 2) ? b[S_WZ] : (R)1;
 #pragma unroll
@@ -434,7 +439,7 @@ __device__ __forceinline__ void axis_2d(const typename C::R *b, const double *ge
 
 // Phase C: ket HRR for one (mu, xi, i, j).
 template <class C>
-__device__ __forceinline__ void phase_ket(const double *geo, int mu, int xi, int i, int j,
+__device__ __forceinline__ void phase_ket(const typename C::R *rg, int mu, int xi, int i, int j,
                                           const typename C::R *Hq, typename C::R *Iq) {
     using R = typename C::R;
     R s[C::NCD + 1];
@@ -442,7 +447,7 @@ __device__ __forceinline__ void phase_ket(const double *geo, int mu, int xi, int
 #pragma unroll
     for (int k = 0; k <= C::NCD; ++k) s[k] = src[k];
     R o[C::Lc + 1][C::Ld + 1];
-    ket_hrr<C>(s, (R)geo[G_CDX + xi], geo[G_SWCD] != 0.0, o);
+    ket_hrr<C>(s, rg[RG_CDX + xi], rg[RG_SWCD] != (R)0, o);
 #pragma unroll
     for (int k = 0; k <= C::Lc; ++k)
 #pragma unroll
@@ -557,6 +562,7 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                                            unsigned char *smem) {
     using R = typename C::R;
     double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
+    R *rg_s = reinterpret_cast<R *>(smem + C::OFF_RG);
     R *bc_s = reinterpret_cast<R *>(smem + C::OFF_BC);
     unsigned long long *bmax_s = reinterpret_cast<unsigned long long *>(smem + C::OFF_BMAX);
     R *H_s = reinterpret_cast<R *>(smem + C::OFF_H);
@@ -587,10 +593,9 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
             // setup values of the tile, field-major in the setup buffer (coalesced loads)
             const R *su = reinterpret_cast<const R *>(args.setup);
             const long long ss = args.setup_stride;
-            constexpr int gslot[8] = {G_ABX, G_ABY, G_ABZ, G_CDX, G_CDY, G_CDZ, G_SWAB, G_SWCD};
             for (int it = tid; it < C::Q * C::SETUP_GEO; it += C::THREADS) {
                 int f = it / C::Q, q = it % C::Q;
-                geo_s[q * G_N + gslot[f]] = q < qn ? (double)su[f * ss + q0 + q] : 0.0;
+                rg_s[q * RG_N + f] = q < qn ? su[f * ss + q0 + q] : (R)0;
             }
             for (int it = tid; it < C::Q * C::NRYS * S_N; it += C::THREADS) {
                 int f = it / C::Q, q = it % C::Q;
@@ -615,6 +620,15 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                                                                                   : (s == G_IPQ ? 0.5 : 0.0);
                 }
                 if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
+                R *rg = rg_s + q * RG_N;
+                rg[RG_ABX] = (R)geo[G_ABX];
+                rg[RG_ABY] = (R)geo[G_ABY];
+                rg[RG_ABZ] = (R)geo[G_ABZ];
+                rg[RG_CDX] = (R)geo[G_CDX];
+                rg[RG_CDY] = (R)geo[G_CDY];
+                rg[RG_CDZ] = (R)geo[G_CDZ];
+                rg[RG_SWAB] = (R)geo[G_SWAB];
+                rg[RG_SWCD] = (R)geo[G_SWCD];
             }
             __syncthreads();
             // A1: roots, weights, B and C per (quartet, root)
@@ -628,7 +642,7 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
         for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
             int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
             int mu = r / 3, xi = r % 3;
-            phase_vrr<C>(bc_s + q * C::NRYS * S_N, geo_s + q * G_N, mu, xi,
+            phase_vrr<C>(bc_s + q * C::NRYS * S_N, rg_s + q * RG_N, mu, xi,
                          H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
                          I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
         }
@@ -640,7 +654,7 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 int mu = r / (3 * NIJ);
                 r %= 3 * NIJ;
                 int xi = r / NIJ, ij = r % NIJ;
-                phase_ket<C>(geo_s + q * G_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
+                phase_ket<C>(rg_s + q * RG_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
                              H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
                              I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
             }
@@ -726,17 +740,22 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
     for (int w = tid; w < nw; w += C::THREADS) stage[w] = 0u;
     __syncthreads();
     if (live) {
-        const double M = (double)((1u << (bits - 1)) - 1u);
-        double bmax;
-        if constexpr (sizeof(R) == 8)
-            bmax = __longlong_as_double((long long)bmax_s[dq]);
-        else
-            bmax = (double)__uint_as_float(*reinterpret_cast<const unsigned int *>(bmax_s + dq));
-        float eps = (float)(bmax / M);
+        // eps = b_max / M rounded to FP32 (Eq. 9).  In mixed precision b_max is an FP32 value and
+        // M is exact in FP32, so the correctly rounded FP32 quotient is that rounding.
+        float eps;
+        R inv;
+        if constexpr (sizeof(R) == 8) {
+            const double M = (double)((1u << (bits - 1)) - 1u);
+            eps = (float)(__longlong_as_double((long long)bmax_s[dq]) / M);
+            inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
+        } else {
+            const float M = (float)((1u << (bits - 1)) - 1u);
+            eps = __uint_as_float(*reinterpret_cast<const unsigned int *>(bmax_s + dq)) / M;
+            inv = (eps > 0.0f) ? (R)(1.0f / eps) : (R)0;
+        }
         if (da == 0 && dc == 0 && dch == 0) args.scales[q0 + dq] = eps;
-        R inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
         const uint32_t mask = (1u << bits) - 1u;
-        const R Mr = (R)M;
+        const R Mr = (R)((1u << (bits - 1)) - 1u);
         const long long qbase = (q0 + dq) * (long long)C::NERI + da * st0 + dc * st2;
 #pragma unroll
         for (int bb = 0; bb < C::BCH; ++bb) {
@@ -862,14 +881,22 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
         for (int prim = 0; prim < nprim; ++prim) {
             double geo[G_N];
             phase_geometry<C>(sh, qt, prim, geo, nprim);
+            R rg[RG_N];
+#pragma unroll
+            for (int x = 0; x < 3; ++x) {
+                rg[RG_ABX + x] = (R)geo[G_ABX + x];
+                rg[RG_CDX + x] = (R)geo[G_CDX + x];
+            }
+            rg[RG_SWAB] = (R)geo[G_SWAB];
+            rg[RG_SWCD] = (R)geo[G_SWCD];
 #pragma unroll 1
             for (int mu = 0; mu < C::NRYS; ++mu) {
                 R bc[S_N];
                 phase_setup<C>(tb, geo, mu, bc);
                 R X[C::IBLK], Y[C::IBLK], Z[C::IBLK];
-                axis_2d<C>(bc, geo, 0, X);
-                axis_2d<C>(bc, geo, 1, Y);
-                axis_2d<C>(bc, geo, 2, Z);
+                axis_2d<C>(bc, rg, 0, X);
+                axis_2d<C>(bc, rg, 1, Y);
+                axis_2d<C>(bc, rg, 2, Z);
 #pragma unroll
                 for (int a = 0; a < C::NA; ++a)
 #pragma unroll
@@ -930,12 +957,19 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
             m = v > m ? v : m;
         }
         if (bad) atomicOr(args.err, 1);
-        const double M = (double)((1u << (bits - 1)) - 1u);
-        float eps = (float)((double)m / M);
+        float eps;
+        R inv;
+        if constexpr (sizeof(R) == 8) {
+            const double M = (double)((1u << (bits - 1)) - 1u);
+            eps = (float)((double)m / M);
+            inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
+        } else {
+            eps = (float)m / (float)((1u << (bits - 1)) - 1u);
+            inv = (eps > 0.0f) ? (R)(1.0f / eps) : (R)0;
+        }
         args.scales[q0 + tid] = eps;
-        R inv = (eps > 0.0f) ? (R)(1.0 / (double)eps) : (R)0;
         const uint32_t mask = (1u << bits) - 1u;
-        const R Mr = (R)M;
+        const R Mr = (R)((1u << (bits - 1)) - 1u);
         const long long qbase = (q0 + tid) * (long long)C::NERI;
 #pragma unroll
         for (int a = 0; a < C::NA; ++a)

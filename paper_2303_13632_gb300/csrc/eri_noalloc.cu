@@ -1,4 +1,4 @@
-// eri_noalloc.cu -- eri_compute_class_noalloc: FP64 ERIs of one class without any device
+// eri_noalloc.cu -- eri_compute_class_noalloc: ERIs of one class (FP64 or mixed) without any device
 // allocation by this library.
 //
 // Some callers cannot let a library call cudaMalloc: applications that reserve all device
@@ -80,6 +80,8 @@ cudaError_t device_state(DeviceState **out) {
         t.herm_w = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::boys_grid_h)) != cudaSuccess) return e;
         t.boys_grid = static_cast<const double *>(p);
+        if ((e = cudaGetSymbolAddress(&p, device_tables::rys_tail_f_h)) != cudaSuccess) return e;
+        t.rys_tail = static_cast<const float *>(p);
         for (int i = 0; i <= kRysNmax; ++i) {
             t.tasym[i] = host_tables::rys_tasym_h[i];
             t.offset[i] = host_tables::rys_offset_h[i];

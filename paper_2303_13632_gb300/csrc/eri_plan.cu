@@ -121,6 +121,27 @@ __global__ void histogram_kernel(const uint8_t *__restrict__ keys, long long n,
         if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
 }
 
+// Largest |b - a| / max|a| over the quartets (a: FP64 values, b: mixed values) of n quartets of
+// neri values each; quartets with max|a| <= 1e-30 (below the FP32 range once scaled) are
+// skipped.  One warp per quartet; the result (non-negative float) is atomically max-ed in bits.
+__global__ void calib_kernel(const double *__restrict__ a, const double *__restrict__ b, long long n,
+                             int neri, unsigned int *out) {
+    long long q = ((long long)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+    int lane = threadIdx.x & 31;
+    if (q >= n) return;
+    const double *x = a + q * neri, *y = b + q * neri;
+    double m = 0.0, d = 0.0;
+    for (int i = lane; i < neri; i += 32) {
+        m = fmax(m, fabs(x[i]));
+        d = fmax(d, fabs(y[i] - x[i]));
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+        m = fmax(m, __shfl_down_sync(0xffffffffu, m, off));
+        d = fmax(d, __shfl_down_sync(0xffffffffu, d, off));
+    }
+    if (lane == 0 && m > 1e-30) atomicMax(out, __float_as_uint((float)(d / m)));
+}
+
 }  // namespace
 
 }  // namespace eri
@@ -150,6 +171,9 @@ struct eri_plan_s {
     int g_bits = -1, g_prec = -1;
     void *g_packed = nullptr;
     float *g_scales = nullptr;
+    // per-class precision (-1: the plan's) and the calibrated mixed-path error per class
+    int class_prec[256];
+    float class_err[256];
     // autotuned launch choice per canonical class and variant (grid 0 = all resident CTAs)
     int tune_phase[256 * kNumVariants] = {0};
     int tune_grid[256 * kNumVariants] = {0};
@@ -208,8 +232,12 @@ int class_neri(int cls) {
     return ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) * ncart_h(cls & 3);
 }
 
-int plan_variant(const eri_plan_s *p) {
-    return p->precision == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
+int class_precision(const eri_plan_s *p, int cls) {
+    return p->class_prec[cls] >= 0 ? p->class_prec[cls] : p->precision;
+}
+
+int class_variant(const eri_plan_s *p, int cls) {
+    return class_precision(p, cls) == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
 }
 
 ClassArgs class_args(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed, float *d_scales,
@@ -235,30 +263,16 @@ ClassArgs class_args(eri_plan_s *p, int cls, double *d_out, int bits, void *d_pa
     return a;
 }
 
-eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed,
-                        float *d_scales, size_t packed_off, cudaStream_t stream) {
-    if (p->count[cls] == 0) return ERI_OK;
+// Launches the kernels of generic class cls with prepared arguments `a` (its quartets, count
+// and output) in precision variant `variant`; primitive plans run the split setup/recurrence
+// path in chunks of kSetupChunk quartets where the class has no thread-per-quartet form.
+eri_status_t launch_class_args(eri_plan_s *p, int cls, const ClassArgs &a, int variant,
+                               cudaStream_t stream) {
+    if (a.nq == 0) return ERI_OK;
     Canon c = canonicalise(cls);
     ShellsDev sh{p->d_cx, p->d_cy, p->d_cz, p->d_pofs, p->d_nprim, p->d_exps, p->d_cn};
-    ClassArgs a{};
-    for (int k = 0; k < 4; ++k) {
-        a.perm[k] = c.perm[k];
-        a.ostride[k] = c.ostride[k];
-    }
-    a.quartets = p->d_quartets + p->first[cls];
-    a.nq = p->count[cls];
-    a.err = p->d_err;
-    int neri = ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) *
-               ncart_h(cls & 3);
-    if (d_out) {
-        a.out_fp64 = d_out + p->fp64_off[cls];
-    } else {
-        a.packed = reinterpret_cast<uint32_t *>(static_cast<char *>(d_packed) + packed_off);
-        a.seg_words = (long long)(packed_segment_bytes(p->count[cls], neri, bits) / 4);
-        a.scales = d_scales + p->first[cls];
-        a.bits = bits;
-    }
-    int variant = p->precision == ERI_FP64 ? 0 : (p->max_nprim > 1 ? 2 : 1);
+    const int neri = class_neri(cls);
+    const int bits = a.bits;
     LaunchFn fn = g_launch[c.cls * kNumVariants + variant];
     if (!fn) return ERI_E_UNSUPPORTED;
     LaunchOpts o;
@@ -275,7 +289,7 @@ eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d
         ClassArgs ac = a;
         ac.quartets = a.quartets + c0;
         ac.nq = std::min<long long>(kSetupChunk, a.nq - c0);
-        if (d_out) {
+        if (a.out_fp64) {
             ac.out_fp64 = a.out_fp64 + c0 * neri;
         } else {
             long long w = c0 * neri * bits / 32;
@@ -287,6 +301,13 @@ eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d
         if (e != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
+}
+
+eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed,
+                        float *d_scales, size_t packed_off, cudaStream_t stream) {
+    if (p->count[cls] == 0) return ERI_OK;
+    ClassArgs a = class_args(p, cls, d_out, bits, d_packed, d_scales, packed_off);
+    return launch_class_args(p, cls, a, class_variant(p, cls), stream);
 }
 
 eri_status_t ensure_batched_resources(eri_plan_s *p) {
@@ -322,10 +343,10 @@ eri_status_t enqueue_batched(eri_plan_s *p, int bits, void *d_packed, float *d_s
         return p->count[x] * class_neri(x) > p->count[y] * class_neri(y);
     });
     ShellsDev sh{p->d_cx, p->d_cy, p->d_cz, p->d_pofs, p->d_nprim, p->d_exps, p->d_cn};
-    const int variant = plan_variant(p);
     for (size_t i = 0; i < cls.size(); ++i) {
         int c = cls[i];
         int cc = canonicalise(c).cls;
+        const int variant = class_variant(p, c);
         LaunchFn fn = g_launch[cc * kNumVariants + variant];
         if (!fn) return ERI_E_UNSUPPORTED;
         ClassArgs a = class_args(p, c, nullptr, bits, d_packed, d_scales, off[c]);
@@ -428,6 +449,10 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     p->n_prims = (long long)ex.size();
     p->nq = nq;
     p->max_nprim = max_nprim;
+    for (int c = 0; c < 256; ++c) {
+        p->class_prec[c] = -1;
+        p->class_err[c] = -1.0f;
+    }
     if ((e = tables_for_current_device(&p->tables)) != cudaSuccess) { free_plan(p); return cuda_status(e); }
     int *d_L = nullptr;
     e = upload(&p->d_cx, cx);
@@ -534,6 +559,25 @@ void eri_plan_destroy(eri_plan_t plan) {
 eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision) {
     if (!plan || (precision != ERI_FP64 && precision != ERI_MIXED)) return ERI_E_INVALID;
     plan->precision = precision;
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision) {
+    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (precision != ERI_FP64 && precision != ERI_MIXED && precision != -1) return ERI_E_INVALID;
+    plan->class_prec[cls] = precision;
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *precision,
+                                      float *mixed_err) {
+    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (precision) *precision = class_precision(plan, cls);
+    if (mixed_err) *mixed_err = plan->class_err[cls];
     return ERI_OK;
 }
 
@@ -730,23 +774,22 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
     eri_status_t st = ensure_batched_resources(plan);
     if (st != ERI_OK) return st;
     cudaStream_t s = (cudaStream_t)stream;
-    const int variant = plan_variant(plan);
     cudaDeviceProp prop;
     if (cudaGetDeviceProperties(&prop, plan->device) != cudaSuccess) return ERI_E_CUDA;
     std::string gpu = prop.name;
     for (auto &ch : gpu)
         if (ch == ' ') ch = '_';
     // cached choices: lines "gpu variant bits canonical_class force_phase grid"
-    std::vector<int> known(256, 0);
+    std::vector<int> known(256 * kNumVariants, 0);
     if (cache_path) {
         if (FILE *f = std::fopen(cache_path, "r")) {
             char name[256];
             int v, b, c, fp, gr;
             while (std::fscanf(f, "%255s %d %d %d %d %d", name, &v, &b, &c, &fp, &gr) == 6)
-                if (gpu == name && v == variant && b == bits && c >= 0 && c < 256) {
+                if (gpu == name && v >= 0 && v < kNumVariants && b == bits && c >= 0 && c < 256) {
                     plan->tune_phase[c * kNumVariants + v] = fp;
                     plan->tune_grid[c * kNumVariants + v] = gr;
-                    known[c] = 1;
+                    known[c * kNumVariants + v] = 1;
                 }
             std::fclose(f);
         }
@@ -762,12 +805,13 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
         off[c] = o;
         o += packed_segment_bytes(plan->count[c], class_neri(c), bits);
     }
-    std::vector<int> done(256, 0);
+    std::vector<int> done(256 * kNumVariants, 0);
     for (int c = 0; c < 256; ++c) {
         if (plan->count[c] == 0) continue;
         int cc = canonicalise(c).cls;
-        if (known[cc] || done[cc]) continue;
-        done[cc] = 1;
+        const int variant = class_variant(plan, c);
+        if (known[cc * kNumVariants + variant] || done[cc * kNumVariants + variant]) continue;
+        done[cc * kNumVariants + variant] = 1;
         LaunchFn fn = g_launch[cc * kNumVariants + variant];
         ClassArgs a = class_args(plan, c, nullptr, bits, d_packed, d_scales, off[c]);
         int cand_phase[2] = {0, 1};
@@ -820,6 +864,68 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
         plan->graph = nullptr;
     }
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}
+
+eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t sample,
+                                          void *stream) {
+    if (!plan || bits < 2 || bits > 24 || sample < 1) return ERI_E_INVALID;
+    if (plan->nq == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    size_t maxv = 0;
+    for (int c = 0; c < 256; ++c)
+        maxv = std::max(maxv, (size_t)std::min<long long>(plan->count[c], sample) * class_neri(c));
+    double *da = nullptr, *db = nullptr;
+    unsigned int *dres = nullptr;
+    cudaError_t e = cudaMalloc(&da, maxv * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&db, maxv * sizeof(double));
+    if (e == cudaSuccess) e = cudaMalloc(&dres, 256 * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dres, 0, 256 * sizeof(unsigned int), s);
+    for (int c = 0; e == cudaSuccess && c < 256; ++c) {
+        if (plan->count[c] == 0) continue;
+        const long long n = std::min<long long>(plan->count[c], sample);
+        const int neri = class_neri(c);
+        double *bufs[2] = {da, db};
+        for (int k = 0; k < 2; ++k) {
+            ClassArgs a = class_args(plan, c, bufs[k], 0, nullptr, nullptr, 0);
+            a.nq = n;
+            a.out_fp64 = bufs[k];
+            const int variant = k == 0 ? 0 : (plan->max_nprim > 1 ? 2 : 1);
+            eri_status_t st = launch_class_args(plan, c, a, variant, s);
+            if (st != ERI_OK) {
+                cudaFree(da);
+                cudaFree(db);
+                cudaFree(dres);
+                return st;
+            }
+        }
+        if (e == cudaSuccess) {
+            calib_kernel<<<(unsigned)((n * 32 + 255) / 256), 256, 0, s>>>(da, db, n, neri, dres + c);
+            e = cudaGetLastError();
+        }
+    }
+    unsigned int res[256] = {0};
+    if (e == cudaSuccess) e = cudaMemcpyAsync(res, dres, sizeof(res), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(da);
+    cudaFree(db);
+    cudaFree(dres);
+    if (e != cudaSuccess) return cuda_status(e);
+    // a class keeps the FP32 recurrences when its measured error stays below a quarter of the
+    // quantisation step eps / b_max = 1 / (2^{bits-1} - 1)
+    const float thr = 0.25f / (float)((1u << (bits - 1)) - 1u);
+    for (int c = 0; c < 256; ++c) {
+        if (plan->count[c] == 0) continue;
+        float err;
+        std::memcpy(&err, &res[c], sizeof(float));
+        plan->class_err[c] = err;
+        plan->class_prec[c] = err < thr ? ERI_MIXED : ERI_FP64;
+    }
+    if (plan->graph) {
+        cudaGraphExecDestroy(plan->graph);
+        plan->graph = nullptr;
+    }
+    return ERI_OK;
 }
 
 eri_status_t eri_sync(eri_plan_t plan, void *stream) {

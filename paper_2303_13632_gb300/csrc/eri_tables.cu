@@ -8,6 +8,8 @@
 
 static_assert(RYS_NMAX == eri::kRysNmax, "table order mismatch");
 static_assert(RYS_DEG == eri::kRysDeg, "table degree mismatch");
+static_assert(RYS_TAIL == eri::kRysTail, "table tail mismatch");
+static_assert(RYS_TAIL_LEN * (RYS_DEG + 1) == RYS_CHEB_LEN * (RYS_DEG + 1 - RYS_TAIL), "tail size");
 static_assert(BOYS_MMAX == eri::kBoysMmax && BOYS_TAYLOR == eri::kBoysTaylor &&
                   BOYS_MCOLS == eri::kBoysCols && BOYS_NGRID == eri::kBoysNgrid,
               "Boys grid mismatch");
@@ -31,7 +33,8 @@ cudaError_t tables_for_current_device(Tables *out) {
     if (!g_tables_ready[dev]) {
         Tables t{};
         double *buf = nullptr;
-        size_t n = (size_t)RYS_CHEB_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN;
+        size_t n = (size_t)RYS_CHEB_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN +
+                   ((size_t)RYS_TAIL_LEN + 1) / 2;
         e = cudaMalloc(&buf, n * sizeof(double));
         if (e != cudaSuccess) return e;
         double *p = buf;
@@ -46,6 +49,9 @@ cudaError_t tables_for_current_device(Tables *out) {
         p += RYS_HERM_LEN;
         if (e == cudaSuccess) e = cudaMemcpy(p, boys_grid_h, sizeof(boys_grid_h), cudaMemcpyHostToDevice);
         t.boys_grid = p;
+        p += BOYS_GRID_LEN;
+        if (e == cudaSuccess) e = cudaMemcpy(p, rys_tail_f_h, sizeof(rys_tail_f_h), cudaMemcpyHostToDevice);
+        t.rys_tail = reinterpret_cast<const float *>(p);
         if (e != cudaSuccess) {
             cudaFree(buf);
             return e;

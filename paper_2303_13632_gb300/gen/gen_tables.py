@@ -8,6 +8,9 @@ Writes ``csrc/eri_tables.inc`` with
     series of degree RYS_DEG on unit intervals of T in [0, T_asym(n)), and the
     2n-point Gauss-Hermite nodes/weights for the large-T limit
         x_mu = u_mu^2 / T,  w_mu = H_mu / sqrt(T)      (T >= T_asym(n));
+  * FP32 copies of the Chebyshev coefficients j >= RYS_TAIL: over every piece their sum is
+    below 1e-9 of the smallest |value| of the series (checked here), so evaluating that tail of
+    Clenshaw's recurrence in FP32 keeps the result accurate to better than 1e-16 relative;
   * the Boys function F_m(T_k) on the grid T_k = k * BOYS_STEP (k < BOYS_NGRID) for
     m = 0..BOYS_MCOLS-1, used by a Taylor expansion plus downward recursion.
 
@@ -30,6 +33,7 @@ mp.mp.dps = 40
 
 RYS_NMAX = 9          # orders needed: forward L <= 12 -> 7; derivative classes need up to 9
 RYS_DEG = 12          # Chebyshev degree per unit interval
+RYS_TAIL = 8          # coefficients j >= RYS_TAIL are also stored as FP32 (evaluated in FP32)
 GL_N = 160            # Gauss-Legendre points discretising the Rys measure
 BOYS_STEP = 0.1
 BOYS_TMAX = 50.0      # F_m(T) for T >= BOYS_TMAX comes from the asymptotic form
@@ -206,6 +210,18 @@ def main():
               flush=True)
     if worst > 6e-16:
         sys.exit(f"Chebyshev fit check failed: {worst}")
+    # tail bound: sum_{j >= RYS_TAIL} |c_j| relative to min |series| on the piece
+    tail_worst = 0.0
+    nfun = len(cheb) // (RYS_DEG + 1)
+    uu = np.linspace(-1.0, 1.0, 41)
+    for f in range(nfun):
+        c = np.array(cheb[f * (RYS_DEG + 1):(f + 1) * (RYS_DEG + 1)])
+        vmin = np.min(np.abs(np.polynomial.chebyshev.chebval(uu, c)))
+        tail_worst = max(tail_worst, float(np.sum(np.abs(c[RYS_TAIL:])) / vmin))
+    if tail_worst > 1e-9:
+        sys.exit(f"Chebyshev tail too large for FP32 evaluation: {tail_worst}")
+    tail = [float(np.float32(v)) for f in range(nfun)
+            for v in cheb[f * (RYS_DEG + 1) + RYS_TAIL:(f + 1) * (RYS_DEG + 1)]]
     lines.append("/* first T of the Gauss-Hermite regime for n = index */")
     lines.append("static const int rys_tasym_h[RYS_NMAX + 1] = {" + ", ".join(map(str, tasym)) + "};")
     lines.append("/* offset (doubles) of the pieces of order n; piece k of order n holds 2n series of")
@@ -215,6 +231,13 @@ def main():
     lines.append("static const double rys_cheb_h[RYS_CHEB_LEN] = {")
     for i in range(0, len(cheb), 4):
         lines.append("  " + ", ".join(fmt(v) for v in cheb[i:i + 4]) + ",")
+    lines.append("};")
+    lines.append(f"#define RYS_TAIL {RYS_TAIL}")
+    lines.append(f"/* FP32 copies of coefficients RYS_TAIL..RYS_DEG of each series (worst tail/min|f| = {tail_worst:.2e}) */")
+    lines.append(f"#define RYS_TAIL_LEN {len(tail)}")
+    lines.append("static const float rys_tail_f_h[RYS_TAIL_LEN] = {")
+    for i in range(0, len(tail), 5):
+        lines.append("  " + ", ".join(float(v).hex() + "f" for v in tail[i:i + 5]) + ",")
     lines.append("};")
     lines.append("/* Gauss-Hermite: index hermite_offset[n] + mu - 1 holds u_mu^2 and H_mu of order n */")
     lines.append("static const int rys_herm_offset_h[RYS_NMAX + 2] = {" + ", ".join(map(str, hoff)) + "};")

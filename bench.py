@@ -31,9 +31,13 @@ sys.path.insert(0, ROOT)
 from paper_2303_13632_gb300 import perfmodel, workloads as W  # noqa: E402
 
 METRIC = "GERIS per quartet class (int16-compressed) at stated max abs err; mixed vs FP64"
-POOL_PER_L = 4096
+POOL_PER_L = W.SWEEP_POOL_PER_L
 BITS = 16
 STUDY_BITS = (8, 12, 16, 20)
+# per-class precision: FP32 recurrences for the classes whose FP32 error, measured on the
+# device over CALIB_SAMPLE quartets per class, stays below CALIB_STEPS quantisation steps
+CALIB_SAMPLE = 4096
+CALIB_STEPS = 0.5
 
 
 def unpack(words: np.ndarray, off_bytes: int, qi: np.ndarray, neri: int, bits: int) -> np.ndarray:
@@ -55,13 +59,25 @@ def classes():
 ONLY = None  # --classes: restrict the sweep to these class ids (profiling runs only)
 
 
+def class_choices(api, plan):
+    """{class: precision name} of the plan's non-empty classes."""
+    return {c: api.eri_plan_class_precision(plan, c)[0] for c in range(256)
+            if api.eri_plan_class_info(plan, c)[0]}
+
+
+def apply_choices(api, plan, choice):
+    """Per-class precision overrides (None: follow the plan's precision)."""
+    for c in range(256):
+        api.eri_plan_set_class_precision(plan, c, choice.get(c) if choice else None)
+
+
 def class_counts(scale: float):
     return {c: (max(1, int(round(W.sweep_quartet_count(W.class_of_id(c)) * scale)))
                 if ONLY is None or c in ONLY else 0) for c in range(256)}
 
 
 def make_pool(seed_k: int = 2):
-    return W.random_primitive_pool(W.rng_for(seed_k), POOL_PER_L)
+    return W.sweep_pool(seed_k)
 
 
 def read_peaks():
@@ -229,20 +245,7 @@ def run_ours(args):
     cls_list = classes()
     pool = make_pool()
     # quartet table, class-major, generated on the device from a seeded generator
-    n_total = sum(counts.values())
-    quartets = torch.empty((n_total, 4), dtype=torch.int32, device=dev)
-    gen = torch.Generator(device=dev)
-    gen.manual_seed(W.SEED_BASE + 2)
-    first = {}
-    pos = 0
-    for c in range(256):
-        cls = cls_list[c]
-        n = counts[c]
-        first[c] = pos
-        for x in range(4):
-            quartets[pos:pos + n, x] = (torch.randint(0, POOL_PER_L, (n,), generator=gen, device=dev,
-                                                      dtype=torch.int32) + cls[x] * POOL_PER_L)
-        pos += n
+    quartets, first = W.sweep_quartets_device(torch, counts, dev)
     torch.cuda.synchronize()
     plan = api.eri_plan_create(pool, quartets, precision="mixed", device=local)
     packed_bytes, scale_bytes = api.eri_output_bytes(plan, BITS)
@@ -258,27 +261,43 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- headline: mixed precision, all 256 classes per step ----
-    for _ in range(args.warmup):
-        step()
-    api.eri_sync(plan, stream)
-    clocks = ClockSampler(local)
-    barrier()
-    clocks.start()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
-    barrier()
-    clk = clocks.stop()
-    api.eri_sync(plan, stream)
-    ms = e0.elapsed_time(e1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    def timed_steps(n_warm, n_steps, clocks=None):
+        for _ in range(n_warm):
+            step()
+        api.eri_sync(plan, stream)
+        barrier()
+        if clocks is not None:
+            clocks.start()
+            torch.cuda.nvtx.range_push("timed_steps")  # lets a profiler select these launches
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n_steps):
+            step()
+        e1.record(stream)
+        if clocks is not None:
+            torch.cuda.nvtx.range_pop()
+        barrier()
+        clk = clocks.stop() if clocks is not None else None
+        api.eri_sync(plan, stream)
+        t = e0.elapsed_time(e1) / n_steps
+        if dist is not None:
+            tt = torch.tensor([t], device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            t = float(tt.item())
+        return t, clk
+
+    # ---- per-class precision for 16-bit output (plan setup, outside the timed region) ----
+    api.eri_plan_calibrate_precision(plan, BITS, sample=CALIB_SAMPLE, max_err_steps=CALIB_STEPS,
+                                     stream=stream)
+    choice16 = class_choices(api, plan)
+    launches = sum(api.eri_plan_class_launches(plan, c) for c in range(256))
+
+    # ---- headline: all 256 classes per step, FP32 recurrences where calibrated ----
+    ms, clk = timed_steps(args.warmup, args.steps, ClockSampler(local))
     value = world * total_eris / (ms * 1e-3) / 1e9
+    # every class in FP32 (no calibration), for context
+    apply_choices(api, plan, None)
+    ms_all32, _ = timed_steps(1, args.steps)
 
     # ---- per-class timing, mixed and FP64 (events on the launching stream) ----
     def per_class_ms(precision):
@@ -299,22 +318,25 @@ def run_ours(args):
     ms_fp64 = per_class_ms("fp64")
     api.eri_plan_set_precision(plan, "mixed")
     fp64_total_ms = sum(ms_fp64.values())
+    # per-class time and precision of the headline configuration
+    ms_cal = {c: (ms_mixed[c] if choice16[c] == "mixed" else ms_fp64[c]) for c in ms_mixed}
 
     # ---- roofline of the dominant kernel (largest share of the mixed step) ----
     peaks, peak_kind = read_peaks()
-    dom = max(ms_mixed, key=lambda c: ms_mixed[c])
+    dom = max(ms_cal, key=lambda c: ms_cal[c])
     dcls = cls_list[dom]
-    flops = perfmodel.fp32_equivalent_flops(dcls, "mixed") * counts[dom]
-    achieved = flops / (ms_mixed[dom] * 1e-3) / 1e12
-    t_roof = perfmodel.roofline_seconds(dcls, counts[dom], "mixed", BITS, peaks["hbm_gbs"])
-    roof = {"bound": "alu", "kernel": f"eri_class_kernel {W.class_id(*dcls)} {fmt_class(dcls)} mixed",
+    dprec = choice16[dom]
+    flops = perfmodel.fp32_equivalent_flops(dcls, dprec) * counts[dom]
+    achieved = flops / (ms_cal[dom] * 1e-3) / 1e12
+    t_roof = perfmodel.roofline_seconds(dcls, counts[dom], dprec, BITS, peaks["hbm_gbs"])
+    roof = {"bound": "alu", "kernel": f"class {W.class_id(*dcls)} {fmt_class(dcls)} {dprec}",
             "achieved": achieved, "peak": perfmodel.PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-            "frac": t_roof / (ms_mixed[dom] * 1e-3), "traffic": None,
+            "frac": t_roof / (ms_cal[dom] * 1e-3), "traffic": None,
             "peak_kind": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz); FP64 work weighted "
                          "by the FP32/FP64 peak ratio (1.25 TFLOP/s FP64)",
-            "share": ms_mixed[dom] / sum(ms_mixed.values())}
-    frac_all = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], "mixed", BITS, peaks["hbm_gbs"])
-                / (ms_mixed[c] * 1e-3) for c in ms_mixed}
+            "share": ms_cal[dom] / sum(ms_cal.values())}
+    frac_all = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], choice16[c], BITS, peaks["hbm_gbs"])
+                / (ms_cal[c] * 1e-3) for c in ms_cal}
 
     # ---- accuracy on a sample, and the CPU oracle baseline ----
     line_extra = {}
@@ -358,8 +380,22 @@ def run_ours(args):
             nbw, sbw = api.eri_output_bytes(plan, bits)
             pk = torch.empty(nbw // 4, dtype=torch.int32, device=dev) if bits != BITS else packed
             sc_t = torch.empty(sbw // 4, dtype=torch.float32, device=dev) if bits != BITS else scales
-            for prec in ("mixed", "fp64"):
-                api.eri_plan_set_precision(plan, prec)
+            for prec in ("mixed", "fp64", "calibrated"):
+                extra = {}
+                if prec == "calibrated":
+                    # FP32 recurrences only where the measured error stays below CALIB_STEPS steps
+                    api.eri_plan_set_precision(plan, "mixed")
+                    api.eri_plan_calibrate_precision(plan, bits, sample=CALIB_SAMPLE,
+                                                     max_err_steps=CALIB_STEPS, stream=stream)
+                    ch = class_choices(api, plan)
+                    t_b = _events(torch, stream,
+                                  lambda: api.eri_compute_compressed(plan, bits, pk, sc_t, stream), reps=2)
+                    extra = {"classes_fp32": sum(v == "mixed" for v in ch.values()),
+                             "geris": total_eris / (t_b * 1e-3) / 1e9}
+                else:
+                    apply_choices(api, plan, None)
+                    api.eri_plan_set_precision(plan, prec)
+                    ch = {c: prec for c in nonempty(counts)}
                 api.eri_compute_compressed(plan, bits, pk, sc_t, stream)
                 api.eri_sync(plan, stream)
                 words = pk.cpu().numpy().view(np.uint32)
@@ -377,9 +413,11 @@ def run_ours(args):
                         "max_abs_err": e, "half_step_max": h}
                     worst = max(worst, e)
                     half_step = max(half_step, h)
-                    within += arith[prec][c] <= 0.5 / ((1 << (bits - 1)) - 1)
+                    within += arith[ch[c]][c] <= 0.5 / ((1 << (bits - 1)) - 1)
                 errs.setdefault(str(bits), {})[prec] = {"max_abs_err": worst, "half_step_max": half_step,
-                                                        "classes_arith_err_below_half_step": within}
+                                                        "classes_arith_err_below_half_step": within, **extra}
+        # back to the headline configuration
+        apply_choices(api, plan, choice16)
         api.eri_plan_set_precision(plan, "mixed")
         line_extra["precision_study"] = errs
         line_extra["arith_err_rel_bmax_max"] = {p_: max(arith[p_].values()) for p_ in arith}
@@ -387,10 +425,11 @@ def run_ours(args):
             study_details = {"decompressed": study,
                              "arith_err_rel_bmax": {p_: {fmt_class(cls_list[c]): v for c, v in arith[p_].items()}
                                                     for p_ in arith}}
-        errs16 = {prec: errs[str(BITS)][prec]["max_abs_err"] for prec in ("mixed", "fp64")}
+        errs16 = {prec: errs[str(BITS)][prec]["max_abs_err"] for prec in ("mixed", "fp64", "calibrated")}
         api.eri_plan_set_precision(plan, "mixed")
         n_sampled = sum(len(v) for v in sample_idx.values())
-        line_extra["max_abs_err"] = {"mixed": errs16["mixed"], "fp64": errs16["fp64"], "unit": "Ha",
+        line_extra["max_abs_err"] = {"headline": errs16["calibrated"], "mixed_all_fp32": errs16["mixed"],
+                                     "fp64": errs16["fp64"], "unit": "Ha",
                                      "sample": f"{n_sampled} quartets (about {args.ref_eris} ERIs per class), "
                                                "decompressed 16-bit vs FP64 oracle"}
         line_extra["cpu_baseline"] = {"value": g_cpu, "unit": "GERIS", "cores": cores, "kind": "oracle",
@@ -399,7 +438,8 @@ def run_ours(args):
                                                 "full class mix"}
 
     # ---- end to end through the C ABI with host buffers ----
-    e2e = run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream) if not args.no_e2e else None
+    e2e = (run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream, choice16)
+           if not args.no_e2e else None)
 
     if rank == 0:
         geris_mixed = {fmt_class(cls_list[c]): round(counts[c] * W.quartet_size(*cls_list[c]) / (ms_mixed[c] * 1e-3) / 1e9, 2)
@@ -411,12 +451,19 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": config_dict(args),
+            "precision": {"classes_fp32": sum(v == "mixed" for v in choice16.values()),
+                          "classes_fp64": [fmt_class(cls_list[c]) for c in sorted(choice16)
+                                           if choice16[c] == "fp64"],
+                          "rule": f"FP32 recurrences where the FP32 error measured on {CALIB_SAMPLE} quartets "
+                                  f"per class stays below {CALIB_STEPS} quantisation steps (16-bit)"},
+            "mixed_all_fp32": {"value": total_eris / (ms_all32 * 1e-3) / 1e9, "unit": "GERIS",
+                               "ms_per_step": ms_all32},
             "fp64": {"value": total_eris / (fp64_total_ms * 1e-3) / 1e9, "unit": "GERIS",
                      "ms_per_step": fp64_total_ms, "speedup_mixed_over_fp64": fp64_total_ms / ms},
             "roofline": roof,
             "roofline_frac_per_class": {"min": min(frac_all.values()), "median": statistics.median(frac_all.values()),
                                         "max": max(frac_all.values())},
-            "clocks": clk, "gpu_launches": len(nonempty(counts)) * args.steps,
+            "clocks": clk, "gpu_launches": launches * args.steps,
             "per_class_geris": {"mixed": geris_mixed, "fp64": geris_fp64},
         }
         out.update(line_extra)
@@ -435,10 +482,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream):
+def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream, choice):
     """Same metric through the public API with host buffers: every step creates the plan from
-    pinned host quartets (host->device copy and class sort inside), computes the compressed
-    ERIs and copies packed codes and scales back to pinned host memory."""
+    pinned host quartets (host->device copy and class sort inside), applies the calibrated
+    per-class precision, computes the compressed ERIs and copies packed codes and scales back
+    to pinned host memory."""
     import torch
 
     qh = torch.empty(quartets.shape, dtype=torch.int32, pin_memory=True)
@@ -454,6 +502,7 @@ def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream):
 
     def one():
         p = api.eri_plan_create(pool, qnp, precision="mixed", device=dev.index)
+        apply_choices(api, p, choice)
         api.eri_compute_compressed(p, BITS, packed, scales, stream)
         packed_h.copy_(packed, non_blocking=True)
         scales_h.copy_(scales, non_blocking=True)
@@ -471,7 +520,8 @@ def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream):
     return {"value": total_eris / dt / 1e9, "unit": "GERIS", "ms_per_step": dt * 1e3,
             "h2d_bytes_per_step": int(qh.numel() * 4),
             "d2h_bytes_per_step": int(packed_h.numel() * 4 + scales_h.numel() * 4),
-            "path": "eri_plan_create(host quartets) + eri_compute_compressed + D2H of codes and scales"}
+            "path": "eri_plan_create(host quartets) + per-class precision + eri_compute_compressed + "
+                    "D2H of codes and scales"}
 
 
 # ---------------------------------------------------------------------------------------------
@@ -600,17 +650,24 @@ def run_molecule(args):
     nb, sb = api.eri_output_bytes(plan, BITS)
     packed = torch.empty(nb // 4, dtype=torch.int32, device=dev)
     scales = torch.empty(sb // 4, dtype=torch.float32, device=dev)
+    api.eri_plan_calibrate_precision(plan, BITS, sample=CALIB_SAMPLE, max_err_steps=CALIB_STEPS, stream=stream)
+    choice = class_choices(api, plan)
     ms_plain = _events(torch, stream, lambda: api.eri_compute_compressed(plan, BITS, packed, scales, stream))
     cache = os.path.join(tempfile.gettempdir(), "eri_autotune_molecule.txt")
     api.eri_autotune(plan, BITS, packed, scales, cache, stream)
     ms_graph = _events(torch, stream, lambda: api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream), reps=3)
+    apply_choices(api, plan, None)
     api.eri_plan_set_precision(plan, "fp64")
+    api.eri_autotune(plan, BITS, packed, scales, cache, stream)
     ms_fp64 = _events(torch, stream, lambda: api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream), reps=1)
     api.eri_plan_set_precision(plan, "mixed")
+    apply_choices(api, plan, choice)
     api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream)
     api.eri_sync(plan, stream)
     out = {"impl": "ours", "workload": "molecule",
            "metric": "GERIS, batched persistent CUDA-graph launch, mixed precision, 16-bit",
+           "precision": {"classes_fp32": sum(v == "mixed" for v in choice.values()),
+                         "classes_fp64": sum(v == "fp64" for v in choice.values())},
            "value": n_eri / (ms_graph * 1e-3) / 1e9, "unit": "GERIS",
            "per_class_launches_geris": n_eri / (ms_plain * 1e-3) / 1e9,
            "fp64_batched_geris": n_eri / (ms_fp64 * 1e-3) / 1e9,

@@ -111,17 +111,24 @@ eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);
 eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision);
 
 /* Chooses the precision of every class of the plan for `bits`-bit output: FP32 recurrences
- * (ERI_MIXED) where the measured error stays below a quarter of the quantisation step, FP64
- * elsewhere.  The error of a class is max |mixed - FP64| / b_max over its first `sample`
- * quartets, both computed on the device (quartets with b_max <= 1e-30 Ha are left out), so it
- * is a sample estimate.  Allocates temporary device buffers; synchronous on `stream`. */
+ * (ERI_MIXED) for the classes whose measured error stays below `max_err_steps` (0 < . <= 1)
+ * quantisation steps eps = b_max / (2^{bits-1} - 1), FP64 for the others.  The error of a
+ * class is max |mixed - FP64| / b_max over its first `sample` quartets, both computed on the
+ * device (quartets with b_max <= 1e-30 Ha are left out), so it is a sample estimate; the
+ * decompressed error of a mixed class is then at most eps / 2 (Eq. 10) plus that error.
+ * Allocates temporary device buffers; synchronous on `stream`. */
 eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t sample,
-                                          void *stream);
+                                          float max_err_steps, void *stream);
 
 /* Effective precision of a class and the error measured by eri_plan_calibrate_precision
  * (-1 when not measured).  Either output may be NULL. */
 eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *precision,
                                       float *mixed_err);
+
+/* Kernel launches eri_compute_class / eri_compute_compressed_class make for class cls in its
+ * current precision: 1 for the fused kernels, 2 per chunk of 2^20 quartets (setup and
+ * recurrence kernels) on the split path of primitive plans, 0 for an empty class. */
+eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches);
 
 /* Total quartets in the plan. */
 eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);

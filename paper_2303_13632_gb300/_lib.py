@@ -58,8 +58,9 @@ SIGNATURES = {
     "eri_plan_destroy": (None, [_p]),
     "eri_plan_set_precision": (_i32, [_p, _i32]),
     "eri_plan_set_class_precision": (_i32, [_p, _i32, _i32]),
-    "eri_plan_calibrate_precision": (_i32, [_p, _i32, _i64, _p]),
+    "eri_plan_calibrate_precision": (_i32, [_p, _i32, _i64, ctypes.c_float, _p]),
     "eri_plan_class_precision": (_i32, [_p, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
+    "eri_plan_class_launches": (_i32, [_p, _i32, _i32p]),
     "eri_plan_num_quartets": (_i32, [_p, _i64p]),
     "eri_plan_class_info": (_i32, [_p, _i32, _i64p, _i32p, _i64p, _i64p]),
     "eri_plan_quartet_order": (_i32, [_p, _i64p]),

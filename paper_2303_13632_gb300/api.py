@@ -104,8 +104,10 @@ def eri_plan_set_class_precision(plan: Plan, cls: int, precision: str | None) ->
     check(_lib.load().eri_plan_set_class_precision(plan.handle, cls, v), "eri_plan_set_class_precision")
 
 
-def eri_plan_calibrate_precision(plan: Plan, bits: int, sample: int = 4096, stream=None) -> None:
-    check(_lib.load().eri_plan_calibrate_precision(plan.handle, bits, sample, _stream_handle(stream)),
+def eri_plan_calibrate_precision(plan: Plan, bits: int, sample: int = 4096,
+                                 max_err_steps: float = 0.5, stream=None) -> None:
+    check(_lib.load().eri_plan_calibrate_precision(plan.handle, bits, sample, max_err_steps,
+                                                   _stream_handle(stream)),
           "eri_plan_calibrate_precision")
 
 
@@ -115,6 +117,12 @@ def eri_plan_class_precision(plan: Plan, cls: int):
     check(_lib.load().eri_plan_class_precision(plan.handle, cls, ctypes.byref(p), ctypes.byref(e)),
           "eri_plan_class_precision")
     return ("fp64" if p.value == ERI_FP64 else "mixed"), float(e.value)
+
+
+def eri_plan_class_launches(plan: Plan, cls: int) -> int:
+    n = ctypes.c_int32()
+    check(_lib.load().eri_plan_class_launches(plan.handle, cls, ctypes.byref(n)), "eri_plan_class_launches")
+    return int(n.value)
 
 
 def eri_plan_num_quartets(plan: Plan) -> int:

@@ -28,6 +28,9 @@ struct GCfg {
     static constexpr int NAB = La + Lb, NCD = Lc + Ld;
     static constexpr int NRYS = (La0 + Lb0 + Lc0 + Ld0 + 2) / 2 + 1;
     static constexpr bool FUSE_BC = false;
+    static constexpr bool DIRECT = false;
+    static constexpr bool SWAB_OK = true, SWCD_OK = true;
+    static constexpr int SN = S_N, S_CB = S_N, S_CD = S_N;
     static constexpr int JL = (Lb + 1) * (Ld + 1);
     static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;
     static constexpr int JLP = (JL % 2) ? JL : JL + 1;

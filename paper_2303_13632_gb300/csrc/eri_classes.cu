@@ -28,7 +28,10 @@ struct Register {
                 tpq[cls * kNumVariants + 0] = Cfg<La, Lb, Lc, Ld, double>::TPQ;
                 tpq[cls * kNumVariants + 1] = Cfg<La, Lb, Lc, Ld, float>::TPQ;
                 tpq[cls * kNumVariants + 2] = false;
+                // setup records fit the setup buffer (kSetupFieldsMax doubles per quartet)
                 static_assert(Cfg<La, Lb, Lc, Ld, double>::SETUP_FIELDS <= kSetupFieldsMax, "setup");
+                static_assert(Cfg<La, Lb, Lc, Ld, float>::SETUP_FIELDS * sizeof(float) <=
+                                  kSetupFieldsMax * sizeof(double), "setup");
             }
             Register<IDX + 1>::apply(table, tpq);
         }

@@ -74,7 +74,10 @@ enum GeoSlot {
 };
 // Per-quartet geometry the recurrence stages read, in the recurrence type R (no FP64 there).
 enum RGeoSlot { RG_ABX = 0, RG_ABY, RG_ABZ, RG_CDX, RG_CDY, RG_CDZ, RG_SWAB, RG_SWCD, RG_N };
-// Per (quartet, root) setup values kept in shared memory (type R).
+// Per (quartet, root) setup values kept in shared memory (type R).  S_C0 / S_C1 are C00 and
+// C00' relative to the centres the recurrence is built on; classes on the four-index path
+// (Cfg::DIRECT) append C00 relative to B (at Cfg::S_CB, when Lb > 0) and C00' relative to D
+// (at Cfg::S_CD, when Ld > 0), Cfg::SN values in all.
 enum BCSlot { S_B00 = 0, S_B10, S_B01, S_C0X, S_C0Y, S_C0Z, S_C1X, S_C1Y, S_C1Z, S_WZ, S_N };
 
 template <int La_, int Lb_, int Lc_, int Ld_, typename R_>
@@ -93,6 +96,19 @@ struct Cfg {
     static constexpr int IBLKP = (La + 1) * (Lc + 1) * JLP;
     static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);  // bra-transferred per (xi, mu)
     static constexpr bool FUSE_BC = HBLK <= 48;             // ket HRR in registers in phase B
+    // thread-per-quartet variant (all intermediates in registers) for the small classes
+    static constexpr bool TPQ = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
+    // FP32 recurrences of the shared-memory kernels with angular momentum on b or d use the
+    // four-index recursion (phase_direct): in FP32 the transfer relation amplifies rounding
+    // by up to about 3^(Lb+Ld).  FP64 keeps the VRR + HRR of Eqs. 6-7.
+    static constexpr bool DIRECT = sizeof(R) == 4 && !TPQ && (Lb + Ld) > 0;
+    // VRR built on B (D) with the HRR transferring to a (c) where that is the better-
+    // conditioned direction; never when b (d) carries no angular momentum
+    static constexpr bool SWAB_OK = !DIRECT && Lb > 0;
+    static constexpr bool SWCD_OK = !DIRECT && Ld > 0;
+    static constexpr int S_CB = S_N;
+    static constexpr int S_CD = S_N + (DIRECT && Lb > 0 ? 3 : 0);
+    static constexpr int SN = S_CD + (DIRECT && Ld > 0 ? 3 : 0);
     static constexpr int RWORDS = sizeof(R) / 4;
     // outputs per thread: bchunk x ND accumulators (+ Kahan compensation in FP32)
     static constexpr int ACC_REGS = (sizeof(R) == 8) ? 48 : 64;
@@ -101,8 +117,8 @@ struct Cfg {
     static constexpr int ITEMS_D = NA * NC * NCH;
     // shared memory per quartet (bytes)
     static constexpr int GEO_BYTES = G_N * 8;
-    static constexpr int BC_BYTES = NRYS * S_N * (int)sizeof(R);
-    static constexpr int H_BYTES = FUSE_BC ? 0 : 3 * NRYS * HBLK * (int)sizeof(R);
+    static constexpr int BC_BYTES = NRYS * SN * (int)sizeof(R);
+    static constexpr int H_BYTES = (FUSE_BC || DIRECT) ? 0 : 3 * NRYS * HBLK * (int)sizeof(R);
     static constexpr int I_BYTES = 3 * NRYS * IBLKP * (int)sizeof(R);
     static constexpr int STAGE_BYTES = NERI * 3;  // worst case 24-bit codes
     static constexpr int UNION_BYTES = imax(H_BYTES + I_BYTES, STAGE_BYTES);
@@ -123,9 +139,7 @@ struct Cfg {
     static constexpr int SMEM = OFF_U + ((Q * UNION_BYTES + 16 + 15) / 16) * 16 + 16;
     // values per quartet written by the separate setup kernel (K = 1 plans)
     static constexpr int SETUP_GEO = 8;  // AB, CD, swab, swcd
-    static constexpr int SETUP_FIELDS = SETUP_GEO + NRYS * S_N;
-    // thread-per-quartet variant (all intermediates in registers) for the small classes
-    static constexpr bool TPQ = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
+    static constexpr int SETUP_FIELDS = SETUP_GEO + NRYS * SN;
     static constexpr int TPQ_THREADS = 128;
 };
 
@@ -168,8 +182,8 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
         double PA = -eb * ip * AB, QC = -ed * iq * CD;
         double PQ = (A[x] + PA) - (Cc[x] + QC);
         // the VRR is built on the centre nearer to P (the larger exponent): P - B = (P - A) + AB
-        geo[G_PAX + x] = eb > ea ? PA + AB : PA;
-        geo[G_QCX + x] = ed > ec ? QC + CD : QC;
+        geo[G_PAX + x] = (C::SWAB_OK && eb > ea) ? PA + AB : PA;
+        geo[G_QCX + x] = (C::SWCD_OK && ed > ec) ? QC + CD : QC;
         geo[G_PQX + x] = PQ;
         geo[G_ABX + x] = AB;
         geo[G_CDX + x] = CD;
@@ -188,8 +202,8 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     geo[G_T] = rho * pq2;
     geo[G_P] = p;
     geo[G_Q] = q;
-    geo[G_SWAB] = eb > ea ? 1.0 : 0.0;
-    geo[G_SWCD] = ed > ec ? 1.0 : 0.0;
+    geo[G_SWAB] = (C::SWAB_OK && eb > ea) ? 1.0 : 0.0;
+    geo[G_SWCD] = (C::SWCD_OK && ed > ec) ? 1.0 : 0.0;
     geo[G_IP] = ip;
     geo[G_IQ] = iq;
     geo[G_IPQ] = ipq;
@@ -225,6 +239,17 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
             double pq = geo[G_PQX + s];
             bc[S_C0X + s] = (R)(geo[G_PAX + s] - fq * pq);
             bc[S_C1X + s] = (R)(geo[G_QCX + s] + fp * pq);
+        }
+        // four-index path: P - B = (P - A) + (A - B), Q - D = (Q - C) + (C - D)
+        if constexpr (C::DIRECT && C::Lb > 0) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                bc[C::S_CB + s] = (R)((geo[G_PAX + s] + geo[G_ABX + s]) - fq * geo[G_PQX + s]);
+        }
+        if constexpr (C::DIRECT && C::Ld > 0) {
+#pragma unroll
+            for (int s = 0; s < 3; ++s)
+                bc[C::S_CD + s] = (R)((geo[G_QCX + s] + geo[G_CDX + s]) + fp * geo[G_PQX + s]);
         }
     }
 }
@@ -310,7 +335,7 @@ template <class C>
 __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const typename C::R *rg, int mu,
                                           int xi, typename C::R *Hq, typename C::R *Iq) {
     using R = typename C::R;
-    const R *b = bc + mu * S_N;
+    const R *b = bc + mu * C::SN;
     R c00 = b[S_C0X + xi], c01 = b[S_C1X + xi];
     R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
     R ab = rg[RG_ABX + xi];
@@ -375,6 +400,101 @@ __device__ __forceinline__ void phase_vrr(const typename C::R *bc, const typenam
 #pragma unroll
                     for (int l = 0; l <= C::Ld; ++l) Iq[i_index<C>(xi, mu, i, k, j, l)] = o[k][l];
             }
+    }
+}
+
+// Phase B of the four-index path (Cfg::DIRECT): the 2-D integrals I(i, j, k, l) of one
+// (quartet, root, axis) by the Rys recursion in which every index is raised with the C
+// coefficient of its own centre (the recurrences of the 2-D integrals behind Eqs. 6-7 before
+// the transfer relation is introduced):
+//   I(i+1, 0, 0, 0) = C00_A I(i) + i B10 I(i-1)
+//   I(i, j+1, 0, 0) = C00_B I(i, j) + j B10 I(i, j-1) + i B10 I(i-1, j)
+//   I(i, j, k+1, 0) = C00'_C I(k) + k B01 I(k-1) + (i I(i-1, j) + j I(i, j-1)) B00 at k
+//   I(i, j, k, l+1) = C00'_D I(l) + l B01 I(l-1) + k B01 I(k-1, l) + (i I(i-1) + j I(j-1)) B00
+// where C00_X = (P - X) - q x / (p+q) (P - Q), C00'_Y = (Q - Y) + p x / (p+q) (P - Q).
+// Exact arithmetic gives the VRR + HRR values; in FP32 no step subtracts transferred
+// values of a larger magnitude, so the rounding is not amplified.  The (i, j) plane of the
+// current (k, l) is kept in registers, lower planes are read back from the I block already
+// written (a small register footprint next to the accumulators of phase D).
+template <class C>
+__device__ __forceinline__ void phase_direct(const typename C::R *bc, int mu, int xi,
+                                             typename C::R *Iq) {
+    using R = typename C::R;
+    constexpr int NI = C::La + 1, NJ = C::Lb + 1;
+    const R *b = bc + mu * C::SN;
+    const R cA = b[S_C0X + xi], cC = b[S_C1X + xi];
+    R cB = (R)0, cD = (R)0;
+    if constexpr (C::Lb > 0) cB = b[C::S_CB + xi];
+    if constexpr (C::Ld > 0) cD = b[C::S_CD + xi];
+    const R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
+    R *blk = Iq + i_index<C>(xi, mu, 0, 0, 0, 0);
+    // plane (k, l) = (0, 0)
+    R pl[NI][NJ];
+    pl[0][0] = (xi == 2) ? b[S_WZ] : (R)1;
+#pragma unroll
+    for (int i = 1; i < NI; ++i)
+        pl[i][0] = i > 1 ? fma((R)(i - 1) * b10, pl[i - 2][0], cA * pl[i - 1][0]) : cA * pl[i - 1][0];
+#pragma unroll
+    for (int j = 1; j < NJ; ++j)
+#pragma unroll
+        for (int i = 0; i < NI; ++i) {
+            R v = cB * pl[i][j - 1];
+            if (j > 1) v = fma((R)(j - 1) * b10, pl[i][j - 2], v);
+            if (i > 0) v = fma((R)i * b10, pl[i - 1][j - 1], v);
+            pl[i][j] = v;
+        }
+#pragma unroll
+    for (int k = 0; k <= C::Lc; ++k) {
+        if (k > 0) {
+            // raise k at l = 0 from the planes (k-1, 0) and (k-2, 0) read back from the I block
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) {
+                    const int e = (i * (C::Lc + 1) + k) * C::JLP + j * (C::Ld + 1);
+                    R v = cC * blk[e - C::JLP];
+                    if (k > 1) v = fma((R)(k - 1) * b01, blk[e - 2 * C::JLP], v);
+                    if (i > 0) v = fma((R)i * b00, blk[e - (C::Lc + 2) * C::JLP], v);
+                    if (j > 0) v = fma((R)j * b00, blk[e - C::JLP - (C::Ld + 1)], v);
+                    pl[i][j] = v;
+                }
+        }
+#pragma unroll
+        for (int i = 0; i < NI; ++i)
+#pragma unroll
+            for (int j = 0; j < NJ; ++j) blk[(i * (C::Lc + 1) + k) * C::JLP + j * (C::Ld + 1)] = pl[i][j];
+        if constexpr (C::Ld > 0) {
+            // raise l: the plane (k, l-1) stays in registers, (k, l-2) and (k-1, l-1) are read
+            // back from the I block (keeps the register footprint at two planes)
+            R q1[NI][NJ];
+#pragma unroll
+            for (int i = 0; i < NI; ++i)
+#pragma unroll
+                for (int j = 0; j < NJ; ++j) q1[i][j] = pl[i][j];
+#pragma unroll
+            for (int l = 1; l <= C::Ld; ++l) {
+                R nw[NI][NJ];
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        const int e = (i * (C::Lc + 1) + k) * C::JLP + j * (C::Ld + 1) + l;
+                        R v = cD * q1[i][j];
+                        if (l > 1) v = fma((R)(l - 1) * b01, blk[e - 2], v);
+                        if (k > 0) v = fma((R)k * b01, blk[e - C::JLP - 1], v);
+                        if (i > 0) v = fma((R)i * b00, q1[i - 1][j], v);
+                        if (j > 0) v = fma((R)j * b00, q1[i][j - 1], v);
+                        nw[i][j] = v;
+                    }
+#pragma unroll
+                for (int i = 0; i < NI; ++i)
+#pragma unroll
+                    for (int j = 0; j < NJ; ++j) {
+                        blk[(i * (C::Lc + 1) + k) * C::JLP + j * (C::Ld + 1) + l] = nw[i][j];
+                        q1[i][j] = nw[i][j];
+                    }
+            }
+        }
     }
 }
 
@@ -597,9 +717,9 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 int f = it / C::Q, q = it % C::Q;
                 rg_s[q * RG_N + f] = q < qn ? su[f * ss + q0 + q] : (R)0;
             }
-            for (int it = tid; it < C::Q * C::NRYS * S_N; it += C::THREADS) {
+            for (int it = tid; it < C::Q * C::NRYS * C::SN; it += C::THREADS) {
                 int f = it / C::Q, q = it % C::Q;
-                bc_s[q * C::NRYS * S_N + f] = q < qn ? su[(C::SETUP_GEO + f) * ss + q0 + q] : (R)0;
+                bc_s[q * C::NRYS * C::SN + f] = q < qn ? su[(C::SETUP_GEO + f) * ss + q0 + q] : (R)0;
             }
             __syncthreads();
         } else {
@@ -634,20 +754,25 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
             // A1: roots, weights, B and C per (quartet, root)
             for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
                 int q = it / C::NRYS, mu = it % C::NRYS;
-                phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
+                phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * C::SN);
             }
             __syncthreads();
         }
-        // B: VRR (+ bra HRR, + ket HRR when fused) per (quartet, root, axis)
+        // B: VRR (+ bra HRR, + ket HRR when fused), or the four-index recursion, per
+        // (quartet, root, axis)
         for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
             int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
             int mu = r / 3, xi = r % 3;
-            phase_vrr<C>(bc_s + q * C::NRYS * S_N, rg_s + q * RG_N, mu, xi,
-                         H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
-                         I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
+            if constexpr (C::DIRECT)
+                phase_direct<C>(bc_s + q * C::NRYS * C::SN, mu, xi,
+                                I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
+            else
+                phase_vrr<C>(bc_s + q * C::NRYS * C::SN, rg_s + q * RG_N, mu, xi,
+                             H_s + (size_t)q * (C::H_BYTES / sizeof(R)),
+                             I_s + (size_t)q * (C::I_BYTES / sizeof(R)));
         }
         __syncthreads();
-        if constexpr (!C::FUSE_BC) {
+        if constexpr (!C::FUSE_BC && !C::DIRECT) {
             constexpr int NIJ = (C::La + 1) * (C::Lb + 1);
             for (int it = tid; it < C::Q * C::NRYS * 3 * NIJ; it += C::THREADS) {
                 int q = it / (C::NRYS * 3 * NIJ), r = it % (C::NRYS * 3 * NIJ);
@@ -831,10 +956,10 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
     o[7 * stride] = (R)geo[G_SWCD];
 #pragma unroll 1
     for (int mu = 0; mu < C::NRYS; ++mu) {
-        R bc[S_N];
+        R bc[C::SN];
         phase_setup<C>(tb, geo, mu, bc);
 #pragma unroll
-        for (int f = 0; f < S_N; ++f) o[(C::SETUP_GEO + mu * S_N + f) * stride] = bc[f];
+        for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * stride] = bc[f];
     }
 }
 
@@ -891,7 +1016,7 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
             rg[RG_SWCD] = (R)geo[G_SWCD];
 #pragma unroll 1
             for (int mu = 0; mu < C::NRYS; ++mu) {
-                R bc[S_N];
+                R bc[C::SN];
                 phase_setup<C>(tb, geo, mu, bc);
                 R X[C::IBLK], Y[C::IBLK], Z[C::IBLK];
                 axis_2d<C>(bc, rg, 0, X);

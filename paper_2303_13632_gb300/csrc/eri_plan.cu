@@ -866,9 +866,22 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
 }
 
+eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches) {
+    if (!plan || cls < 0 || cls > 255 || !n_launches) return ERI_E_INVALID;
+    *n_launches = 0;
+    if (plan->count[cls] == 0) return ERI_OK;
+    const int v = class_variant(plan, cls);
+    const int k = canonicalise(cls).cls * kNumVariants + v;
+    if (!g_launch[k]) return ERI_E_UNSUPPORTED;
+    const bool split = plan->max_nprim == 1 && !g_tpq[k];
+    *n_launches = split ? 2 * (int32_t)((plan->count[cls] + kSetupChunk - 1) / kSetupChunk) : 1;
+    return ERI_OK;
+}
+
 eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t sample,
-                                          void *stream) {
+                                          float max_err_steps, void *stream) {
     if (!plan || bits < 2 || bits > 24 || sample < 1) return ERI_E_INVALID;
+    if (!(max_err_steps > 0.0f && max_err_steps <= 1.0f)) return ERI_E_INVALID;
     if (plan->nq == 0) return ERI_OK;
     cudaSetDevice(plan->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -911,9 +924,9 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
     cudaFree(db);
     cudaFree(dres);
     if (e != cudaSuccess) return cuda_status(e);
-    // a class keeps the FP32 recurrences when its measured error stays below a quarter of the
-    // quantisation step eps / b_max = 1 / (2^{bits-1} - 1)
-    const float thr = 0.25f / (float)((1u << (bits - 1)) - 1u);
+    // a class keeps the FP32 recurrences when its measured error stays below max_err_steps
+    // quantisation steps, one step being eps / b_max = 1 / (2^{bits-1} - 1)
+    const float thr = max_err_steps / (float)((1u << (bits - 1)) - 1u);
     for (int c = 0; c < 256; ++c) {
         if (plan->count[c] == 0) continue;
         float err;

@@ -111,6 +111,35 @@ def sweep_quartet_count(cls, target_eris: int = 1 << 26) -> int:
     return max(1, int(round(target_eris / quartet_size(*cls))))
 
 
+SWEEP_POOL_PER_L = 4096
+
+
+def sweep_pool(seed_k: int = 2) -> ShellSet:
+    """Shell pool of the 256-class sweep: SWEEP_POOL_PER_L primitive shells per L."""
+    return random_primitive_pool(rng_for(seed_k), SWEEP_POOL_PER_L)
+
+
+def sweep_quartets_device(torch, counts, device, seed_k: int = 2, n_per_L: int = SWEEP_POOL_PER_L):
+    """Class-major int32 quartet table [sum(counts), 4] of the sweep, drawn on the device with
+    a seeded torch generator (class c gets counts[c] rows of shell ids of its four angular
+    momenta from the pool of sweep_pool); returns (table, first row of each class)."""
+    n_total = sum(counts[c] for c in range(256))
+    q = torch.empty((n_total, 4), dtype=torch.int32, device=device)
+    gen = torch.Generator(device=device)
+    gen.manual_seed(SEED_BASE + seed_k)
+    first = {}
+    pos = 0
+    for c in range(256):
+        cls = class_of_id(c)
+        n = counts[c]
+        first[c] = pos
+        for x in range(4):
+            q[pos:pos + n, x] = (torch.randint(0, n_per_L, (n,), generator=gen, device=device,
+                                               dtype=torch.int32) + cls[x] * n_per_L)
+        pos += n
+    return q, first
+
+
 def lattice_sites() -> np.ndarray:
     """32 sites of the 4 x 4 x 2 cubic lattice of Sec. IV-A, spacing 1 Angstrom, in bohr."""
     g = np.array([(i, j, k) for i in range(4) for j in range(4) for k in range(2)], dtype=np.float64)

@@ -71,7 +71,8 @@ enum {
 
 /* Flags of eri_plan_opts_t.flags */
 enum {
-    ERI_QUARTETS_ON_DEVICE = 1 /* `quartets` is a device pointer (no host->device copy) */
+    ERI_QUARTETS_ON_DEVICE = 1, /* `quartets` is a device pointer (no host->device copy) */
+    ERI_NO_PAIR_TABLE = 2       /* do not build the primitive-pair table (see eri_plan_create) */
 };
 
 /* One shell (host memory; eri_plan_create copies it). */
@@ -91,7 +92,12 @@ typedef struct {
 } eri_plan_opts_t;
 
 /* Builds a plan: validates and normalises the shells, classifies and sorts the quartets by
- * class on the device, and keeps device copies of everything the kernels read.
+ * class on the device, and keeps device copies of everything the kernels read.  Unless
+ * ERI_NO_PAIR_TABLE is set, it also tabulates the Gaussian-product quantities of every pair of
+ * primitives (p, 1/p, P - A and the exponential prefactor times both coefficients, 48 bytes a
+ * pair, n_prims^2 pairs) when that table stays within 16 GiB and a quarter of the free device
+ * memory; the kernels then read them instead of recomputing them per quartet (same values up to
+ * rounding order).
  *   shells      n_shells entries (host)
  *   quartets    n_quartets x 4 int32 shell ids, row major (host unless
  *               ERI_QUARTETS_ON_DEVICE), or NULL with ERI_ALL

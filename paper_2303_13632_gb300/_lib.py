@@ -25,6 +25,7 @@ ERI_MIXED = 1
 ERI_EXPLICIT = 0
 ERI_ALL = 1
 ERI_QUARTETS_ON_DEVICE = 1
+ERI_NO_PAIR_TABLE = 2
 ERI_NOALLOC_MAX_QUARTETS = 16384
 
 STATUS_NAMES = {

@@ -52,9 +52,10 @@ class Plan:
 
 
 def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = "explicit",
-                    device: int = 0) -> Plan:
+                    device: int = 0, pair_table: bool = True) -> Plan:
     """shells: a ShellSet (workloads.py); quartets: [n, 4] int32 numpy array (host), a
-    contiguous int32 CUDA tensor (device), or None with mode="all"."""
+    contiguous int32 CUDA tensor (device), or None with mode="all"; pair_table=False sets
+    ERI_NO_PAIR_TABLE."""
     lib = _lib.load()
     n = len(shells.L)
     arr = (_lib.eri_shell_t * max(n, 1))()
@@ -72,7 +73,7 @@ def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = 
         sh.exps = ctypes.cast(base_e + off, _lib.c_double_p)
         sh.coefs = ctypes.cast(base_c + off, _lib.c_double_p)
     opts = _lib.eri_plan_opts_t(PRECISIONS[precision], ERI_ALL if mode == "all" else ERI_EXPLICIT,
-                                device, 0)
+                                device, 0 if pair_table else _lib.ERI_NO_PAIR_TABLE)
     if quartets is None:
         qptr, nq = ctypes.c_void_p(0), 0
     elif isinstance(quartets, np.ndarray):

@@ -39,6 +39,7 @@ struct Tables {
     const double *herm_x2;
     const double *herm_w;
     const double *boys_grid;
+    const double *boys_t01;  // F_0, F_1 Taylor coefficients divided by j! (kBoysTaylor each)
     int tasym[kRysNmax + 1];
     long long offset[kRysNmax + 1];
     int herm_off[kRysNmax + 2];
@@ -70,7 +71,14 @@ struct ClassArgs {
     int *err;              // device error latch (bit 0: non-finite result)
     const void *setup;     // per-quartet setup values from the setup kernel, or null
     long long setup_stride;  // elements between two fields of the setup buffer
+    const double *pairs;   // primitive-pair table (kPairFields per pair, index pa * np + pb), or null
+    long long np;          // primitives of the plan (row length of the pair table)
 };
+
+// Primitive-pair record: the Gaussian-product quantities of primitives (pa, pb) of shells
+// (X, Y) that do not depend on the other pair (Sec. II-A): p = a + b, 1/p, P - X =
+// -(b/p)(X - Y), and exp(-ab/p |X - Y|^2) times both coefficient x normalisation factors.
+enum PairField { PR_P = 0, PR_IP, PR_PAX, PR_PAY, PR_PAZ, PR_KCN, kPairFields };
 
 // Launch options of a class kernel (see launch_class).
 struct LaunchOpts {
@@ -109,19 +117,19 @@ __device__ __forceinline__ void boys_eval(int mmax, double T, const double *__re
 // point for T < 50; beyond, F_0 = sqrt(pi/T)/2 and F_1 = F_0/(2T) (the exp(-T) terms are below
 // 1e-20 relative there).
 template <bool WANT1>
-__device__ __forceinline__ void boys_f01(double T, const double *__restrict__ grid, double &F0,
+__device__ __forceinline__ void boys_f01(double T, const double *__restrict__ t01, double &F0,
                                          double &F1) {
     if (T < kBoysTmax) {
+        // F_m(T_k - d) = sum_j F_{m+j}(T_k) / j! d^j with the 1/j! folded into the table
         int k = __double2int_rn(T * (1.0 / kBoysStep));
         double d = k * kBoysStep - T;
-        const double *g = grid + k * kBoysCols;
+        const double *g = t01 + k * (2 * kBoysTaylor);
         double s0 = __ldg(g + kBoysTaylor - 1);
-        double s1 = WANT1 ? __ldg(g + kBoysTaylor) : 0.0;
+        double s1 = WANT1 ? __ldg(g + 2 * kBoysTaylor - 1) : 0.0;
 #pragma unroll
-        for (int j = kBoysTaylor - 1; j >= 1; --j) {
-            const double dj = d * inv_int(j);
-            s0 = fma(s0, dj, __ldg(g + j - 1));
-            if (WANT1) s1 = fma(s1, dj, __ldg(g + j));
+        for (int j = kBoysTaylor - 2; j >= 0; --j) {
+            s0 = fma(s0, d, __ldg(g + j));
+            if (WANT1) s1 = fma(s1, d, __ldg(g + kBoysTaylor + j));
         }
         F0 = s0;
         F1 = s1;
@@ -160,7 +168,7 @@ __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double
                                          double &w) {
     if (n == 1) {
         double F0, F1;
-        boys_f01<true>(T, tb.boys_grid, F0, F1);
+        boys_f01<true>(T, tb.boys_t01, F0, F1);
         w = F0;
         x = F1 / F0;
         return;

@@ -15,6 +15,9 @@ cudaError_t tables_for_current_device(Tables *out);
 // starts on a 32-bit word of the packed stream) and the widest setup record (n_Rys = 7).
 constexpr long long kSetupChunk = 1LL << 20;
 constexpr int kSetupFieldsMax = 8 + 7 * 10;
+// largest primitive-pair table a plan builds (bytes); larger plans compute the pair
+// quantities per quartet instead
+constexpr double kPairTableMaxBytes = 16.0 * 1024 * 1024 * 1024;
 
 // Launcher of one canonical class kernel in one arithmetic variant.
 using LaunchFn = cudaError_t (*)(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,

@@ -209,6 +209,78 @@ __device__ __forceinline__ void phase_geometry(const ShellsDev &sh, const int4 &
     geo[G_IPQ] = ipq;
 }
 
+// Phase A0 from the plan's primitive-pair table: the same geo values as phase_geometry, with
+// the per-pair part (1/p, P - A, the exponential prefactor) read from the two pair records
+// instead of recomputed for every quartet.
+template <class C>
+__device__ __forceinline__ void phase_geometry_pairs(const ShellsDev &sh,
+                                                     const double *__restrict__ pairs,
+                                                     long long np, const int4 &qt, int prim,
+                                                     double *geo, int &nprim_total) {
+    int na = sh.nprim[qt.x], nb = sh.nprim[qt.y], nc = sh.nprim[qt.z], nd = sh.nprim[qt.w];
+    nprim_total = na * nb * nc * nd;
+    if (prim >= nprim_total) {
+        geo[G_PREF] = 0.0;
+        geo[G_T] = 0.0;
+        for (int s = G_P; s < G_N; ++s)
+            geo[s] = (s == G_P || s == G_Q || s == G_IP || s == G_IQ) ? 1.0 : (s == G_IPQ ? 0.5 : 0.0);
+        return;
+    }
+    int id = prim % nd, t = prim / nd;
+    int ic = t % nc;
+    t /= nc;
+    int ib = t % nb, ia = t / nb;
+    const long long pa = sh.pofs[qt.x] + ia, pb = sh.pofs[qt.y] + ib, pc = sh.pofs[qt.z] + ic,
+                    pd = sh.pofs[qt.w] + id;
+    const double *rab = pairs + (pa * np + pb) * kPairFields;
+    const double *rcd = pairs + (pc * np + pd) * kPairFields;
+    const double p = __ldg(rab + PR_P), ip = __ldg(rab + PR_IP);
+    const double q = __ldg(rcd + PR_P), iq = __ldg(rcd + PR_IP);
+    bool swab = false, swcd = false;
+    if constexpr (C::SWAB_OK) swab = __ldg(sh.exps + pb) > __ldg(sh.exps + pa);
+    if constexpr (C::SWCD_OK) swcd = __ldg(sh.exps + pd) > __ldg(sh.exps + pc);
+    double A[3] = {sh.cx[qt.x], sh.cy[qt.x], sh.cz[qt.x]};
+    double B[3] = {sh.cx[qt.y], sh.cy[qt.y], sh.cz[qt.y]};
+    double Cc[3] = {sh.cx[qt.z], sh.cy[qt.z], sh.cz[qt.z]};
+    double D[3] = {sh.cx[qt.w], sh.cy[qt.w], sh.cz[qt.w]};
+    const double rs = rsqrt(p + q);
+    double pq2 = 0.0;
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+        double AB = A[x] - B[x], CD = Cc[x] - D[x];
+        double PA = __ldg(rab + PR_PAX + x), QC = __ldg(rcd + PR_PAX + x);
+        double PQ = (A[x] + PA) - (Cc[x] + QC);
+        geo[G_PAX + x] = swab ? PA + AB : PA;
+        geo[G_QCX + x] = swcd ? QC + CD : QC;
+        geo[G_PQX + x] = PQ;
+        geo[G_ABX + x] = AB;
+        geo[G_CDX + x] = CD;
+        pq2 += PQ * PQ;
+    }
+    const double ipq = rs * rs;
+    const double two_pi_52 = 34.986836655249725;
+    geo[G_PREF] = two_pi_52 * (ip * iq) * rs * (__ldg(rab + PR_KCN) * __ldg(rcd + PR_KCN));
+    geo[G_T] = (p * q * ipq) * pq2;
+    geo[G_P] = p;
+    geo[G_Q] = q;
+    geo[G_SWAB] = swab ? 1.0 : 0.0;
+    geo[G_SWCD] = swcd ? 1.0 : 0.0;
+    geo[G_IP] = ip;
+    geo[G_IQ] = iq;
+    geo[G_IPQ] = ipq;
+}
+
+// Phase A0 dispatch: the pair table when the plan has one, else the full computation.
+template <class C>
+__device__ __forceinline__ void geometry_of(const ShellsDev &sh, const ClassArgs &args,
+                                            const int4 &qt, int prim, double *geo,
+                                            int &nprim_total) {
+    if (args.pairs != nullptr)
+        phase_geometry_pairs<C>(sh, args.pairs, args.np, qt, prim, geo, nprim_total);
+    else
+        phase_geometry<C>(sh, qt, prim, geo, nprim_total);
+}
+
 // Phase A1: root mu of quartet geometry geo -> B and C values (Rys setup stage), formed in
 // FP64 and rounded to the recurrence type R.  C00 and C00' use the offsets of P and Q from the
 // centres the VRR is built on (phase_geometry).  Classes with L = 0 need only F_0 (no root).
@@ -220,7 +292,7 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
     double x, w;
     if constexpr (LTOT == 0) {
         double F0, F1;
-        boys_f01<false>(geo[G_T], tb.boys_grid, F0, F1);
+        boys_f01<false>(geo[G_T], tb.boys_t01, F0, F1);
         w = F0;
         x = 0.0;
     } else {
@@ -731,7 +803,7 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                     int4 g = args.quartets[q0 + q];
                     int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]),
                                         pick(g, args.perm[2]), pick(g, args.perm[3]));
-                    phase_geometry<C>(sh, qt, prim, geo, np);
+                    geometry_of<C>(sh, args, qt, prim, geo, np);
                 } else {
                     geo[G_PREF] = 0.0;
                     geo[G_T] = 0.0;
@@ -944,7 +1016,7 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
                         pick(g, args.perm[3]));
     double geo[G_N];
     int np = 0;
-    phase_geometry<C>(sh, qt, 0, geo, np);
+    geometry_of<C>(sh, args, qt, 0, geo, np);
     R *o = out + q;
     o[0 * stride] = (R)geo[G_ABX];
     o[1 * stride] = (R)geo[G_ABY];
@@ -1005,7 +1077,7 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
         int nprim = 1;
         for (int prim = 0; prim < nprim; ++prim) {
             double geo[G_N];
-            phase_geometry<C>(sh, qt, prim, geo, nprim);
+            geometry_of<C>(sh, args, qt, prim, geo, nprim);
             R rg[RG_N];
 #pragma unroll
             for (int x = 0; x < 3; ++x) {

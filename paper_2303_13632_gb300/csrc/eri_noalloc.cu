@@ -80,6 +80,8 @@ cudaError_t device_state(DeviceState **out) {
         t.herm_w = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::boys_grid_h)) != cudaSuccess) return e;
         t.boys_grid = static_cast<const double *>(p);
+        if ((e = cudaGetSymbolAddress(&p, device_tables::boys_t01_h)) != cudaSuccess) return e;
+        t.boys_t01 = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::rys_tail_f_h)) != cudaSuccess) return e;
         t.rys_tail = static_cast<const float *>(p);
         for (int i = 0; i <= kRysNmax; ++i) {

@@ -121,6 +121,32 @@ __global__ void histogram_kernel(const uint8_t *__restrict__ keys, long long n,
         if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
 }
 
+// Primitive-pair table: record (pa, pb) at (pa * np + pb) * kPairFields holds p = a + b, 1/p,
+// P - X = -(b/p)(X - Y) and exp(-ab/p |X - Y|^2) cn_a cn_b for primitives pa of shell X and pb
+// of shell Y (Sec. II-A), all in FP64.
+__global__ void pair_table_kernel(const double *__restrict__ cx, const double *__restrict__ cy,
+                                  const double *__restrict__ cz, const double *__restrict__ exps,
+                                  const double *__restrict__ cn, const int *__restrict__ prim_shell,
+                                  long long np, double *__restrict__ out) {
+    const long long total = np * np;
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long pa = i / np, pb = i - pa * np;
+        const int x = prim_shell[pa], y = prim_shell[pb];
+        const double ea = exps[pa], eb = exps[pb];
+        const double p = ea + eb, ip = 1.0 / p;
+        const double ab[3] = {cx[x] - cx[y], cy[x] - cy[y], cz[x] - cz[y]};
+        const double ab2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+        double *o = out + i * kPairFields;
+        o[PR_P] = p;
+        o[PR_IP] = ip;
+        o[PR_PAX] = -eb * ip * ab[0];
+        o[PR_PAY] = -eb * ip * ab[1];
+        o[PR_PAZ] = -eb * ip * ab[2];
+        o[PR_KCN] = exp(-(ea * eb * ip) * ab2) * cn[pa] * cn[pb];
+    }
+}
+
 // Largest |b - a| / max|a| over the quartets (a: FP64 values, b: mixed values) of n quartets of
 // neri values each; quartets with max|a| <= 1e-30 (below the FP32 range once scaled) are
 // skipped.  One warp per quartet; the result (non-negative float) is atomically max-ed in bits.
@@ -162,6 +188,7 @@ struct eri_plan_s {
     int *d_perm = nullptr;       // sorted position -> caller's index
     int *d_err = nullptr;
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
+    double *d_pairs = nullptr;    // primitive-pair table (n_prims^2 records), or null
     // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
     unsigned long long *d_counters = nullptr;
     static constexpr int kSide = 4;
@@ -199,6 +226,7 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_perm);
     cudaFree(p->d_err);
     cudaFree(p->d_setup);
+    cudaFree(p->d_pairs);
     cudaFree(p->d_counters);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     for (int i = 0; i < eri_plan_s::kSide; ++i) {
@@ -251,6 +279,8 @@ ClassArgs class_args(eri_plan_s *p, int cls, double *d_out, int bits, void *d_pa
     a.quartets = p->d_quartets + p->first[cls];
     a.nq = p->count[cls];
     a.err = p->d_err;
+    a.pairs = p->d_pairs;
+    a.np = p->n_prims;
     int neri = class_neri(cls);
     if (d_out) {
         a.out_fp64 = d_out + p->fp64_off[cls];
@@ -537,6 +567,31 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         }
     }
     cudaFree(d_L);
+    // primitive-pair table, when it fits: n_prims^2 records of kPairFields doubles
+    if (!(o.flags & ERI_NO_PAIR_TABLE) && p->nq > 0) {
+        const double bytes = (double)p->n_prims * (double)p->n_prims * kPairFields * sizeof(double);
+        size_t free_b = 0, total_b = 0;
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) free_b = 0;
+        if (bytes <= (double)kPairTableMaxBytes && bytes <= 0.25 * (double)free_b) {
+            std::vector<int> prim_shell(ex.size());
+            for (int s2 = 0; s2 < n_shells; ++s2)
+                for (int k = 0; k < shells[s2].nprim; ++k) prim_shell[pofs[s2] + k] = s2;
+            int *d_ps = nullptr;
+            cudaError_t pe = upload(&d_ps, prim_shell);
+            if (pe == cudaSuccess) pe = cudaMalloc(&p->d_pairs, (size_t)bytes);
+            if (pe == cudaSuccess) {
+                pair_table_kernel<<<4 * 1024, 256>>>(p->d_cx, p->d_cy, p->d_cz, p->d_exps, p->d_cn,
+                                                      d_ps, p->n_prims, p->d_pairs);
+                pe = cudaGetLastError();
+                if (pe == cudaSuccess) pe = cudaDeviceSynchronize();
+            }
+            cudaFree(d_ps);
+            if (pe != cudaSuccess) {
+                free_plan(p);
+                return cuda_status(pe);
+            }
+        }
+    }
     long long f = 0, off = 0;
     for (int c = 0; c < 256; ++c) {
         p->first[c] = f;

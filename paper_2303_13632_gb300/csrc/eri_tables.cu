@@ -13,6 +13,7 @@ static_assert(RYS_TAIL_LEN * (RYS_DEG + 1) == RYS_CHEB_LEN * (RYS_DEG + 1 - RYS_
 static_assert(BOYS_MMAX == eri::kBoysMmax && BOYS_TAYLOR == eri::kBoysTaylor &&
                   BOYS_MCOLS == eri::kBoysCols && BOYS_NGRID == eri::kBoysNgrid,
               "Boys grid mismatch");
+static_assert(BOYS_T01_LEN == 2 * BOYS_TAYLOR * BOYS_NGRID, "F0/F1 Taylor table size");
 
 namespace eri {
 
@@ -34,7 +35,7 @@ cudaError_t tables_for_current_device(Tables *out) {
         Tables t{};
         double *buf = nullptr;
         size_t n = (size_t)RYS_CHEB_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN +
-                   ((size_t)RYS_TAIL_LEN + 1) / 2;
+                   (size_t)BOYS_T01_LEN + ((size_t)RYS_TAIL_LEN + 1) / 2;
         e = cudaMalloc(&buf, n * sizeof(double));
         if (e != cudaSuccess) return e;
         double *p = buf;
@@ -50,6 +51,9 @@ cudaError_t tables_for_current_device(Tables *out) {
         if (e == cudaSuccess) e = cudaMemcpy(p, boys_grid_h, sizeof(boys_grid_h), cudaMemcpyHostToDevice);
         t.boys_grid = p;
         p += BOYS_GRID_LEN;
+        if (e == cudaSuccess) e = cudaMemcpy(p, boys_t01_h, sizeof(boys_t01_h), cudaMemcpyHostToDevice);
+        t.boys_t01 = p;
+        p += BOYS_T01_LEN;
         if (e == cudaSuccess) e = cudaMemcpy(p, rys_tail_f_h, sizeof(rys_tail_f_h), cudaMemcpyHostToDevice);
         t.rys_tail = reinterpret_cast<const float *>(p);
         if (e != cudaSuccess) {

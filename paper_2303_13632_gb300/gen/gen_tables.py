@@ -256,6 +256,21 @@ def main():
     for i in range(0, len(grid), 4):
         lines.append("  " + ", ".join(fmt(v) for v in grid[i:i + 4]) + ",")
     lines.append("};")
+    # Taylor coefficients of F_0 and F_1 about each grid point, already divided by j!, so that
+    # F_0(T_k - d) = sum_j t[j] d^j and F_1(T_k - d) = sum_j t[BOYS_TAYLOR + j] d^j
+    t01 = []
+    for k in range(BOYS_NGRID):
+        T = mp.mpf(k) * mp.mpf(BOYS_STEP)
+        F = [boys_mp(m, T) for m in range(BOYS_TAYLOR + 1)]
+        t01 += [float(F[j] / mp.factorial(j)) for j in range(BOYS_TAYLOR)]
+        t01 += [float(F[j + 1] / mp.factorial(j)) for j in range(BOYS_TAYLOR)]
+    lines.append(f"#define BOYS_T01_LEN {len(t01)}")
+    lines.append("/* F_0 and F_1 Taylor coefficients F_{m+j}(k * BOYS_STEP) / j! at index")
+    lines.append("   k * 2 * BOYS_TAYLOR + m * BOYS_TAYLOR + j */")
+    lines.append("static const double boys_t01_h[BOYS_T01_LEN] = {")
+    for i in range(0, len(t01), 4):
+        lines.append("  " + ", ".join(fmt(v) for v in t01[i:i + 4]) + ",")
+    lines.append("};")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
     print(f"wrote {OUT}: {len(cheb)} Chebyshev coefficients, {len(grid)} Boys values, "

@@ -12,9 +12,9 @@ def class_of(shells, q):
     return ((L[q[0]] * 4 + L[q[1]]) * 4 + L[q[2]]) * 4 + L[q[3]]
 
 
-def gpu_fp64(shells, quartets, precision="fp64"):
+def gpu_fp64(shells, quartets, precision="fp64", pair_table=True):
     """Returns (values in the caller's order as a list of per-quartet arrays)."""
-    plan = api.eri_plan_create(shells, quartets, precision=precision)
+    plan = api.eri_plan_create(shells, quartets, precision=precision, pair_table=pair_table)
     nbytes, _ = api.eri_output_bytes(plan, 0)
     out = torch.empty(max(1, nbytes // 8), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()

@@ -106,6 +106,23 @@ def test_fp64_all_classes(workload, oracle_values):
     assert not bad, f"classes out of tolerance (class id -> max abs err): {bad}"
 
 
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_without_pair_table(workload, oracle_values, precision):
+    """Plans built with ERI_NO_PAIR_TABLE compute the pair quantities per quartet: same
+    tolerances against the oracle, and agreement with the pair-table plan to rounding."""
+    pool, q = workload
+    per, _ = gpu_fp64(pool, q, precision, pair_table=False)
+    ref_pairs, _ = gpu_fp64(pool, q, precision)
+    for i in range(len(q)):
+        ref = oracle_values[i]
+        bmax = np.max(np.abs(ref))
+        if precision == "fp64":
+            assert np.all(fp64_ok(per[i], ref)), i
+            assert np.max(np.abs(per[i] - ref_pairs[i])) <= 1e-13 * bmax + 1e-300, i
+        else:
+            assert np.max(np.abs(per[i] - ref)) <= bmax / 65534.0 + 1e-30, i
+
+
 def test_compressed_16bit_all_classes(workload, oracle_values):
     pool, q = workload
     codes, eps, _ = gpu_compressed(pool, q, 16, "fp64")
@@ -168,12 +185,13 @@ def test_mixed_compressed_16bit(workload, oracle_values):
 
 
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
-def test_contracted_shells(precision):
+@pytest.mark.parametrize("pair_table", [True, False])
+def test_contracted_shells(precision, pair_table):
     """Contraction over primitives (K = 3): sum of primitive quartets, Kahan-compensated in
-    mixed precision."""
+    mixed precision; with and without the primitive-pair table."""
     pool, q = mixed_workload(seed=11, per_class=lambda n: 2 if n > 1000 else 5, K=3)
     vals, offs = oracle.eri_batch(pool, q)
-    per, _ = gpu_fp64(pool, q, precision)
+    per, _ = gpu_fp64(pool, q, precision, pair_table=pair_table)
     for i in range(len(q)):
         ref = vals[offs[i]:offs[i + 1]]
         if precision == "fp64":

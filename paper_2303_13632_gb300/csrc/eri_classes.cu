@@ -16,7 +16,7 @@ namespace eri {
 
 template <int IDX>
 struct Register {
-    static void apply(LaunchFn *table, bool *tpq) {
+    static void apply(LaunchFn *table, KernelInfo *info) {
         if constexpr (IDX < kNumCanonical) {
             if constexpr (IDX % kNumTU == ERI_TU) {
                 constexpr int cls = canonical_class(IDX);
@@ -25,19 +25,21 @@ struct Register {
                 table[cls * kNumVariants + 0] = &launch_class<La, Lb, Lc, Ld, double, false>;
                 table[cls * kNumVariants + 1] = &launch_class<La, Lb, Lc, Ld, float, false>;
                 table[cls * kNumVariants + 2] = &launch_class<La, Lb, Lc, Ld, float, true>;
-                tpq[cls * kNumVariants + 0] = Cfg<La, Lb, Lc, Ld, double>::TPQ;
-                tpq[cls * kNumVariants + 1] = Cfg<La, Lb, Lc, Ld, float>::TPQ;
-                tpq[cls * kNumVariants + 2] = false;
+                info[cls * kNumVariants + 0] = {Cfg<La, Lb, Lc, Ld, double>::TPQ,
+                                                 Cfg<La, Lb, Lc, Ld, double>::USES_SETUP};
+                info[cls * kNumVariants + 1] = {Cfg<La, Lb, Lc, Ld, float>::TPQ,
+                                                 Cfg<La, Lb, Lc, Ld, float>::USES_SETUP};
+                info[cls * kNumVariants + 2] = {false, false};  // contracted: fused kernels
                 // setup records fit the setup buffer (kSetupFieldsMax doubles per quartet)
                 static_assert(Cfg<La, Lb, Lc, Ld, double>::SETUP_FIELDS <= kSetupFieldsMax, "setup");
                 static_assert(Cfg<La, Lb, Lc, Ld, float>::SETUP_FIELDS * sizeof(float) <=
                                   kSetupFieldsMax * sizeof(double), "setup");
             }
-            Register<IDX + 1>::apply(table, tpq);
+            Register<IDX + 1>::apply(table, info);
         }
     }
 };
 
-void ERI_REGISTER_NAME(LaunchFn *table, bool *tpq) { Register<0>::apply(table, tpq); }
+void ERI_REGISTER_NAME(LaunchFn *table, KernelInfo *info) { Register<0>::apply(table, info); }
 
 }  // namespace eri

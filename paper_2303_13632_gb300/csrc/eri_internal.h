@@ -32,8 +32,13 @@ void eri_register_backward(BackwardFn *table);
 
 // Each class translation unit fills table[cls * kNumVariants + variant] for its classes.
 constexpr int kNumTU = 16;
-// tpq[cls * kNumVariants + v] is set when that kernel is the thread-per-quartet one.
-#define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table, bool *tpq);
+// info[cls * kNumVariants + v] describes that launcher.
+struct KernelInfo {
+    bool tpq;    // has a thread-per-quartet kernel (LaunchOpts::force_phase selects the other)
+    bool setup;  // primitive (K = 1) plans run it through the setup kernel: the caller passes
+                 // LaunchOpts::scratch and at most kSetupChunk quartets per launch
+};
+#define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table, KernelInfo *info);
 ERI_DECLARE_REGISTER(0) ERI_DECLARE_REGISTER(1) ERI_DECLARE_REGISTER(2) ERI_DECLARE_REGISTER(3)
 ERI_DECLARE_REGISTER(4) ERI_DECLARE_REGISTER(5) ERI_DECLARE_REGISTER(6) ERI_DECLARE_REGISTER(7)
 ERI_DECLARE_REGISTER(8) ERI_DECLARE_REGISTER(9) ERI_DECLARE_REGISTER(10) ERI_DECLARE_REGISTER(11)

@@ -96,12 +96,18 @@ struct Cfg {
     static constexpr int IBLKP = (La + 1) * (Lc + 1) * JLP;
     static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);  // bra-transferred per (xi, mu)
     static constexpr bool FUSE_BC = HBLK <= 48;             // ket HRR in registers in phase B
-    // thread-per-quartet variant (all intermediates in registers) for the small classes
-    static constexpr bool TPQ = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
-    // FP32 recurrences of the shared-memory kernels with angular momentum on b or d use the
-    // four-index recursion (phase_direct): in FP32 the transfer relation amplifies rounding
-    // by up to about 3^(Lb+Ld).  FP64 keeps the VRR + HRR of Eqs. 6-7.
-    static constexpr bool DIRECT = sizeof(R) == 4 && !TPQ && (Lb + Ld) > 0;
+    // thread-per-quartet kernels (all intermediates in registers): with the FP64 setup inline
+    // for the small classes (TPQ_SMALL); in FP32 up to 100 outputs, reading the records of the
+    // split path's setup kernel (TPQ_SPLIT)
+    static constexpr bool TPQ_SMALL = (sizeof(R) == 4 ? NERI <= 36 : NERI <= 18) && IBLK <= 16;
+    static constexpr bool TPQ_SPLIT = sizeof(R) == 4 && !TPQ_SMALL && NERI <= 100 && IBLK <= 16;
+    static constexpr bool TPQ = TPQ_SMALL || TPQ_SPLIT;
+    // primitive (K = 1) plans run the class through the setup kernel
+    static constexpr bool USES_SETUP = !TPQ_SMALL;
+    // FP32 recurrences with angular momentum on b or d use the four-index recursion
+    // (phase_direct, axis_direct): in FP32 the transfer relation amplifies rounding by up to
+    // about 3^(Lb+Ld).  FP64 and the small inline-setup classes keep the VRR + HRR of Eqs. 6-7.
+    static constexpr bool DIRECT = sizeof(R) == 4 && !TPQ_SMALL && (Lb + Ld) > 0;
     // VRR built on B (D) with the HRR transferring to a (c) where that is the better-
     // conditioned direction; never when b (d) carries no angular momentum
     static constexpr bool SWAB_OK = !DIRECT && Lb > 0;
@@ -1054,11 +1060,104 @@ eri_class_persistent(ShellsDev sh, Tables tb, ClassArgs args, unsigned long long
     }
 }
 
+// The four-index recursion of phase_direct for one (root, axis) in registers, in the layout of
+// axis_2d (I[((i * (Lc+1) + k) * (Lb+1) + j) * (Ld+1) + l]); thread-per-quartet kernels.
+template <class C>
+__device__ __forceinline__ void axis_direct(const typename C::R *b, int xi,
+                                            typename C::R (&I)[C::IBLK]) {
+    using R = typename C::R;
+    constexpr int LB1 = C::Lb + 1, LC1 = C::Lc + 1, LD1 = C::Ld + 1;
+#define ERI_IX(i, k, j, l) ((((i) * LC1 + (k)) * LB1 + (j)) * LD1 + (l))
+    const R cA = b[S_C0X + xi], cC = b[S_C1X + xi];
+    R cB = (R)0, cD = (R)0;
+    if constexpr (C::Lb > 0) cB = b[C::S_CB + xi];
+    if constexpr (C::Ld > 0) cD = b[C::S_CD + xi];
+    const R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
+    I[0] = (xi == 2) ? b[S_WZ] : (R)1;
+#pragma unroll
+    for (int i = 1; i <= C::La; ++i) {
+        R v = cA * I[ERI_IX(i - 1, 0, 0, 0)];
+        if (i > 1) v = fma((R)(i - 1) * b10, I[ERI_IX(i - 2, 0, 0, 0)], v);
+        I[ERI_IX(i, 0, 0, 0)] = v;
+    }
+#pragma unroll
+    for (int j = 1; j <= C::Lb; ++j)
+#pragma unroll
+        for (int i = 0; i <= C::La; ++i) {
+            R v = cB * I[ERI_IX(i, 0, j - 1, 0)];
+            if (j > 1) v = fma((R)(j - 1) * b10, I[ERI_IX(i, 0, j - 2, 0)], v);
+            if (i > 0) v = fma((R)i * b10, I[ERI_IX(i - 1, 0, j - 1, 0)], v);
+            I[ERI_IX(i, 0, j, 0)] = v;
+        }
+#pragma unroll
+    for (int k = 1; k <= C::Lc; ++k)
+#pragma unroll
+        for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+            for (int j = 0; j <= C::Lb; ++j) {
+                R v = cC * I[ERI_IX(i, k - 1, j, 0)];
+                if (k > 1) v = fma((R)(k - 1) * b01, I[ERI_IX(i, k - 2, j, 0)], v);
+                if (i > 0) v = fma((R)i * b00, I[ERI_IX(i - 1, k - 1, j, 0)], v);
+                if (j > 0) v = fma((R)j * b00, I[ERI_IX(i, k - 1, j - 1, 0)], v);
+                I[ERI_IX(i, k, j, 0)] = v;
+            }
+#pragma unroll
+    for (int k = 0; k <= C::Lc; ++k)
+#pragma unroll
+        for (int l = 1; l <= C::Ld; ++l)
+#pragma unroll
+            for (int i = 0; i <= C::La; ++i)
+#pragma unroll
+                for (int j = 0; j <= C::Lb; ++j) {
+                    R v = cD * I[ERI_IX(i, k, j, l - 1)];
+                    if (l > 1) v = fma((R)(l - 1) * b01, I[ERI_IX(i, k, j, l - 2)], v);
+                    if (k > 0) v = fma((R)k * b01, I[ERI_IX(i, k - 1, j, l - 1)], v);
+                    if (i > 0) v = fma((R)i * b00, I[ERI_IX(i - 1, k, j, l - 1)], v);
+                    if (j > 0) v = fma((R)j * b00, I[ERI_IX(i, k, j - 1, l - 1)], v);
+                    I[ERI_IX(i, k, j, l)] = v;
+                }
+#undef ERI_IX
+}
+
 // ---------------------------------------------------------------------------------------
 // Thread-per-quartet kernel for the small classes: each thread runs every stage of one
 // quartet in registers (no shared-memory phases, no barriers before the store), so the FP64
 // setup of all threads overlaps.  Shared memory is used only to pack the compressed tile.
+// PRESET: the geometry and per-root setup come from the setup kernel's records (FP32 only).
+
+// 2-D integrals of one root and the quadrature (Eq. 8) into the thread's accumulators.
 template <class C>
+__device__ __forceinline__ void tpq_root(const typename C::R *bc, const typename C::R *rg,
+                                         typename C::R (&acc)[C::NERI]) {
+    using R = typename C::R;
+    R X[C::IBLK], Y[C::IBLK], Z[C::IBLK];
+    if constexpr (C::DIRECT) {
+        axis_direct<C>(bc, 0, X);
+        axis_direct<C>(bc, 1, Y);
+        axis_direct<C>(bc, 2, Z);
+    } else {
+        axis_2d<C>(bc, rg, 0, X);
+        axis_2d<C>(bc, rg, 1, Y);
+        axis_2d<C>(bc, rg, 2, Z);
+    }
+#pragma unroll
+    for (int a = 0; a < C::NA; ++a)
+#pragma unroll
+        for (int b = 0; b < C::NB; ++b)
+#pragma unroll
+            for (int c = 0; c < C::NC; ++c)
+#pragma unroll
+                for (int d = 0; d < C::ND; ++d) {
+                    constexpr int LB1 = C::Lb + 1, LC1 = C::Lc + 1, LD1 = C::Ld + 1;
+                    const int ix = ((cart_x(C::La, a) * LC1 + cart_x(C::Lc, c)) * LB1 + cart_x(C::Lb, b)) * LD1 + cart_x(C::Ld, d);
+                    const int iy = ((cart_y(C::La, a) * LC1 + cart_y(C::Lc, c)) * LB1 + cart_y(C::Lb, b)) * LD1 + cart_y(C::Ld, d);
+                    const int iz = ((cart_z(C::La, a) * LC1 + cart_z(C::Lc, c)) * LB1 + cart_z(C::Lb, b)) * LD1 + cart_z(C::Ld, d);
+                    const int o = ((a * C::NB + b) * C::NC + c) * C::ND + d;
+                    acc[o] = fma(X[ix] * Y[iy], Z[iz], acc[o]);
+                }
+}
+
+template <class C, bool PRESET = false>
 __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                                          const ClassArgs &args, long long tile,
                                          unsigned char *smem) {
@@ -1071,44 +1170,42 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
 #pragma unroll
     for (int o = 0; o < C::NERI; ++o) acc[o] = (R)0;
     if (live) {
-        int4 g = args.quartets[q0 + tid];
-        int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
-                            pick(g, args.perm[3]));
-        int nprim = 1;
-        for (int prim = 0; prim < nprim; ++prim) {
-            double geo[G_N];
-            geometry_of<C>(sh, args, qt, prim, geo, nprim);
+        if constexpr (PRESET) {
+            // field-major setup records: consecutive threads read consecutive words
+            const R *su = reinterpret_cast<const R *>(args.setup) + (q0 + tid);
+            const long long ss = args.setup_stride;
             R rg[RG_N];
 #pragma unroll
-            for (int x = 0; x < 3; ++x) {
-                rg[RG_ABX + x] = (R)geo[G_ABX + x];
-                rg[RG_CDX + x] = (R)geo[G_CDX + x];
-            }
-            rg[RG_SWAB] = (R)geo[G_SWAB];
-            rg[RG_SWCD] = (R)geo[G_SWCD];
+            for (int f = 0; f < RG_N; ++f) rg[f] = su[f * ss];
 #pragma unroll 1
             for (int mu = 0; mu < C::NRYS; ++mu) {
                 R bc[C::SN];
-                phase_setup<C>(tb, geo, mu, bc);
-                R X[C::IBLK], Y[C::IBLK], Z[C::IBLK];
-                axis_2d<C>(bc, rg, 0, X);
-                axis_2d<C>(bc, rg, 1, Y);
-                axis_2d<C>(bc, rg, 2, Z);
 #pragma unroll
-                for (int a = 0; a < C::NA; ++a)
+                for (int f = 0; f < C::SN; ++f) bc[f] = su[(C::SETUP_GEO + mu * C::SN + f) * ss];
+                tpq_root<C>(bc, rg, acc);
+            }
+        } else {
+            int4 g = args.quartets[q0 + tid];
+            int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
+                                pick(g, args.perm[3]));
+            int nprim = 1;
+            for (int prim = 0; prim < nprim; ++prim) {
+                double geo[G_N];
+                geometry_of<C>(sh, args, qt, prim, geo, nprim);
+                R rg[RG_N];
 #pragma unroll
-                    for (int b = 0; b < C::NB; ++b)
-#pragma unroll
-                        for (int c = 0; c < C::NC; ++c)
-#pragma unroll
-                            for (int d = 0; d < C::ND; ++d) {
-                                constexpr int LB1 = C::Lb + 1, LC1 = C::Lc + 1, LD1 = C::Ld + 1;
-                                const int ix = ((cart_x(C::La, a) * LC1 + cart_x(C::Lc, c)) * LB1 + cart_x(C::Lb, b)) * LD1 + cart_x(C::Ld, d);
-                                const int iy = ((cart_y(C::La, a) * LC1 + cart_y(C::Lc, c)) * LB1 + cart_y(C::Lb, b)) * LD1 + cart_y(C::Ld, d);
-                                const int iz = ((cart_z(C::La, a) * LC1 + cart_z(C::Lc, c)) * LB1 + cart_z(C::Lb, b)) * LD1 + cart_z(C::Ld, d);
-                                const int o = ((a * C::NB + b) * C::NC + c) * C::ND + d;
-                                acc[o] = fma(X[ix] * Y[iy], Z[iz], acc[o]);
-                            }
+                for (int x = 0; x < 3; ++x) {
+                    rg[RG_ABX + x] = (R)geo[G_ABX + x];
+                    rg[RG_CDX + x] = (R)geo[G_CDX + x];
+                }
+                rg[RG_SWAB] = (R)geo[G_SWAB];
+                rg[RG_SWCD] = (R)geo[G_SWCD];
+#pragma unroll 1
+                for (int mu = 0; mu < C::NRYS; ++mu) {
+                    R bc[C::SN];
+                    phase_setup<C>(tb, geo, mu, bc);
+                    tpq_root<C>(bc, rg, acc);
+                }
             }
         }
     }
@@ -1207,11 +1304,11 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
     }
 }
 
-template <class C>
+template <class C, bool PRESET = false>
 __global__ void __launch_bounds__(C::TPQ_THREADS)
 eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     extern __shared__ __align__(16) unsigned char smem[];
-    tpq_tile<C>(sh, tb, args, blockIdx.x, smem);
+    tpq_tile<C, PRESET>(sh, tb, args, blockIdx.x, smem);
 }
 
 template <class C>
@@ -1253,6 +1350,21 @@ cudaError_t launch_class(const ShellsDev &sh, const Tables &tb, const ClassArgs 
             long long tiles = (args.nq + C::TPQ_THREADS - 1) / C::TPQ_THREADS;
             if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
             if (!o.counter) {
+                if constexpr (C::TPQ_SPLIT) {
+                    if (o.scratch) {
+                        // FP64 setup kernel, then the FP32 thread-per-quartet kernel
+                        const long long stride = (args.nq + 31) / 32 * 32;
+                        eri_setup_kernel<C><<<(unsigned)((args.nq + 127) / 128), 128, 0, stream>>>(
+                            sh, tb, args, reinterpret_cast<R *>(o.scratch), stride);
+                        cudaError_t e = cudaGetLastError();
+                        if (e != cudaSuccess) return e;
+                        ClassArgs a2 = args;
+                        a2.setup = o.scratch;
+                        a2.setup_stride = stride;
+                        eri_tpq_kernel<C, true><<<(unsigned)tiles, C::TPQ_THREADS, smem, stream>>>(sh, tb, a2);
+                        return cudaGetLastError();
+                    }
+                }
                 eri_tpq_kernel<C><<<(unsigned)tiles, C::TPQ_THREADS, smem, stream>>>(sh, tb, args);
                 return cudaGetLastError();
             }

@@ -44,18 +44,18 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 DeviceState g_state[kMaxDevices];
 LaunchFn g_table[256 * kNumVariants];
-bool g_tpq_unused[256 * kNumVariants];
+KernelInfo g_info_unused[256 * kNumVariants];
 std::once_flag g_table_once;
 
 void fill_table() {
-    eri_register_tu_0(g_table, g_tpq_unused); eri_register_tu_1(g_table, g_tpq_unused);
-    eri_register_tu_2(g_table, g_tpq_unused); eri_register_tu_3(g_table, g_tpq_unused);
-    eri_register_tu_4(g_table, g_tpq_unused); eri_register_tu_5(g_table, g_tpq_unused);
-    eri_register_tu_6(g_table, g_tpq_unused); eri_register_tu_7(g_table, g_tpq_unused);
-    eri_register_tu_8(g_table, g_tpq_unused); eri_register_tu_9(g_table, g_tpq_unused);
-    eri_register_tu_10(g_table, g_tpq_unused); eri_register_tu_11(g_table, g_tpq_unused);
-    eri_register_tu_12(g_table, g_tpq_unused); eri_register_tu_13(g_table, g_tpq_unused);
-    eri_register_tu_14(g_table, g_tpq_unused); eri_register_tu_15(g_table, g_tpq_unused);
+    eri_register_tu_0(g_table, g_info_unused); eri_register_tu_1(g_table, g_info_unused);
+    eri_register_tu_2(g_table, g_info_unused); eri_register_tu_3(g_table, g_info_unused);
+    eri_register_tu_4(g_table, g_info_unused); eri_register_tu_5(g_table, g_info_unused);
+    eri_register_tu_6(g_table, g_info_unused); eri_register_tu_7(g_table, g_info_unused);
+    eri_register_tu_8(g_table, g_info_unused); eri_register_tu_9(g_table, g_info_unused);
+    eri_register_tu_10(g_table, g_info_unused); eri_register_tu_11(g_table, g_info_unused);
+    eri_register_tu_12(g_table, g_info_unused); eri_register_tu_13(g_table, g_info_unused);
+    eri_register_tu_14(g_table, g_info_unused); eri_register_tu_15(g_table, g_info_unused);
 }
 
 // Device addresses of the __device__ arrays for the current device (host code sees only a

@@ -20,20 +20,20 @@ namespace eri {
 namespace {
 
 LaunchFn g_launch[256 * kNumVariants];
-bool g_tpq[256 * kNumVariants];
+KernelInfo g_info[256 * kNumVariants];
 BackwardFn g_backward[256];
 std::once_flag g_launch_once;
 
 void register_all() {
     eri_register_backward(g_backward);
-    eri_register_tu_0(g_launch, g_tpq); eri_register_tu_1(g_launch, g_tpq);
-    eri_register_tu_2(g_launch, g_tpq); eri_register_tu_3(g_launch, g_tpq);
-    eri_register_tu_4(g_launch, g_tpq); eri_register_tu_5(g_launch, g_tpq);
-    eri_register_tu_6(g_launch, g_tpq); eri_register_tu_7(g_launch, g_tpq);
-    eri_register_tu_8(g_launch, g_tpq); eri_register_tu_9(g_launch, g_tpq);
-    eri_register_tu_10(g_launch, g_tpq); eri_register_tu_11(g_launch, g_tpq);
-    eri_register_tu_12(g_launch, g_tpq); eri_register_tu_13(g_launch, g_tpq);
-    eri_register_tu_14(g_launch, g_tpq); eri_register_tu_15(g_launch, g_tpq);
+    eri_register_tu_0(g_launch, g_info); eri_register_tu_1(g_launch, g_info);
+    eri_register_tu_2(g_launch, g_info); eri_register_tu_3(g_launch, g_info);
+    eri_register_tu_4(g_launch, g_info); eri_register_tu_5(g_launch, g_info);
+    eri_register_tu_6(g_launch, g_info); eri_register_tu_7(g_launch, g_info);
+    eri_register_tu_8(g_launch, g_info); eri_register_tu_9(g_launch, g_info);
+    eri_register_tu_10(g_launch, g_info); eri_register_tu_11(g_launch, g_info);
+    eri_register_tu_12(g_launch, g_info); eri_register_tu_13(g_launch, g_info);
+    eri_register_tu_14(g_launch, g_info); eri_register_tu_15(g_launch, g_info);
 }
 
 int ncart_h(int L) { return (L + 1) * (L + 2) / 2; }
@@ -307,7 +307,7 @@ eri_status_t launch_class_args(eri_plan_s *p, int cls, const ClassArgs &a, int v
     if (!fn) return ERI_E_UNSUPPORTED;
     LaunchOpts o;
     o.device = p->device;
-    const bool split = p->max_nprim == 1 && !g_tpq[c.cls * kNumVariants + variant];
+    const bool split = p->max_nprim == 1 && g_info[c.cls * kNumVariants + variant].setup;
     if (!split) return cuda_status(fn(sh, p->tables, a, stream, o));
     if (!p->d_setup) {
         cudaError_t e = cudaMalloc(&p->d_setup, (size_t)kSetupChunk * kSetupFieldsMax * sizeof(double));
@@ -870,7 +870,7 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
         LaunchFn fn = g_launch[cc * kNumVariants + variant];
         ClassArgs a = class_args(plan, c, nullptr, bits, d_packed, d_scales, off[c]);
         int cand_phase[2] = {0, 1};
-        int n_phase = g_tpq[cc * kNumVariants + variant] ? 2 : 1;
+        int n_phase = g_info[cc * kNumVariants + variant].tpq ? 2 : 1;
         int grids[3] = {0, prop.multiProcessorCount, 2 * prop.multiProcessorCount};
         float best = 1e30f;
         int bp = 0, bg = 0;
@@ -928,7 +928,7 @@ eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_la
     const int v = class_variant(plan, cls);
     const int k = canonicalise(cls).cls * kNumVariants + v;
     if (!g_launch[k]) return ERI_E_UNSUPPORTED;
-    const bool split = plan->max_nprim == 1 && !g_tpq[k];
+    const bool split = plan->max_nprim == 1 && g_info[k].setup;
     *n_launches = split ? 2 * (int32_t)((plan->count[cls] + kSetupChunk - 1) / kSetupChunk) : 1;
     return ERI_OK;
 }

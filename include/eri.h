@@ -281,6 +281,12 @@ eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t n, double 
 eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
                             double *d_w, void *stream);
 
+/* The binary64 -> binary32 -> binary64 conversions the setup stages use (integer arithmetic,
+ * IEEE round to nearest, ties to even; no counterpart in the paper): d_f[i] = (float)d_in[i],
+ * d_back[i] = (double)d_f[i].  Asynchronous on `stream`. */
+eri_status_t eri_convert_device(const double *d_in, int64_t n, float *d_f, double *d_back,
+                                void *stream);
+
 /* Class helpers (no device needed). */
 int32_t eri_class_id(int32_t La, int32_t Lb, int32_t Lc, int32_t Ld);
 /* n_eri = n_ga n_gb n_gc n_gd, n_rys = (La+Lb+Lc+Ld)/2 + 1. */

@@ -237,3 +237,9 @@ def eri_class_shape(cls: int):
     a, b = ctypes.c_int32(), ctypes.c_int32()
     check(_lib.load().eri_class_shape(cls, ctypes.byref(a), ctypes.byref(b)), "eri_class_shape")
     return a.value, b.value
+
+
+def eri_convert_device(x, f_out, back_out, stream=None) -> None:
+    """Integer-pipe binary64 -> binary32 -> binary64 conversions of the setup stages."""
+    check(_lib.load().eri_convert_device(_dev_ptr(x), x.numel(), _dev_ptr(f_out), _dev_ptr(back_out),
+                                         _stream_handle(stream)), "eri_convert_device")

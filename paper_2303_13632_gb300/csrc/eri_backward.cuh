@@ -159,15 +159,20 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
             }
         }
         __syncthreads();
-        // contraction with G: threads over the outputs of one quartet at a time, accumulators
-        // in registers, then a warp-shuffle reduction and one shared atomic per warp
-        for (int q = 0; q < qn; ++q) {
+        // contraction with G: a group of WPQ warps per quartet of the tile (all warps busy
+        // whatever Q is), threads over the quartet's outputs, accumulators in registers, then a
+        // warp-shuffle reduction and one store (one warp per quartet) or shared atomic per warp
+        constexpr int WARPS = C::THREADS / 32;
+        constexpr int WPQ = WARPS / C::Q > 0 ? WARPS / C::Q : 1;
+        const int lane = tid & 31, warp = tid >> 5;
+        const int gth = (warp % WPQ) * 32 + lane;  // thread index within the quartet's group
+        for (int q = warp / WPQ; q < qn; q += WARPS / WPQ) {
             const double *ex = prim_s + q * 8;
             const double *Iq = I_s + (size_t)q * (C::I_BYTES / 8);
             double r[C::NACC];
 #pragma unroll
             for (int k = 0; k < C::NACC; ++k) r[k] = 0.0;
-            for (int o = tid; o < C::oNERI; o += C::THREADS) {
+            for (int o = gth; o < C::oNERI; o += WPQ * 32) {
                 int d = o % C::oND, t = o / C::oND;
                 int c = t % C::oNC;
                 t /= C::oNC;
@@ -216,7 +221,12 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                 double v = r[k];
 #pragma unroll
                 for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-                if ((tid & 31) == 0 && v != 0.0) atomicAdd(acc_s + q * C::NACC + k, v);
+                if (lane == 0) {
+                    if constexpr (WPQ == 1)
+                        acc_s[q * C::NACC + k] = v;  // this warp owns quartet q
+                    else if (v != 0.0)
+                        atomicAdd(acc_s + q * C::NACC + k, v);
+                }
             }
         }
         __syncthreads();

@@ -4,8 +4,8 @@
 // arXiv 2303.13632, Sec. II-C: the Rys quadrature needs the roots t_mu and weights w_mu
 // of order n_Rys for T = rho |P-Q|^2 (the input R_Rys, Eq. 5).  The paper computes them
 // on the CPU in FP64 (footnote of Sec. II-C); here they are evaluated on the GPU in FP64
-// from piecewise Chebyshev series (T below a per-order threshold) or the Gauss-Hermite
-// limit (T above it), both generated offline with 40-digit arithmetic.
+// from piecewise polynomials (Chebyshev fits in monomial form, T below a per-order threshold)
+// or the Gauss-Hermite limit (T above it), both generated offline with 40-digit arithmetic.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -15,7 +15,7 @@ namespace eri {
 
 constexpr int kRysNmax = 9;
 constexpr int kRysDeg = 12;
-constexpr int kRysTail = 8;  // coefficients j >= kRysTail are evaluated in FP32
+constexpr int kRysTail = 10;  // coefficients j >= kRysTail are evaluated in FP32
 constexpr int kBoysMmax = 16;
 constexpr int kBoysTaylor = 10;
 constexpr int kBoysCols = kBoysMmax + kBoysTaylor + 1;
@@ -32,10 +32,84 @@ __device__ __forceinline__ double inv_int(int j) {
     return t[j];
 }
 
+// Conversions between binary64 and binary32 on the integer pipe.  On this part the FP64
+// conversion instructions issue on the FP64 pipe, at the FP64 rate, and so do 64-bit integer
+// operations; the setup stages hand every B, C and weight value to the FP32 recurrences, so
+// they convert with 32-bit integer operations on the two halves instead.  Both are exact
+// IEEE-754 conversions (binary64 -> binary32 rounds to nearest, ties to even), including
+// subnormal results, overflow to infinity and NaN, with no floating-point instruction.
+__device__ __forceinline__ float f64_to_f32(double d) {
+    const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
+    const unsigned int sign = hi & 0x80000000u, ahi = hi & 0x7FFFFFFFu;
+    const unsigned int e = ahi >> 20;
+    if (e - 897u <= 253u) {
+        // normal binary32 result: rebias the exponent (1023 -> 127), keep 20 + 3 fraction
+        // bits, round on the 29 dropped bits (a carry increments the exponent, up to infinity)
+        const unsigned int t = __funnelshift_l(lo, ahi - (896u << 20), 3);
+        const unsigned int rem = lo & 0x1FFFFFFFu;
+        const unsigned int up = (rem > 0x10000000u) | ((rem == 0x10000000u) & t);
+        return __uint_as_float(sign | (t + (up & 1u)));
+    }
+    if (e >= 1151u) {  // beyond the binary32 range: infinity, or NaN (quiet, top payload bits)
+        const bool nan = e == 2047u && ((ahi & 0xFFFFFu) | lo) != 0u;
+        return __uint_as_float(sign | (nan ? 0x7FC00000u | __funnelshift_l(lo, ahi & 0xFFFFFu, 3)
+                                           : 0x7F800000u));
+    }
+    // subnormal binary32 result (or zero): the 53-bit significand shifted right by 926 - e
+    // bits (>= 30), rounded to nearest even; a carry into bit 23 gives the smallest normal
+    const unsigned int sh = 926u - e;
+    if (e == 0u || sh > 54u) return __uint_as_float(sign);
+    const unsigned int mh = (ahi & 0xFFFFFu) | 0x100000u;  // significand bits 32..52
+    // q = significand >> sh; the dropped part compared with half
+    unsigned int q, rem_hi, rem_lo, half_hi, half_lo;
+    if (sh < 32u) {  // sh in [30, 31]
+        q = __funnelshift_r(lo, mh, sh);
+        rem_hi = 0u;
+        rem_lo = lo & ((1u << sh) - 1u);
+        half_hi = 0u;
+        half_lo = 1u << (sh - 1u);
+    } else {
+        const unsigned int s2 = sh - 32u;  // 0..22
+        q = mh >> s2;
+        rem_hi = mh & ((1u << s2) - 1u);
+        rem_lo = lo;
+        half_hi = s2 ? 1u << (s2 - 1u) : 0u;
+        half_lo = s2 ? 0u : 0x80000000u;
+    }
+    const bool gt = rem_hi > half_hi || (rem_hi == half_hi && rem_lo > half_lo);
+    const bool eq = rem_hi == half_hi && rem_lo == half_lo;
+    return __uint_as_float(sign | (q + ((gt || (eq && (q & 1u))) ? 1u : 0u)));
+}
+
+__device__ __forceinline__ double f32_to_f64(float f) {
+    const unsigned int u = __float_as_uint(f);
+    const unsigned int sign = u & 0x80000000u, a = u & 0x7FFFFFFFu;
+    if (a - 0x00800000u < 0x7F000000u)  // normal: exponent field 1..254
+        return __hiloint2double((int)(sign | ((a >> 3) + (896u << 20))), (int)(a << 29));
+    if (a >= 0x7F800000u)  // infinity or NaN: all-ones exponent, fraction moved up
+        return __hiloint2double((int)(sign | 0x7FF00000u | ((a & 0x007FFFFFu) >> 3)), (int)(a << 29));
+    if (a == 0u) return __hiloint2double((int)sign, 0);
+    // subnormal: value a * 2^-149 with its leading one at bit p; fraction bits below it moved
+    // to the top of the 52-bit field
+    const int p = 31 - __clz((int)a);
+    const unsigned int fr = p ? a << (32 - p) : 0u;  // fraction bits below the leading one, left-aligned
+    return __hiloint2double((int)(sign | ((unsigned int)(p + 874) << 20) | (fr >> 12)),
+                            (int)(fr << 20));
+}
+
+// Rounding of an FP64 setup value to the recurrence type R.
+template <typename R>
+__device__ __forceinline__ R to_r(double v) {
+    if constexpr (sizeof(R) == 4)
+        return f64_to_f32(v);
+    else
+        return v;
+}
+
 // Device addresses of the generated tables (see eri_tables.cu).
 struct Tables {
-    const double *rys_cheb;
-    const float *rys_tail;  // FP32 copies of coefficients kRysTail..kRysDeg of every series
+    const double *rys_poly;  // monomial coefficients of the Rys root/weight pieces
+    const float *rys_tail;   // FP32 copies of coefficients kRysTail..kRysDeg of every piece
     const double *herm_x2;
     const double *herm_w;
     const double *boys_grid;
@@ -119,10 +193,12 @@ __device__ __forceinline__ void boys_eval(int mmax, double T, const double *__re
 template <bool WANT1>
 __device__ __forceinline__ void boys_f01(double T, const double *__restrict__ t01, double &F0,
                                          double &F1) {
-    if (T < kBoysTmax) {
+    // grid point from an FP32 copy of T (no FP64 conversion instruction): any point within
+    // 0.05 (plus FP32 rounding) serves, since d below is formed exactly in FP64
+    const int k = __float2int_rn(f64_to_f32(T) * (float)(1.0 / kBoysStep));
+    if (k <= (int)(kBoysTmax / kBoysStep)) {
         // F_m(T_k - d) = sum_j F_{m+j}(T_k) / j! d^j with the 1/j! folded into the table
-        int k = __double2int_rn(T * (1.0 / kBoysStep));
-        double d = k * kBoysStep - T;
+        double d = fma(f32_to_f64((float)k), kBoysStep, -T);
         const double *g = t01 + k * (2 * kBoysTaylor);
         double s0 = __ldg(g + kBoysTaylor - 1);
         double s1 = WANT1 ? __ldg(g + 2 * kBoysTaylor - 1) : 0.0;
@@ -139,28 +215,20 @@ __device__ __forceinline__ void boys_f01(double T, const double *__restrict__ t0
     }
 }
 
-// Chebyshev series sum_j c_j T_j(u) by Clenshaw's recurrence.  The terms j >= kRysTail sum to
-// less than 1e-9 of the series' smallest value on the piece (checked when the tables are
-// generated), so that part of the recurrence runs in FP32 from FP32 coefficients without
-// disturbing the FP64 result by more than 1e-16 relative; the rest runs in FP64.
-__device__ __forceinline__ double cheb_eval(const double *__restrict__ c,
-                                            const float *__restrict__ ct, double u) {
-    const float u2f = 2.0f * (float)u;
-    float b1f = 0.0f, b2f = 0.0f;
+// Polynomial sum_j a_j u^j of degree kRysDeg by Horner's rule: the terms j >= kRysTail
+// (below 1e-9 of the value on every piece, checked when the tables are generated) in FP32 from
+// FP32 coefficients and u rounded to FP32, the rest in FP64; the result stays accurate to
+// FP64 rounding (verified by emulating exactly this evaluation at generation time).
+__device__ __forceinline__ double poly_eval(const double *__restrict__ a,
+                                            const float *__restrict__ at, double u) {
+    const float uf = f64_to_f32(u);
+    float sf = __ldg(at + (kRysDeg - kRysTail));
 #pragma unroll
-    for (int j = kRysDeg; j >= kRysTail; --j) {
-        float t = fmaf(u2f, b1f, __ldg(ct + (j - kRysTail)) - b2f);
-        b2f = b1f;
-        b1f = t;
-    }
-    double b1 = (double)b1f, b2 = (double)b2f, u2 = 2.0 * u;
+    for (int j = kRysDeg - 1; j >= kRysTail; --j) sf = fmaf(sf, uf, __ldg(at + (j - kRysTail)));
+    double s = f32_to_f64(sf);
 #pragma unroll
-    for (int j = kRysTail - 1; j >= 1; --j) {
-        double t = fma(u2, b1, __ldg(c + j) - b2);
-        b2 = b1;
-        b1 = t;
-    }
-    return fma(u, b1, __ldg(c) - b2);
+    for (int j = kRysTail - 1; j >= 0; --j) s = fma(s, u, __ldg(a + j));
+    return s;
 }
 
 // Root mu (0-based, ascending) and weight of the order-n Rys rule at T.
@@ -173,14 +241,17 @@ __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double
         x = F1 / F0;
         return;
     }
-    if (T < (double)tb.tasym[n]) {
-        int k = (int)T;
-        double u = 2.0 * (T - k) - 1.0;
+    // unit interval from an FP32 copy of T (no FP64 conversion instruction); when FP32
+    // rounding lifts T to the next integer (T < 90: by less than 4e-6), u lands within 1e-5
+    // below -1, where the degree-12 fit still holds to the same accuracy
+    const int k = (int)f64_to_f32(T);
+    if (k < tb.tasym[n]) {
+        double u = 2.0 * (T - f32_to_f64((float)k)) - 1.0;
         const long long f = (tb.offset[n] / (kRysDeg + 1)) + (long long)k * (2 * n) + 2 * mu;
-        const double *c = tb.rys_cheb + f * (kRysDeg + 1);
+        const double *c = tb.rys_poly + f * (kRysDeg + 1);
         const float *ct = tb.rys_tail + f * (kRysDeg + 1 - kRysTail);
-        x = cheb_eval(c, ct, u);
-        w = cheb_eval(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTail), u);
+        x = poly_eval(c, ct, u);
+        w = poly_eval(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTail), u);
     } else {
         int h = tb.herm_off[n] + mu;
         x = __ldg(tb.herm_x2 + h) / T;

@@ -39,10 +39,14 @@ struct RTraits;
 template <>
 struct RTraits<double> {
     static __device__ __forceinline__ double round_away(double v) { return round(v); }
+    static __device__ __forceinline__ double to_f64(double v) { return v; }
+    static __device__ __forceinline__ bool finite(double v) { return fabs(v) <= 1.7976931348623157e308; }
 };
 template <>
 struct RTraits<float> {
     static __device__ __forceinline__ float round_away(float v) { return roundf(v); }
+    static __device__ __forceinline__ double to_f64(float v) { return f32_to_f64(v); }
+    static __device__ __forceinline__ bool finite(float v) { return fabsf(v) <= 3.4028234663852886e38f; }
 };
 
 // Two's complement bits of an integral value |v| <= 2^{bits-1} - 1.  In FP32 and for widths up
@@ -304,30 +308,30 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
     } else {
         rys_root(tb, C::NRYS, mu, geo[G_T], x, w);
     }
-    bc[S_WZ] = (R)(geo[G_PREF] * w);
+    bc[S_WZ] = to_r<R>(geo[G_PREF] * w);
     if constexpr (LTOT > 0) {
         double p = geo[G_P], q = geo[G_Q];
         double ipq = geo[G_IPQ];
         double fq = q * x * ipq, fp = p * x * ipq;
-        bc[S_B00] = (R)(0.5 * x * ipq);
-        bc[S_B10] = (R)((1.0 - fq) * (0.5 * geo[G_IP]));
-        bc[S_B01] = (R)((1.0 - fp) * (0.5 * geo[G_IQ]));
+        bc[S_B00] = to_r<R>(0.5 * x * ipq);
+        bc[S_B10] = to_r<R>((1.0 - fq) * (0.5 * geo[G_IP]));
+        bc[S_B01] = to_r<R>((1.0 - fp) * (0.5 * geo[G_IQ]));
 #pragma unroll
         for (int s = 0; s < 3; ++s) {
             double pq = geo[G_PQX + s];
-            bc[S_C0X + s] = (R)(geo[G_PAX + s] - fq * pq);
-            bc[S_C1X + s] = (R)(geo[G_QCX + s] + fp * pq);
+            bc[S_C0X + s] = to_r<R>(geo[G_PAX + s] - fq * pq);
+            bc[S_C1X + s] = to_r<R>(geo[G_QCX + s] + fp * pq);
         }
         // four-index path: P - B = (P - A) + (A - B), Q - D = (Q - C) + (C - D)
         if constexpr (C::DIRECT && C::Lb > 0) {
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                bc[C::S_CB + s] = (R)((geo[G_PAX + s] + geo[G_ABX + s]) - fq * geo[G_PQX + s]);
+                bc[C::S_CB + s] = to_r<R>((geo[G_PAX + s] + geo[G_ABX + s]) - fq * geo[G_PQX + s]);
         }
         if constexpr (C::DIRECT && C::Ld > 0) {
 #pragma unroll
             for (int s = 0; s < 3; ++s)
-                bc[C::S_CD + s] = (R)((geo[G_QCX + s] + geo[G_CDX + s]) + fp * geo[G_PQX + s]);
+                bc[C::S_CD + s] = to_r<R>((geo[G_QCX + s] + geo[G_CDX + s]) + fp * geo[G_PQX + s]);
         }
     }
 }
@@ -819,14 +823,14 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 }
                 if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
                 R *rg = rg_s + q * RG_N;
-                rg[RG_ABX] = (R)geo[G_ABX];
-                rg[RG_ABY] = (R)geo[G_ABY];
-                rg[RG_ABZ] = (R)geo[G_ABZ];
-                rg[RG_CDX] = (R)geo[G_CDX];
-                rg[RG_CDY] = (R)geo[G_CDY];
-                rg[RG_CDZ] = (R)geo[G_CDZ];
-                rg[RG_SWAB] = (R)geo[G_SWAB];
-                rg[RG_SWCD] = (R)geo[G_SWCD];
+                rg[RG_ABX] = to_r<R>(geo[G_ABX]);
+                rg[RG_ABY] = to_r<R>(geo[G_ABY]);
+                rg[RG_ABZ] = to_r<R>(geo[G_ABZ]);
+                rg[RG_CDX] = to_r<R>(geo[G_CDX]);
+                rg[RG_CDY] = to_r<R>(geo[G_CDY]);
+                rg[RG_CDZ] = to_r<R>(geo[G_CDZ]);
+                rg[RG_SWAB] = to_r<R>(geo[G_SWAB]);
+                rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
             }
             __syncthreads();
             // A1: roots, weights, B and C per (quartet, root)
@@ -884,9 +888,8 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 if (b < C::NB) {
 #pragma unroll
                     for (int d = 0; d < C::ND; ++d) {
-                        double v = (double)acc[bb][d];
-                        bad |= !(fabs(v) <= 1.7976931348623157e308);
-                        o[b * st1 + d * st3] = v;
+                        bad |= !RTraits<R>::finite(acc[bb][d]);
+                        o[b * st1 + d * st3] = RTraits<R>::to_f64(acc[bb][d]);
                     }
                 }
             }
@@ -1024,14 +1027,14 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
     int np = 0;
     geometry_of<C>(sh, args, qt, 0, geo, np);
     R *o = out + q;
-    o[0 * stride] = (R)geo[G_ABX];
-    o[1 * stride] = (R)geo[G_ABY];
-    o[2 * stride] = (R)geo[G_ABZ];
-    o[3 * stride] = (R)geo[G_CDX];
-    o[4 * stride] = (R)geo[G_CDY];
-    o[5 * stride] = (R)geo[G_CDZ];
-    o[6 * stride] = (R)geo[G_SWAB];
-    o[7 * stride] = (R)geo[G_SWCD];
+    o[0 * stride] = to_r<R>(geo[G_ABX]);
+    o[1 * stride] = to_r<R>(geo[G_ABY]);
+    o[2 * stride] = to_r<R>(geo[G_ABZ]);
+    o[3 * stride] = to_r<R>(geo[G_CDX]);
+    o[4 * stride] = to_r<R>(geo[G_CDY]);
+    o[5 * stride] = to_r<R>(geo[G_CDZ]);
+    o[6 * stride] = to_r<R>(geo[G_SWAB]);
+    o[7 * stride] = to_r<R>(geo[G_SWCD]);
 #pragma unroll 1
     for (int mu = 0; mu < C::NRYS; ++mu) {
         R bc[C::SN];
@@ -1195,11 +1198,11 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                 R rg[RG_N];
 #pragma unroll
                 for (int x = 0; x < 3; ++x) {
-                    rg[RG_ABX + x] = (R)geo[G_ABX + x];
-                    rg[RG_CDX + x] = (R)geo[G_CDX + x];
+                    rg[RG_ABX + x] = to_r<R>(geo[G_ABX + x]);
+                    rg[RG_CDX + x] = to_r<R>(geo[G_CDX + x]);
                 }
-                rg[RG_SWAB] = (R)geo[G_SWAB];
-                rg[RG_SWCD] = (R)geo[G_SWCD];
+                rg[RG_SWAB] = to_r<R>(geo[G_SWAB]);
+                rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
 #pragma unroll 1
                 for (int mu = 0; mu < C::NRYS; ++mu) {
                     R bc[C::SN];
@@ -1223,9 +1226,9 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                     for (int c = 0; c < C::NC; ++c)
 #pragma unroll
                         for (int d = 0; d < C::ND; ++d) {
-                            double v = (double)acc[((a * C::NB + b) * C::NC + c) * C::ND + d];
-                            bad |= !(fabs(v) <= 1.7976931348623157e308);
-                            out[a * st0 + b * st1 + c * st2 + d * st3] = v;
+                            const R v = acc[((a * C::NB + b) * C::NC + c) * C::ND + d];
+                            bad |= !RTraits<R>::finite(v);
+                            out[a * st0 + b * st1 + c * st2 + d * st3] = RTraits<R>::to_f64(v);
                         }
             if (bad) atomicOr(args.err, 1);
         }

@@ -72,8 +72,8 @@ cudaError_t device_state(DeviceState **out) {
         Tables t{};
         if ((e = cudaGetSymbolAddress(&p, g_noalloc_scratch)) != cudaSuccess) return e;
         s.scratch = p;
-        if ((e = cudaGetSymbolAddress(&p, device_tables::rys_cheb_h)) != cudaSuccess) return e;
-        t.rys_cheb = static_cast<const double *>(p);
+        if ((e = cudaGetSymbolAddress(&p, device_tables::rys_poly_h)) != cudaSuccess) return e;
+        t.rys_poly = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::rys_herm_x2_h)) != cudaSuccess) return e;
         t.herm_x2 = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::rys_herm_w_h)) != cudaSuccess) return e;

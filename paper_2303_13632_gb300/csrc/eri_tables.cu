@@ -9,7 +9,7 @@
 static_assert(RYS_NMAX == eri::kRysNmax, "table order mismatch");
 static_assert(RYS_DEG == eri::kRysDeg, "table degree mismatch");
 static_assert(RYS_TAIL == eri::kRysTail, "table tail mismatch");
-static_assert(RYS_TAIL_LEN * (RYS_DEG + 1) == RYS_CHEB_LEN * (RYS_DEG + 1 - RYS_TAIL), "tail size");
+static_assert(RYS_TAIL_LEN * (RYS_DEG + 1) == RYS_POLY_LEN * (RYS_DEG + 1 - RYS_TAIL), "tail size");
 static_assert(BOYS_MMAX == eri::kBoysMmax && BOYS_TAYLOR == eri::kBoysTaylor &&
                   BOYS_MCOLS == eri::kBoysCols && BOYS_NGRID == eri::kBoysNgrid,
               "Boys grid mismatch");
@@ -34,14 +34,14 @@ cudaError_t tables_for_current_device(Tables *out) {
     if (!g_tables_ready[dev]) {
         Tables t{};
         double *buf = nullptr;
-        size_t n = (size_t)RYS_CHEB_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN +
+        size_t n = (size_t)RYS_POLY_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN +
                    (size_t)BOYS_T01_LEN + ((size_t)RYS_TAIL_LEN + 1) / 2;
         e = cudaMalloc(&buf, n * sizeof(double));
         if (e != cudaSuccess) return e;
         double *p = buf;
-        e = cudaMemcpy(p, rys_cheb_h, sizeof(rys_cheb_h), cudaMemcpyHostToDevice);
-        t.rys_cheb = p;
-        p += RYS_CHEB_LEN;
+        e = cudaMemcpy(p, rys_poly_h, sizeof(rys_poly_h), cudaMemcpyHostToDevice);
+        t.rys_poly = p;
+        p += RYS_POLY_LEN;
         if (e == cudaSuccess) e = cudaMemcpy(p, rys_herm_x2_h, sizeof(rys_herm_x2_h), cudaMemcpyHostToDevice);
         t.herm_x2 = p;
         p += RYS_HERM_LEN;
@@ -93,6 +93,14 @@ __global__ void rys_kernel(Tables tb, int nroots, const double *__restrict__ T, 
     W[i] = w;
 }
 
+__global__ void convert_kernel(const double *in, long long n, float *f, double *back) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float v = f64_to_f32(in[i]);
+    f[i] = v;
+    back[i] = f32_to_f64(v);
+}
+
 }  // namespace eri
 
 using namespace eri;
@@ -118,5 +126,14 @@ extern "C" eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_
     long long total = n * nroots;
     long long blocks = (total + 255) / 256;
     rys_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, nroots, d_T, n, d_x, d_w);
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}
+
+
+extern "C" eri_status_t eri_convert_device(const double *d_in, int64_t n, float *d_f, double *d_back,
+                                           void *stream) {
+    if (n < 0 || (n > 0 && (!d_in || !d_f || !d_back))) return ERI_E_INVALID;
+    if (n == 0) return ERI_OK;
+    convert_kernel<<<(unsigned)((n + 255) / 256), 256, 0, (cudaStream_t)stream>>>(d_in, n, d_f, d_back);
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
 }

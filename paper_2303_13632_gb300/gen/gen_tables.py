@@ -4,13 +4,16 @@
 
 Writes ``csrc/eri_tables.inc`` with
   * Rys roots x_mu = t_mu^2 and weights w_mu of the weight exp(-T t^2) on t in [0, 1]
-    (Sec. II-C, Eq. 5 inputs R_Rys), for n_Rys = 1..RYS_NMAX, as piecewise Chebyshev
-    series of degree RYS_DEG on unit intervals of T in [0, T_asym(n)), and the
-    2n-point Gauss-Hermite nodes/weights for the large-T limit
+    (Sec. II-C, Eq. 5 inputs R_Rys), for n_Rys = 1..RYS_NMAX, as piecewise polynomials of
+    degree RYS_DEG in u = 2(T - k) - 1 on unit intervals [k, k+1) of T in [0, T_asym(n)):
+    fitted as Chebyshev series (interpolation at Chebyshev points) and converted exactly, at
+    40 digits, to monomial coefficients so the device evaluates them by Horner's rule (one
+    FMA per term); and the 2n-point Gauss-Hermite nodes/weights for the large-T limit
         x_mu = u_mu^2 / T,  w_mu = H_mu / sqrt(T)      (T >= T_asym(n));
-  * FP32 copies of the Chebyshev coefficients j >= RYS_TAIL: over every piece their sum is
-    below 1e-9 of the smallest |value| of the series (checked here), so evaluating that tail of
-    Clenshaw's recurrence in FP32 keeps the result accurate to better than 1e-16 relative;
+  * FP32 copies of the monomial coefficients j >= RYS_TAIL: the device runs that part of
+    Horner's rule in FP32 (with u rounded to FP32) and the rest in FP64.  The tail is below
+    1e-9 of the value over every piece, and the whole evaluation, emulated here with numpy
+    float32, is verified against fresh high-precision values before the file is written;
   * the Boys function F_m(T_k) on the grid T_k = k * BOYS_STEP (k < BOYS_NGRID) for
     m = 0..BOYS_MCOLS-1, used by a Taylor expansion plus downward recursion.
 
@@ -32,8 +35,8 @@ import numpy as np
 mp.mp.dps = 40
 
 RYS_NMAX = 9          # orders needed: forward L <= 12 -> 7; derivative classes need up to 9
-RYS_DEG = 12          # Chebyshev degree per unit interval
-RYS_TAIL = 8          # coefficients j >= RYS_TAIL are also stored as FP32 (evaluated in FP32)
+RYS_DEG = 12          # polynomial degree per unit interval
+RYS_TAIL = 10         # coefficients j >= RYS_TAIL are also stored as FP32 (evaluated in FP32)
 GL_N = 160            # Gauss-Legendre points discretising the Rys measure
 BOYS_STEP = 0.1
 BOYS_TMAX = 50.0      # F_m(T) for T >= BOYS_TMAX comes from the asymptotic form
@@ -145,15 +148,34 @@ def chebyshev_piece(n, a, b, deg):
                             for k in range(deg + 1)) * 2 / (deg + 1)
                 c.append(s)
             c[0] /= 2
-            coefs.append([float(v) for v in c])
+            coefs.append(c)
     return coefs
 
 
-def clenshaw(c, u):
-    b1 = b2 = 0.0
-    for cj in reversed(c[1:]):
-        b1, b2 = 2 * u * b1 - b2 + cj, b1
-    return u * b1 - b2 + c[0]
+def cheb_to_monomial(c):
+    """Monomial coefficients a_i of sum_j c_j T_j(u) (exact integer recurrence, mp arithmetic)."""
+    deg = len(c) - 1
+    Tm = [[0] * (deg + 1) for _ in range(deg + 1)]
+    Tm[0][0] = 1
+    if deg >= 1:
+        Tm[1][1] = 1
+    for j in range(2, deg + 1):
+        for i in range(deg + 1):
+            Tm[j][i] = (2 * Tm[j - 1][i - 1] if i > 0 else 0) - Tm[j - 2][i]
+    return [mp.fsum(c[j] * Tm[j][i] for j in range(deg + 1)) for i in range(deg + 1)]
+
+
+def horner_split(a, u):
+    """The device evaluation: terms j >= RYS_TAIL by Horner in FP32 on float32(u), the rest in
+    FP64."""
+    uf = np.float32(u)
+    sf = np.float32(a[-1])
+    for j in range(len(a) - 2, RYS_TAIL - 1, -1):
+        sf = np.float32(np.float32(sf * uf) + np.float32(a[j]))
+    s = float(sf)
+    for j in range(RYS_TAIL - 1, -1, -1):
+        s = s * u + a[j]
+    return s
 
 
 def boys_mp(m, T):
@@ -181,6 +203,7 @@ def main():
     tasym, offsets, cheb, hx, hw = [0], [0], [], [0.0], [0.0]
     hoff = [0, 1]
     worst = 0.0
+    tail_worst = 0.0
     for n in range(1, RYS_NMAX + 1):
         herm = hermite_positive(n)
         T = 30
@@ -191,49 +214,49 @@ def main():
         tasym.append(T)
         offsets.append(len(cheb))
         for k in range(T):
-            piece = chebyshev_piece(n, k, k + 1, RYS_DEG)
-            for _ in range(3):
+            piece = [cheb_to_monomial(c) for c in chebyshev_piece(n, k, k + 1, RYS_DEG)]
+            piece_d = [[float(v) for v in a] for a in piece]
+            for _ in range(8):
                 Tt = k + rng.random()
                 x, w = rys_roots_weights(n, Tt)
                 u = 2 * (Tt - k) - 1
                 for mu in range(n):
                     worst = max(worst,
-                                abs(clenshaw(piece[2 * mu], u) - float(x[mu])) / float(x[mu]),
-                                abs(clenshaw(piece[2 * mu + 1], u) - float(w[mu])) / float(w[mu]))
-            for f in piece:
+                                abs(horner_split(piece_d[2 * mu], u) - float(x[mu])) / float(x[mu]),
+                                abs(horner_split(piece_d[2 * mu + 1], u) - float(w[mu])) / float(w[mu]))
+            # tail bound: |sum_{j >= RYS_TAIL} a_j u^j| / |p(u)| on a grid of the piece
+            uu = np.linspace(-1.0, 1.0, 41)
+            for a, ad in zip(piece, piece_d):
+                pv = np.array([float(mp.polyval(a[::-1], mp.mpf(v))) for v in uu])
+                tv = np.abs(sum(ad[j] * uu ** j for j in range(RYS_TAIL, RYS_DEG + 1)))
+                tail_worst = max(tail_worst, float(np.max(tv / np.abs(pv))))
+            for f in piece_d:
                 cheb.extend(f)
         for u, h in herm:
             hx.append(float(u * u))
             hw.append(float(h))
         hoff.append(len(hx))
-        print(f"n={n}: T_asym={T}, pieces={T}, worst so far {worst:.3e}, {time.time() - t0:.0f}s",
-              flush=True)
+        print(f"n={n}: T_asym={T}, pieces={T}, worst so far {worst:.3e}, tail {tail_worst:.2e}, "
+              f"{time.time() - t0:.0f}s", flush=True)
     if worst > 6e-16:
-        sys.exit(f"Chebyshev fit check failed: {worst}")
-    # tail bound: sum_{j >= RYS_TAIL} |c_j| relative to min |series| on the piece
-    tail_worst = 0.0
-    nfun = len(cheb) // (RYS_DEG + 1)
-    uu = np.linspace(-1.0, 1.0, 41)
-    for f in range(nfun):
-        c = np.array(cheb[f * (RYS_DEG + 1):(f + 1) * (RYS_DEG + 1)])
-        vmin = np.min(np.abs(np.polynomial.chebyshev.chebval(uu, c)))
-        tail_worst = max(tail_worst, float(np.sum(np.abs(c[RYS_TAIL:])) / vmin))
+        sys.exit(f"polynomial fit check failed: {worst}")
     if tail_worst > 1e-9:
-        sys.exit(f"Chebyshev tail too large for FP32 evaluation: {tail_worst}")
+        sys.exit(f"polynomial tail too large for FP32 evaluation: {tail_worst}")
+    nfun = len(cheb) // (RYS_DEG + 1)
     tail = [float(np.float32(v)) for f in range(nfun)
             for v in cheb[f * (RYS_DEG + 1) + RYS_TAIL:(f + 1) * (RYS_DEG + 1)]]
     lines.append("/* first T of the Gauss-Hermite regime for n = index */")
     lines.append("static const int rys_tasym_h[RYS_NMAX + 1] = {" + ", ".join(map(str, tasym)) + "};")
-    lines.append("/* offset (doubles) of the pieces of order n; piece k of order n holds 2n series of")
-    lines.append("   RYS_DEG+1 coefficients: x_1, w_1, x_2, w_2, ... on T in [k, k+1) */")
+    lines.append("/* offset (doubles) of the pieces of order n; piece k of order n holds 2n polynomials of")
+    lines.append("   RYS_DEG+1 monomial coefficients in u = 2(T - k) - 1: x_1, w_1, x_2, w_2, ... */")
     lines.append("static const long rys_offset_h[RYS_NMAX + 1] = {" + ", ".join(map(str, offsets)) + "};")
-    lines.append(f"#define RYS_CHEB_LEN {len(cheb)}")
-    lines.append("static const double rys_cheb_h[RYS_CHEB_LEN] = {")
+    lines.append(f"#define RYS_POLY_LEN {len(cheb)}")
+    lines.append("static const double rys_poly_h[RYS_POLY_LEN] = {")
     for i in range(0, len(cheb), 4):
         lines.append("  " + ", ".join(fmt(v) for v in cheb[i:i + 4]) + ",")
     lines.append("};")
     lines.append(f"#define RYS_TAIL {RYS_TAIL}")
-    lines.append(f"/* FP32 copies of coefficients RYS_TAIL..RYS_DEG of each series (worst tail/min|f| = {tail_worst:.2e}) */")
+    lines.append(f"/* FP32 copies of coefficients RYS_TAIL..RYS_DEG of each polynomial (worst tail/|p| = {tail_worst:.2e}) */")
     lines.append(f"#define RYS_TAIL_LEN {len(tail)}")
     lines.append("static const float rys_tail_f_h[RYS_TAIL_LEN] = {")
     for i in range(0, len(tail), 5):
@@ -273,7 +296,7 @@ def main():
     lines.append("};")
     with open(OUT, "w") as f:
         f.write("\n".join(lines) + "\n")
-    print(f"wrote {OUT}: {len(cheb)} Chebyshev coefficients, {len(grid)} Boys values, "
+    print(f"wrote {OUT}: {len(cheb)} polynomial coefficients, {len(grid)} Boys values, "
           f"fit check {worst:.3e}, {time.time() - t0:.0f}s")
 
 

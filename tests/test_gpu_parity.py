@@ -57,6 +57,37 @@ def oracle_values(workload):
     return [vals[offs[i]:offs[i + 1]] for i in range(len(q))]
 
 
+def test_integer_pipe_conversions_match_ieee():
+    """The setup stages' binary64 -> binary32 rounding (integer arithmetic) against numpy's
+    IEEE casts: random magnitudes across the binary32 range, exact ties at the 29th bit, the
+    largest finite values, subnormal results, zeros, infinities and NaN."""
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(200000) * np.exp(rng.uniform(-95.0, 95.0, 200000))
+    base = rng.integers(0, 2**52, 20000, dtype=np.uint64) & ~np.uint64((1 << 29) - 1)
+    expo = rng.integers(897, 1150, 20000, dtype=np.uint64) << np.uint64(52)
+    ties = (expo | base | np.uint64(1 << 28)).view(np.float64)  # exactly halfway
+    near = (expo | base | np.uint64((1 << 28) - 1)).view(np.float64)
+    special = np.array([0.0, -0.0, 1.0, -1.0, 3.4028234663852886e38, 3.4028235677973366e38,
+                        3.5e38, 1e300, -1e300, 1.1754943508222875e-38, 1.1754942e-38, 1e-40,
+                        1.4e-45, 7e-46, 1e-50, 5e-324, np.inf, -np.inf, np.nan])
+    h = np.concatenate([x, ties, -ties, near, special])
+    d = torch.as_tensor(h, device="cuda")
+    f = torch.empty(len(h), dtype=torch.float32, device="cuda")
+    back = torch.empty(len(h), dtype=torch.float64, device="cuda")
+    api.eri_convert_device(d, f, back)
+    torch.cuda.synchronize()
+    with np.errstate(over="ignore"):
+        ref = h.astype(np.float32)
+    got = f.cpu().numpy()
+    assert np.array_equal(got.view(np.uint32), ref.view(np.uint32)) or \
+        np.array_equal(np.isnan(got), np.isnan(ref)) and \
+        np.array_equal(got[~np.isnan(ref)].view(np.uint32), ref[~np.isnan(ref)].view(np.uint32))
+    bk = back.cpu().numpy()
+    ok = ~np.isnan(ref)
+    assert np.array_equal(bk[ok].view(np.uint64), ref[ok].astype(np.float64).view(np.uint64))
+    assert np.all(np.isnan(bk[~ok]))
+
+
 def test_boys_device_matches_oracle():
     Ts = np.concatenate([[0.0, 1e-12, 1e-6, 0.05, 0.0999, 0.1, 0.15, 35.94, 35.96, 36.0, 49.94,
                           49.96, 49.999, 50.0, 50.0001, 1e3, 1e6],

@@ -59,6 +59,24 @@ def classes():
 ONLY = None  # --classes: restrict the sweep to these class ids (profiling runs only)
 
 
+def max_over_ranks(value: float, dist, device) -> float:
+    """The largest value over the ranks (the slowest rank's step time); `dist` is None with one
+    process."""
+    if dist is None:
+        return value
+    import torch
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_geris(eris_per_rank: int, world: int, ms: float) -> float:
+    """Whole-job throughput: the ERIs of all ranks (replicas of the same workload) over the
+    slowest rank's time."""
+    return world * eris_per_rank / (ms * 1e-3) / 1e9
+
+
 def class_choices(api, plan):
     """{class: precision name} of the plan's non-empty classes."""
     return {c: api.eri_plan_class_precision(plan, c)[0] for c in range(256)
@@ -279,11 +297,7 @@ def run_ours(args):
         barrier()
         clk = clocks.stop() if clocks is not None else None
         api.eri_sync(plan, stream)
-        t = e0.elapsed_time(e1) / n_steps
-        if dist is not None:
-            tt = torch.tensor([t], device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            t = float(tt.item())
+        t = max_over_ranks(e0.elapsed_time(e1) / n_steps, dist, dev)
         return t, clk
 
     # ---- per-class precision for 16-bit output (plan setup, outside the timed region) ----
@@ -294,7 +308,7 @@ def run_ours(args):
 
     # ---- headline: all 256 classes per step, FP32 recurrences where calibrated ----
     ms, clk = timed_steps(args.warmup, args.steps, ClockSampler(local))
-    value = world * total_eris / (ms * 1e-3) / 1e9
+    value = job_geris(total_eris, world, ms)
     # every class in FP32 (no calibration), for context
     apply_choices(api, plan, None)
     ms_all32, _ = timed_steps(1, args.steps)
@@ -335,6 +349,16 @@ def run_ours(args):
             "peak_kind": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz); FP64 work weighted "
                          "by the FP32/FP64 peak ratio (1.25 TFLOP/s FP64)",
             "share": ms_cal[dom] / sum(ms_cal.values())}
+    # DRAM traffic of the dominant kernel: bytes per quartet from the committed ncu capture of
+    # the same kernel (a smaller case of the class), scaled to this launch's quartets
+    try:
+        with open(os.path.join(ROOT, "profiles", "dram_bytes_per_quartet.json")) as f:
+            tr = json.load(f)
+        if tr["class"] == dom and tr["precision"] == dprec:
+            roof["traffic"] = tr["dram_bytes_per_quartet"] * counts[dom]
+            roof["traffic_source"] = tr["source"] + f", scaled to {counts[dom]} quartets"
+    except (OSError, KeyError, ValueError):
+        pass
     frac_all = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], choice16[c], BITS, peaks["hbm_gbs"])
                 / (ms_cal[c] * 1e-3) for c in ms_cal}
 

@@ -240,10 +240,12 @@ __device__ __forceinline__ void phase_geometry_pairs(const ShellsDev &sh,
     int ic = t % nc;
     t /= nc;
     int ib = t % nb, ia = t / nb;
-    const long long pa = sh.pofs[qt.x] + ia, pb = sh.pofs[qt.y] + ib, pc = sh.pofs[qt.z] + ic,
-                    pd = sh.pofs[qt.w] + id;
-    const double *rab = pairs + (pa * np + pb) * kPairFields;
-    const double *rcd = pairs + (pc * np + pd) * kPairFields;
+    // 32-bit index arithmetic (64-bit integer operations issue on the FP64 pipe): the table
+    // holds at most 16 GiB / 48 B < 2^32 / kPairFields records
+    const unsigned int pa = sh.pofs[qt.x] + ia, pb = sh.pofs[qt.y] + ib, pc = sh.pofs[qt.z] + ic,
+                       pd = sh.pofs[qt.w] + id, npu = (unsigned int)np;
+    const double *rab = pairs + (pa * npu + pb) * (unsigned int)kPairFields;
+    const double *rcd = pairs + (pc * npu + pd) * (unsigned int)kPairFields;
     const double p = __ldg(rab + PR_P), ip = __ldg(rab + PR_IP);
     const double q = __ldg(rcd + PR_P), iq = __ldg(rcd + PR_IP);
     bool swab = false, swcd = false;
@@ -793,15 +795,15 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
     for (int prim = 0; prim < maxprim_s; ++prim) {
         if constexpr (PRESET) {
             // setup values of the tile, field-major in the setup buffer (coalesced loads)
-            const R *su = reinterpret_cast<const R *>(args.setup);
-            const long long ss = args.setup_stride;
+            const R *su = reinterpret_cast<const R *>(args.setup) + q0;
+            const int ss = (int)args.setup_stride;  // <= 2^20: 32-bit offsets
             for (int it = tid; it < C::Q * C::SETUP_GEO; it += C::THREADS) {
                 int f = it / C::Q, q = it % C::Q;
-                rg_s[q * RG_N + f] = q < qn ? su[f * ss + q0 + q] : (R)0;
+                rg_s[q * RG_N + f] = q < qn ? su[f * ss + q] : (R)0;
             }
             for (int it = tid; it < C::Q * C::NRYS * C::SN; it += C::THREADS) {
                 int f = it / C::Q, q = it % C::Q;
-                bc_s[q * C::NRYS * C::SN + f] = q < qn ? su[(C::SETUP_GEO + f) * ss + q0 + q] : (R)0;
+                bc_s[q * C::NRYS * C::SN + f] = q < qn ? su[(C::SETUP_GEO + f) * ss + q] : (R)0;
             }
             __syncthreads();
         } else {
@@ -962,7 +964,10 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
         if (da == 0 && dc == 0 && dch == 0) args.scales[q0 + dq] = eps;
         const uint32_t mask = (1u << bits) - 1u;
         const R Mr = (R)((1u << (bits - 1)) - 1u);
-        const long long qbase = (q0 + dq) * (long long)C::NERI + da * st0 + dc * st2;
+        // bit offsets relative to the tile's first stage word, in 32-bit arithmetic (the tile
+        // holds at most Q * n_ERIQ * bits < 2^31 bits)
+        const int head = (int)(bit0 & 31);
+        const int qbase = dq * C::NERI + da * st0 + dc * st2;
 #pragma unroll
         for (int bb = 0; bb < C::BCH; ++bb) {
             int b = dch * C::BCH + bb;
@@ -972,8 +977,8 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                     R v = RTraits<R>::round_away(acc[bb][d] * inv);
                     v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
                     uint32_t code = to_code<R>(v, bits) & mask;
-                    long long s = (qbase + b * st1 + d * st3) * bits - (w0 << 5);
-                    int wi = (int)(s >> 5), off = (int)(s & 31);
+                    const int s = head + (qbase + b * st1 + d * st3) * bits;
+                    int wi = s >> 5, off = s & 31;
                     atomicOr(stage + wi, code << off);
                     if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
                 }
@@ -1020,6 +1025,7 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
     using R = typename C::R;
     const long long q = (long long)blockIdx.x * 128 + threadIdx.x;
     if (q >= args.nq) return;
+    const int st = (int)stride;  // <= 2^20: field offsets in 32-bit arithmetic
     int4 g = args.quartets[q];
     int4 qt = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
                         pick(g, args.perm[3]));
@@ -1027,20 +1033,20 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
     int np = 0;
     geometry_of<C>(sh, args, qt, 0, geo, np);
     R *o = out + q;
-    o[0 * stride] = to_r<R>(geo[G_ABX]);
-    o[1 * stride] = to_r<R>(geo[G_ABY]);
-    o[2 * stride] = to_r<R>(geo[G_ABZ]);
-    o[3 * stride] = to_r<R>(geo[G_CDX]);
-    o[4 * stride] = to_r<R>(geo[G_CDY]);
-    o[5 * stride] = to_r<R>(geo[G_CDZ]);
-    o[6 * stride] = to_r<R>(geo[G_SWAB]);
-    o[7 * stride] = to_r<R>(geo[G_SWCD]);
+    o[0 * st] = to_r<R>(geo[G_ABX]);
+    o[1 * st] = to_r<R>(geo[G_ABY]);
+    o[2 * st] = to_r<R>(geo[G_ABZ]);
+    o[3 * st] = to_r<R>(geo[G_CDX]);
+    o[4 * st] = to_r<R>(geo[G_CDY]);
+    o[5 * st] = to_r<R>(geo[G_CDZ]);
+    o[6 * st] = to_r<R>(geo[G_SWAB]);
+    o[7 * st] = to_r<R>(geo[G_SWCD]);
 #pragma unroll 1
     for (int mu = 0; mu < C::NRYS; ++mu) {
         R bc[C::SN];
         phase_setup<C>(tb, geo, mu, bc);
 #pragma unroll
-        for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * stride] = bc[f];
+        for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * st] = bc[f];
     }
 }
 
@@ -1176,7 +1182,7 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
         if constexpr (PRESET) {
             // field-major setup records: consecutive threads read consecutive words
             const R *su = reinterpret_cast<const R *>(args.setup) + (q0 + tid);
-            const long long ss = args.setup_stride;
+            const int ss = (int)args.setup_stride;  // <= 2^20: 32-bit offsets
             R rg[RG_N];
 #pragma unroll
             for (int f = 0; f < RG_N; ++f) rg[f] = su[f * ss];
@@ -1267,7 +1273,9 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
         args.scales[q0 + tid] = eps;
         const uint32_t mask = (1u << bits) - 1u;
         const R Mr = (R)((1u << (bits - 1)) - 1u);
-        const long long qbase = (q0 + tid) * (long long)C::NERI;
+        // bit offsets relative to the tile's first stage word, in 32-bit arithmetic
+        const int head = (int)(bit0 & 31);
+        const int tbase = tid * C::NERI;
 #pragma unroll
         for (int a = 0; a < C::NA; ++a)
 #pragma unroll
@@ -1279,8 +1287,8 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                         R v = RTraits<R>::round_away(acc[((a * C::NB + b) * C::NC + c) * C::ND + d] * inv);
                         v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
                         uint32_t code = to_code<R>(v, bits) & mask;
-                        long long sb = (qbase + a * st0 + b * st1 + c * st2 + d * st3) * bits - (w0 << 5);
-                        int wi = (int)(sb >> 5), off = (int)(sb & 31);
+                        const int sb = head + (tbase + a * st0 + b * st1 + c * st2 + d * st3) * bits;
+                        int wi = sb >> 5, off = sb & 31;
                         atomicOr(stage + wi, code << off);
                         if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
                     }

@@ -186,6 +186,19 @@ eri_status_t eri_compute_class(eri_plan_t plan, int32_t cls, double *d_out, void
 eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
                                     void *stream);
 
+/* eri_compute_compressed with the result delivered to host memory: each class's kernels run on
+ * `stream`, and as soon as a class finishes its packed segment and scales are copied to the
+ * same offsets of h_packed / h_scales on a plan-owned copy stream, overlapping the kernels of
+ * the following classes (no counterpart in the paper, whose output crosses PCIe after the run).
+ *   d_packed, d_scales  device buffers of eri_output_bytes(plan, bits) sizes (staging)
+ *   h_packed, h_scales  host buffers of the same sizes; page-locked memory lets the copies
+ *                       overlap the kernels (pageable memory works, serialised)
+ * Asynchronous: `stream` completes after the last copy; synchronise it before reading the host
+ * buffers.  Errors as eri_compute_compressed. */
+eri_status_t eri_compute_compressed_to_host(eri_plan_t plan, int32_t bits, void *d_packed,
+                                            float *d_scales, void *h_packed, float *h_scales,
+                                            void *stream);
+
 /* eri_compute_compressed for one class only (full-size buffers). */
 eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
                                           void *d_packed, float *d_scales, void *stream);

@@ -70,6 +70,7 @@ SIGNATURES = {
     "eri_compute": (_i32, [_p, _p, _p]),
     "eri_compute_class": (_i32, [_p, _i32, _p, _p]),
     "eri_compute_compressed": (_i32, [_p, _i32, _p, _p, _p]),
+    "eri_compute_compressed_to_host": (_i32, [_p, _i32, _p, _p, _p, _p, _p]),
     "eri_compute_compressed_class": (_i32, [_p, _i32, _i32, _p, _p, _p]),
     "eri_sync": (_i32, [_p, _p]),
     "eri_backward": (_i32, [_p, _p, _p, _p, _p]),

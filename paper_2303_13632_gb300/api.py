@@ -171,6 +171,15 @@ def eri_compute_class(plan: Plan, cls: int, out, stream=None) -> None:
           "eri_compute_class")
 
 
+def eri_compute_compressed_to_host(plan: Plan, bits: int, d_packed, d_scales, h_packed, h_scales,
+                                   stream=None) -> None:
+    """Compressed ERIs streamed class by class to host tensors (pinned for overlap)."""
+    check(_lib.load().eri_compute_compressed_to_host(
+        plan.handle, bits, _dev_ptr(d_packed), _dev_ptr(d_scales),
+        ctypes.c_void_p(h_packed.data_ptr()), ctypes.c_void_p(h_scales.data_ptr()),
+        _stream_handle(stream)), "eri_compute_compressed_to_host")
+
+
 def eri_compute_compressed(plan: Plan, bits: int, packed, scales, stream=None) -> None:
     check(_lib.load().eri_compute_compressed(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales),
                                              _stream_handle(stream)), "eri_compute_compressed")

@@ -194,6 +194,10 @@ struct eri_plan_s {
     static constexpr int kSide = 4;
     cudaStream_t side[kSide] = {};
     cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
+    // streamed copies to the host: copy stream and one event per class
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t class_ev[256] = {};
+    cudaEvent_t copy_done = nullptr;
     cudaGraphExec_t graph = nullptr;
     int g_bits = -1, g_prec = -1;
     void *g_packed = nullptr;
@@ -234,6 +238,10 @@ void free_plan(eri_plan_s *p) {
         if (p->join_ev[i]) cudaEventDestroy(p->join_ev[i]);
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
+    if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+    for (int c = 0; c < 256; ++c)
+        if (p->class_ev[c]) cudaEventDestroy(p->class_ev[c]);
+    if (p->copy_done) cudaEventDestroy(p->copy_done);
     delete p;
 }
 
@@ -741,6 +749,52 @@ eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packe
         off += packed_segment_bytes(plan->count[c], neri, bits);
     }
     return ERI_OK;
+}
+
+eri_status_t eri_compute_compressed_to_host(eri_plan_t plan, int32_t bits, void *d_packed,
+                                            float *d_scales, void *h_packed, float *h_scales,
+                                            void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales || !h_packed || !h_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
+        return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaSuccess;
+    if (!plan->copy_stream) e = cudaStreamCreateWithFlags(&plan->copy_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !plan->copy_done)
+        e = cudaEventCreateWithFlags(&plan->copy_done, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_status(e);
+    size_t off = 0;
+    for (int c = 0; c < 256; ++c) {
+        int neri = 0;
+        eri_class_shape(c, &neri, nullptr);
+        const size_t seg = packed_segment_bytes(plan->count[c], neri, bits);
+        if (plan->count[c] > 0) {
+            eri_status_t st = launch_one(plan, c, nullptr, bits, d_packed, d_scales, off, s);
+            if (st != ERI_OK) return st;
+            if (!plan->class_ev[c] &&
+                (e = cudaEventCreateWithFlags(&plan->class_ev[c], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_status(e);
+            // the class's codes and scales leave while the next classes compute
+            e = cudaEventRecord(plan->class_ev[c], s);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_stream, plan->class_ev[c], 0);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(static_cast<char *>(h_packed) + off,
+                                    static_cast<const char *>(d_packed) + off, seg,
+                                    cudaMemcpyDeviceToHost, plan->copy_stream);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(h_scales + plan->first[c], d_scales + plan->first[c],
+                                    sizeof(float) * (size_t)plan->count[c], cudaMemcpyDeviceToHost,
+                                    plan->copy_stream);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        off += seg;
+    }
+    // the caller's stream completes only after the last copy
+    e = cudaEventRecord(plan->copy_done, plan->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, plan->copy_done, 0);
+    return cuda_status(e);
 }
 
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,

@@ -171,6 +171,29 @@ def test_compressed_16bit_all_classes(workload, oracle_values):
             assert np.all(np.abs(xt - ref) <= float(eps[i]) * (0.5 + 1e-6) + 1e-12)
 
 
+def test_compressed_to_host_equals_device_output(workload):
+    """eri_compute_compressed_to_host delivers the same bytes as eri_compute_compressed followed
+    by copies, for a byte width and an odd width (word-split class segments)."""
+    pool, q = workload
+    plan = api.eri_plan_create(pool, q, precision="mixed")
+    s = torch.cuda.current_stream()
+    for bits in (16, 13):
+        nb, sb = api.eri_output_bytes(plan, bits)
+        packed = torch.full((nb // 4,), -1, dtype=torch.int32, device="cuda")
+        scales = torch.full((sb // 4,), -1.0, dtype=torch.float32, device="cuda")
+        api.eri_compute_compressed(plan, bits, packed, scales, s)
+        api.eri_sync(plan, s)
+        ref_p, ref_s = packed.cpu().numpy(), scales.cpu().numpy()
+        packed.fill_(-1)
+        scales.fill_(-1.0)
+        hp = torch.full((nb // 4,), 7, dtype=torch.int32, pin_memory=True)
+        hs = torch.full((sb // 4,), 7.0, dtype=torch.float32, pin_memory=True)
+        api.eri_compute_compressed_to_host(plan, bits, packed, scales, hp, hs, s)
+        api.eri_sync(plan, s)
+        np.testing.assert_array_equal(hp.numpy(), ref_p)
+        np.testing.assert_array_equal(hs.numpy(), ref_s)
+
+
 @pytest.mark.parametrize("bits", [2, 8, 12, 20, 24])
 def test_compressed_other_widths(bits):
     """Packed n-bit streams for odd widths, tile edges that split 32-bit words, and the

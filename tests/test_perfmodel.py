@@ -1,0 +1,53 @@
+"""The algorithmic work per quartet (the numerator of every roofline figure) against the
+paper's own counts, and the canonical-class mapping it uses."""
+import itertools
+
+import pytest
+
+from oracle.classes import n_eriq
+from paper_2303_13632_gb300 import perfmodel as P
+
+
+def _paper_count(cls):
+    """n_FLOPQ as the paper counts it (Sec. III-A): the Rys roots are prepared on the host there,
+    so the on-device root term 60 n_Rys of the model is left out."""
+    f64, rr = P.flops_per_quartet(cls)
+    La, Lb, Lc, Ld = P.canonical(cls)
+    n = (La + Lb + Lc + Ld) // 2 + 1
+    return f64 - 60 * n + rr
+
+
+def test_matches_the_papers_operation_counts():
+    # Sec. III-A: total n_FLOPQ grows from 80 for [ss|ss] to 2.5e5 for [ff|ff]
+    assert _paper_count((0, 0, 0, 0)) == pytest.approx(80, rel=0.2)
+    assert _paper_count((3, 3, 3, 3)) == pytest.approx(2.5e5, rel=0.05)
+
+
+def test_quadrature_dominates_large_classes_and_setup_small_ones():
+    # Sec. III-A: setup dominates a few small classes, quadrature the large ones
+    f64, rr = P.flops_per_quartet((0, 0, 0, 0))
+    assert f64 > rr
+    La, Lb, Lc, Ld = 3, 3, 3, 3
+    quad = 3 * 7 * n_eriq(La, Lb, Lc, Ld)
+    assert quad > 0.8 * P.flops_per_quartet((La, Lb, Lc, Ld))[1]
+
+
+def test_canonical_classes():
+    canon = {P.canonical(c) for c in itertools.product(range(4), repeat=4)}
+    assert len(canon) == 55
+    for c in itertools.product(range(4), repeat=4):
+        k = P.canonical(c)
+        assert n_eriq(*k) == n_eriq(*c)
+        assert sorted(k[:2]) in (sorted(c[:2]), sorted(c[2:]))
+        assert k[0] >= k[1] and k[2] >= k[3]
+        assert P.ncart(k[0]) * P.ncart(k[1]) >= P.ncart(k[2]) * P.ncart(k[3])
+
+
+def test_roofline_time_is_the_larger_bound():
+    cls, n = (1, 1, 1, 1), 1000
+    t = P.roofline_seconds(cls, n, "mixed", 16, 7000.0)
+    f64, rr = P.flops_per_quartet(cls)
+    t_alu = n * (f64 / (P.PEAK_FP64_TFLOPS * 1e12) + rr / (P.PEAK_FP32_TFLOPS * 1e12))
+    t_mem = n * P.bytes_per_quartet(cls, 16) / 7000e9
+    assert t == pytest.approx(max(t_alu, t_mem))
+    assert P.roofline_seconds(cls, n, "fp64", 16, 7000.0) > t

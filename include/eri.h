@@ -59,8 +59,11 @@ typedef enum {
  * and FP64 for the Rys roots, footnote of Sec. II-C). */
 enum {
     ERI_FP64 = 0,  /* everything in FP64 */
-    ERI_MIXED = 1  /* FP64: Boys function, Rys roots and weights, Gaussian-product prefactors;
-                      FP32: setup B/C, VRR, HRR, quadrature; primitive sums Kahan-compensated */
+    ERI_MIXED = 1  /* FP64: Boys function, Rys roots and weights, Gaussian-product prefactors,
+                      B and C (rounded once to FP32); FP32: the 2-D integral recurrences (Eqs.
+                      6-7, or for classes with angular momentum on b or d the equivalent
+                      four-index recursion, which does not amplify FP32 rounding) and the
+                      quadrature (Eq. 8); primitive sums Kahan-compensated */
 };
 
 /* How eri_plan_create obtains the quartet list. */
@@ -88,7 +91,7 @@ typedef struct {
     int32_t precision;    /* ERI_FP64 or ERI_MIXED */
     int32_t quartet_mode; /* ERI_EXPLICIT or ERI_ALL */
     int32_t device;       /* CUDA device ordinal the plan lives on */
-    int32_t flags;        /* ERI_QUARTETS_ON_DEVICE */
+    int32_t flags;        /* ERI_QUARTETS_ON_DEVICE | ERI_NO_PAIR_TABLE */
 } eri_plan_opts_t;
 
 /* Builds a plan: validates and normalises the shells, classifies and sorts the quartets by
@@ -168,7 +171,7 @@ eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
 
 /* FP64 ERIs of every quartet (Eqs. 5-8 per primitive quartet, summed over primitives) into
  * d_out (eri_output_bytes(plan, 0, ...) bytes, class-sorted, see fp64_offset).
- * Asynchronous on `stream`; one kernel launch per non-empty class. */
+ * Asynchronous on `stream`; the launches per class are given by eri_plan_class_launches. */
 eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream);
 
 /* Same as eri_compute for one class only (cls as in eri_plan_class_info); d_out is the

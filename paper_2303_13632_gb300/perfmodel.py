@@ -76,3 +76,93 @@ def fp32_equivalent_flops(cls, precision: str) -> float:
     f64, rr = flops_per_quartet(cls)
     w = PEAK_FP32_TFLOPS / PEAK_FP64_TFLOPS
     return f64 * w + (rr * w if precision == "fp64" else rr)
+
+
+# ---------------------------------------------------------------------------------------------
+# GPU analogue of the paper's throughput model (Eq. 12: f_max n_ERIQ / (max(n_RR, n_GQ, n_CS) +
+# 10), the slowest pipelined stage plus a fixed per-quartet overhead).  On the GPU the stages
+# are the FP64 setup, the FP32 recurrences/quadrature and the output bytes, each at an effective
+# rate, plus a per-quartet overhead that depends on the kernel form the class runs in:
+#     t_q = max(F64 / R64, F32 / R32, B / BW) + o_form
+# The rates and overheads are fitted to measured per-class times.
+
+def kernel_form(cls) -> str:
+    """The kernel form a primitive FP32 class runs in (inline-setup thread-per-quartet, split
+    setup + FP32 thread-per-quartet, split setup + shared-memory phase kernel)."""
+    La, Lb, Lc, Ld = canonical(cls)
+    neri = ncart(La) * ncart(Lb) * ncart(Lc) * ncart(Ld)
+    iblk = (La + 1) * (Lb + 1) * (Lc + 1) * (Ld + 1)
+    if neri <= 36 and iblk <= 16:
+        return "tpq_inline"
+    if neri <= 100 and iblk <= 16:
+        return "tpq_split"
+    return "phase_split"
+
+
+FORMS = ("tpq_inline", "tpq_split", "phase_split")
+
+
+def model_seconds_per_quartet(cls, params, bits: int = 16) -> float:
+    f64, rr = flops_per_quartet(cls)
+    t = max(f64 / params["R64"], rr / params["R32"], bytes_per_quartet(cls, bits) / params["BW"])
+    return t + params["o_" + kernel_form(cls)]
+
+
+def fit_gpu_model(measured, bits: int = 16):
+    """Fits R64, R32 (FLOP/s), BW (B/s) and one overhead per kernel form (s) to measured
+    {class tuple: seconds per quartet}, minimising the squared log error."""
+    import numpy as np
+    from scipy.optimize import minimize
+
+    classes = list(measured)
+    t_meas = np.array([measured[c] for c in classes])
+
+    def unpack(x):
+        p = {"R64": np.exp(x[0]), "R32": np.exp(x[1]), "BW": np.exp(x[2])}
+        for i, f in enumerate(FORMS):
+            p["o_" + f] = np.exp(x[3 + i])
+        return p
+
+    def loss(x):
+        p = unpack(x)
+        t = np.array([model_seconds_per_quartet(c, p, bits) for c in classes])
+        return float(np.sum(np.log(t / t_meas) ** 2))
+
+    x0 = np.log([PEAK_FP64_TFLOPS * 1e12, PEAK_FP32_TFLOPS * 1e12, 5e12, 1e-12, 1e-12, 1e-12])
+    res = minimize(loss, x0, method="Nelder-Mead", options={"maxiter": 20000, "maxfev": 20000,
+                                                             "xatol": 1e-6, "fatol": 1e-9})
+    p = unpack(res.x)
+    t_fit = np.array([model_seconds_per_quartet(c, p, bits) for c in classes])
+    err = np.log(t_fit / t_meas)
+    return p, {"median_abs_log_err": float(np.median(np.abs(err))),
+               "max_abs_log_err": float(np.max(np.abs(err))),
+               "r2_log": float(1 - np.sum(err ** 2) / np.sum((np.log(t_meas) - np.mean(np.log(t_meas))) ** 2))}
+
+
+def read_class_table(path):
+    """{class tuple: (quartets, GERIS mixed)} from the committed per-class sweep table."""
+    letters = {"s": 0, "p": 1, "d": 2, "f": 3}
+    out = {}
+    with open(path) as f:
+        for line in f:
+            if not line.startswith("| ["):
+                continue
+            name, rest = line[3:].split("] |", 1)  # "[ab\\|cd] | n | geris | ..."
+            cells = [c.strip() for c in rest.strip().strip("|").split("|")]
+            cls = tuple(letters[ch] for ch in name if ch in letters)
+            out[cls] = (int(cells[0]), float(cells[1]))
+    return out
+
+
+if __name__ == "__main__":
+    import sys
+
+    table = read_class_table(sys.argv[1])
+    measured = {c: ncart(c[0]) * ncart(c[1]) * ncart(c[2]) * ncart(c[3]) / (g * 1e9)
+                for c, (n, g) in table.items()}
+    p, q = fit_gpu_model(measured)
+    print(f"R64 = {p['R64'] / 1e12:.3f} TFLOP/s, R32 = {p['R32'] / 1e12:.2f} TFLOP/s, "
+          f"BW = {p['BW'] / 1e9:.0f} GB/s; per-quartet overheads: "
+          + ", ".join(f"{f} {p['o_' + f] * 1e12:.1f} ps" for f in FORMS))
+    print(f"median |log(t_model / t_measured)| = {q['median_abs_log_err']:.3f}, "
+          f"max = {q['max_abs_log_err']:.3f}, R^2 (log t) = {q['r2_log']:.3f}")

@@ -51,3 +51,18 @@ def test_roofline_time_is_the_larger_bound():
     t_mem = n * P.bytes_per_quartet(cls, 16) / 7000e9
     assert t == pytest.approx(max(t_alu, t_mem))
     assert P.roofline_seconds(cls, n, "fp64", 16, 7000.0) > t
+
+
+def test_gpu_model_fits_the_committed_class_table():
+    import os
+
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "profiles",
+                        "sweep256_per_class.md")
+    table = P.read_class_table(path)
+    assert len(table) == 256
+    measured = {c: n_eriq(*c) / (g * 1e9) for c, (n, g) in table.items()}
+    p, q = P.fit_gpu_model(measured)
+    assert q["r2_log"] > 0.95
+    assert q["median_abs_log_err"] < 0.2
+    # the fitted rates stay below the nominal peaks
+    assert p["R64"] < P.PEAK_FP64_TFLOPS * 1e12 and p["R32"] < P.PEAK_FP32_TFLOPS * 1e12

@@ -70,6 +70,10 @@ def _load():
         lib.orc_pack_bits.argtypes = [p, i64, ctypes.c_int, p]
         lib.orc_unpack_bits.restype = None
         lib.orc_unpack_bits.argtypes = [p, i64, ctypes.c_int, p]
+        lib.orc_pack_paper512.restype = None
+        lib.orc_pack_paper512.argtypes = [p, i64, i64, ctypes.c_int, p]
+        lib.orc_unpack_paper512.restype = None
+        lib.orc_unpack_paper512.argtypes = [p, i64, i64, ctypes.c_int, p]
         lib.orc_max_threads.restype = ctypes.c_int
         lib.orc_max_threads.argtypes = []
         lib.orc_ncart.restype = ctypes.c_int
@@ -215,6 +219,29 @@ def unpack_bits(words: np.ndarray, count: int, bits: int) -> np.ndarray:
     words = np.ascontiguousarray(words, dtype=np.uint32)
     q = np.zeros(count, dtype=np.int32)
     _load().orc_unpack_bits(_ptr(words), int(count), int(bits), _ptr(q))
+    return q
+
+
+def paper512_chunks(n_eri: int, bits: int) -> int:
+    """n_CS = ceil(n_ERIQ / floor(512/n)) 512-bit chunks per quartet (Sec. III-C)."""
+    f = 512 // bits
+    return (n_eri + f - 1) // f
+
+
+def pack_paper512(q: np.ndarray, n_quartets: int, n_eri: int, bits: int) -> np.ndarray:
+    """The paper's per-quartet 512-bit output chunks (Sec. III-C), as uint32 words."""
+    q = np.ascontiguousarray(q, dtype=np.int32)
+    assert len(q) == n_quartets * n_eri
+    words = np.zeros(n_quartets * paper512_chunks(n_eri, bits) * 16, dtype=np.uint32)
+    _load().orc_pack_paper512(_ptr(q), int(n_quartets), int(n_eri), int(bits), _ptr(words))
+    return words
+
+
+def unpack_paper512(words: np.ndarray, n_quartets: int, n_eri: int, bits: int) -> np.ndarray:
+    words = np.ascontiguousarray(words, dtype=np.uint32)
+    assert len(words) >= n_quartets * paper512_chunks(n_eri, bits) * 16
+    q = np.zeros(n_quartets * n_eri, dtype=np.int32)
+    _load().orc_unpack_paper512(_ptr(words), int(n_quartets), int(n_eri), int(bits), _ptr(q))
     return q
 
 

@@ -838,6 +838,62 @@ void orc_unpack_bits(const uint32_t *words, int64_t count, int bits, int32_t *q)
     }
 }
 
+/* The paper's output chunks (Sec. III-C, compress-store loops): the ERIs of each quartet are
+ * written as 512-bit words, each holding F = floor(512/bits) n-bit fields; ERIs that do not fit
+ * into the current chunk are carried over and written first into the next one, and the last
+ * chunk of a quartet is padded, so a quartet takes n_CS = ceil(n_eri / F) chunks and no chunk
+ * holds ERIs of two quartets.  Field j of a chunk occupies chunk bits [j*bits, j*bits + bits),
+ * chunk bit s being bit (s % 32) of 32-bit word s / 32 of the chunk (the paper does not fix the
+ * bit order inside a chunk; this one matches the dense stream).  Unused bits are zero.
+ * q holds n_quartets * n_eri codes, quartet after quartet; words must hold
+ * n_quartets * n_CS * 16 entries and is overwritten. */
+void orc_pack_paper512(const int32_t *q, int64_t n_quartets, int64_t n_eri, int bits,
+                       uint32_t *words)
+{
+    int64_t F = 512 / bits;
+    int64_t n_cs = (n_eri + F - 1) / F;
+    memset(words, 0, (size_t)(n_quartets * n_cs * 16) * sizeof(uint32_t));
+    uint64_t mask = (bits == 32) ? 0xffffffffull : ((1ull << bits) - 1ull);
+    for (int64_t i = 0; i < n_quartets; ++i) {
+        int64_t chunk = 0, field = 0; /* position of the next field within the quartet */
+        for (int64_t e = 0; e < n_eri; ++e) {
+            if (field == F) { /* chunk full: the remaining ERIs go to the next chunk */
+                ++chunk;
+                field = 0;
+            }
+            uint32_t *z = words + (i * n_cs + chunk) * 16;
+            uint64_t code = (uint64_t)(uint32_t)q[i * n_eri + e] & mask;
+            for (int b = 0; b < bits; ++b) {
+                int64_t s = field * bits + b;
+                if ((code >> b) & 1ull)
+                    z[s / 32] |= (uint32_t)1u << (s % 32);
+            }
+            ++field;
+        }
+    }
+}
+
+void orc_unpack_paper512(const uint32_t *words, int64_t n_quartets, int64_t n_eri, int bits,
+                         int32_t *q)
+{
+    int64_t F = 512 / bits;
+    int64_t n_cs = (n_eri + F - 1) / F;
+    for (int64_t i = 0; i < n_quartets; ++i)
+        for (int64_t e = 0; e < n_eri; ++e) {
+            const uint32_t *z = words + (i * n_cs + e / F) * 16;
+            int64_t field = e % F;
+            uint32_t code = 0;
+            for (int b = 0; b < bits; ++b) {
+                int64_t s = field * bits + b;
+                if ((z[s / 32] >> (s % 32)) & 1u)
+                    code |= (uint32_t)1u << b;
+            }
+            if (bits < 32 && (code >> (bits - 1)) & 1u)
+                code |= ~((1u << bits) - 1u);
+            q[i * n_eri + e] = (int32_t)code;
+        }
+}
+
 int orc_max_threads(void)
 {
 #ifdef _OPENMP

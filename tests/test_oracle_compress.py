@@ -108,3 +108,83 @@ def test_paper_accuracy_magnitudes_on_lattice_sample():
                 assert err <= 1e-6 * np.max(np.abs(vals))
             else:
                 assert lo <= err <= hi, (cls, bits, err)
+
+
+# --- the paper's 512-bit output chunks (Sec. III-C, compress-store loops) -------------------
+
+def test_paper512_hand_built_12bit():
+    """12-bit fields, worked by hand: F = floor(512/12) = 42 fields (504 bits) per chunk.
+    Codes 1, -1, 2047, -2047 fill bits 0-47: word 0 = 0x001 | 0xFFF << 12 | 0xFF << 24, word 1
+    = 0x7 | 0x801 << 4.  Field 42 opens the second chunk at bit 0; bits 504-511 of the first
+    chunk stay zero."""
+    q = np.zeros(43, dtype=np.int32)
+    q[:4] = [1, -1, 2047, -2047]
+    q[41] = -1   # last field of chunk 0: bits 492-503 -> word 15 bits 12-23
+    q[42] = 5
+    w = oracle.pack_paper512(q, 1, 43, 12)
+    assert len(w) == 32  # n_CS = 2 chunks of 16 words
+    assert w[0] == 0xFFFFF001
+    assert w[1] == 0x00008017
+    assert w[15] == 0x00FFF000  # bits 24-31 of the last word (chunk bits 504-511) are padding
+    assert w[16] == 5 and not np.any(w[17:])
+    assert not np.any(w[2:15])
+
+
+@pytest.mark.parametrize("bits", [8, 16, 32])
+def test_paper512_byte_widths_are_padded_arrays(bits):
+    """For 8-, 16- and 32-bit codes a chunk is a plain little-endian array of 64, 32 or 16
+    integers, the last chunk of each quartet zero-padded."""
+    rng = np.random.default_rng(bits)
+    M = 2 ** (bits - 1) - 1
+    dt = {8: np.int8, 16: np.int16, 32: np.int32}[bits]
+    per = 512 // bits
+    for n_eri in (1, per - 1, per, per + 1, 1000):
+        nq = 3
+        q = rng.integers(-M, M + 1, size=nq * n_eri).astype(np.int32)
+        w = oracle.pack_paper512(q, nq, n_eri, bits)
+        ncs = -(-n_eri // per)
+        arr = w.view(dt).reshape(nq, ncs * per)
+        np.testing.assert_array_equal(arr[:, :n_eri], q.reshape(nq, n_eri))
+        assert not np.any(arr[:, n_eri:])
+
+
+def test_paper512_chunk_count_matches_paper_tables():
+    """Chunks per quartet at 16 bit equal the n_CS the paper tabulates (classes.n_cs is pinned
+    to Tables III and V), for all 256 classes."""
+    from oracle import classes as C
+    for c in C.all_classes():
+        n_eri = C.n_eriq(*c)
+        w = oracle.pack_paper512(np.zeros(2 * n_eri, dtype=np.int32), 2, n_eri, 16)
+        assert len(w) == 2 * 16 * C.n_cs(*c, bits=16)
+        assert oracle.paper512_chunks(n_eri, 16) == C.n_cs(*c, bits=16)
+
+
+@pytest.mark.parametrize("bits", [2, 4, 8, 16])
+def test_paper512_equals_dense_stream_when_chunks_are_full(bits):
+    """When n divides 512 and n_eri is a multiple of 512/n no chunk is padded, so the chunked
+    layout is the dense LSB-first stream of the same codes."""
+    rng = np.random.default_rng(100 + bits)
+    M = 2 ** (bits - 1) - 1
+    n_eri = 3 * (512 // bits)
+    q = rng.integers(-M, M + 1, size=5 * n_eri).astype(np.int32)
+    np.testing.assert_array_equal(oracle.pack_paper512(q, 5, n_eri, bits),
+                                  oracle.pack_bits(q, bits))
+
+
+@pytest.mark.parametrize("bits", [2, 3, 5, 7, 12, 13, 20, 23, 24])
+def test_paper512_round_trip_and_padding(bits):
+    """unpack(pack(q)) = q, and every bit past a chunk's last field is zero."""
+    rng = np.random.default_rng(200 + bits)
+    M = 2 ** (bits - 1) - 1
+    per = 512 // bits
+    for n_eri in (1, 10, per, per + 1, 2 * per + 3, 1000):
+        nq = 4
+        q = rng.integers(-M, M + 1, size=nq * n_eri).astype(np.int32)
+        w = oracle.pack_paper512(q, nq, n_eri, bits)
+        np.testing.assert_array_equal(oracle.unpack_paper512(w, nq, n_eri, bits), q)
+        ncs = -(-n_eri // per)
+        chunks = w.reshape(nq * ncs, 16)
+        for ch in range(nq * ncs):
+            used = min(per, n_eri - (ch % ncs) * per) * bits
+            bitsarr = np.unpackbits(chunks[ch].view(np.uint8), bitorder="little")
+            assert not np.any(bitsarr[used:]), (bits, n_eri, ch)

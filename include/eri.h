@@ -169,6 +169,35 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
 eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                      size_t *byte_offset, size_t *bytes);
 
+/* The paper's output layout (Sec. III-C, compress-store loops): each quartet's codes as 512-bit
+ * chunks of F = floor(512/bits) n-bit fields, in the quartet's ERI order; the fields that do not
+ * fit in a chunk open the next one, and the last chunk of a quartet is zero-padded, so a quartet
+ * takes n_CS = ceil(n_eri / F) chunks of 64 bytes and no chunk holds two quartets.  Field j of a
+ * chunk occupies chunk bits [j*bits, j*bits + bits), chunk bit s being bit s%32 of the chunk's
+ * 32-bit word s/32 (little-endian, least significant bit first, as the dense stream; the paper
+ * does not fix the bit order).  Quartets are class-sorted as everywhere else; class segments
+ * follow each other without gaps (each is a whole number of chunks).
+ * Byte range of class `cls` in that layout; cls = 256 gives the total size in *byte_offset.
+ * bits 2..24; ERI_E_INVALID otherwise.  Host only. */
+eri_status_t eri_paper512_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
+                                       size_t *byte_offset, size_t *bytes);
+
+/* Re-lays the packed output of eri_compute_compressed (d_packed, layout of
+ * eri_packed_class_offset, read only) into the chunk layout above (d_chunks, written in full:
+ * eri_paper512_class_offset(plan, bits, 256) bytes).  Integer copy on the GPU, asynchronous on
+ * `stream`; both pointers device memory, 4-byte aligned, not overlapping.  The scales are
+ * unchanged (one eps per quartet, as written by eri_compute_compressed). */
+eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_packed, void *d_chunks,
+                               void *stream);
+
+/* Same as eri_pack_paper512 for one dense stream without a plan: d_stream holds n_quartets *
+ * n_eri n-bit fields, quartet after quartet, as the dense stream above (at least
+ * ceil(n_quartets * n_eri * bits / 32) 32-bit words); d_chunks receives n_quartets * n_CS * 64
+ * bytes.  n_eri 1..10000, bits 2..24, device pointers 4-byte aligned; ERI_E_INVALID
+ * otherwise, ERI_E_CUDA if a launch fails.  n_quartets = 0 does nothing. */
+eri_status_t eri_pack_paper512_stream(const void *d_stream, int64_t n_quartets, int32_t n_eri,
+                                      int32_t bits, void *d_chunks, void *stream);
+
 /* FP64 ERIs of every quartet (Eqs. 5-8 per primitive quartet, summed over primitives) into
  * d_out (eri_output_bytes(plan, 0, ...) bytes, class-sorted, see fp64_offset).
  * Asynchronous on `stream`; the launches per class are given by eri_plan_class_launches. */

@@ -67,6 +67,9 @@ SIGNATURES = {
     "eri_plan_quartet_order": (_i32, [_p, _i64p]),
     "eri_output_bytes": (_i32, [_p, _i32, _szp, _szp]),
     "eri_packed_class_offset": (_i32, [_p, _i32, _i32, _szp, _szp]),
+    "eri_paper512_class_offset": (_i32, [_p, _i32, _i32, _szp, _szp]),
+    "eri_pack_paper512": (_i32, [_p, _i32, _p, _p, _p]),
+    "eri_pack_paper512_stream": (_i32, [_p, _i64, _i32, _i32, _p, _p]),
     "eri_compute": (_i32, [_p, _p, _p]),
     "eri_compute_class": (_i32, [_p, _i32, _p, _p]),
     "eri_compute_compressed": (_i32, [_p, _i32, _p, _p, _p]),

@@ -162,6 +162,25 @@ def eri_packed_class_offset(plan: Plan, bits: int, cls: int):
     return a.value, b.value
 
 
+def eri_paper512_class_offset(plan: Plan, bits: int, cls: int):
+    """(byte offset, bytes) of class `cls` in the paper's 512-bit chunk layout; cls = 256 gives
+    (total bytes, 0)."""
+    a, b = ctypes.c_size_t(), ctypes.c_size_t()
+    check(_lib.load().eri_paper512_class_offset(plan.handle, bits, cls, ctypes.byref(a), ctypes.byref(b)),
+          "eri_paper512_class_offset")
+    return a.value, b.value
+
+
+def eri_pack_paper512(plan: Plan, bits: int, packed, chunks, stream=None) -> None:
+    check(_lib.load().eri_pack_paper512(plan.handle, bits, _dev_ptr(packed), _dev_ptr(chunks),
+                                        _stream_handle(stream)), "eri_pack_paper512")
+
+
+def eri_pack_paper512_stream(dense, n_quartets: int, n_eri: int, bits: int, chunks, stream=None) -> None:
+    check(_lib.load().eri_pack_paper512_stream(_dev_ptr(dense), n_quartets, n_eri, bits, _dev_ptr(chunks),
+                                               _stream_handle(stream)), "eri_pack_paper512_stream")
+
+
 def eri_compute(plan: Plan, out, stream=None) -> None:
     check(_lib.load().eri_compute(plan.handle, _dev_ptr(out), _stream_handle(stream)), "eri_compute")
 

@@ -48,7 +48,8 @@ def _sources_digest() -> str:
 
 def _units():
     units = [("eri_tables", "eri_tables.cu", []), ("eri_plan", "eri_plan.cu", []),
-             ("eri_backward", "eri_backward.cu", []), ("eri_noalloc", "eri_noalloc.cu", [])]
+             ("eri_backward", "eri_backward.cu", []), ("eri_noalloc", "eri_noalloc.cu", []),
+             ("eri_layout", "eri_layout.cu", [])]
     for k in range(NUM_TU):
         units.append((f"eri_classes_{k}", "eri_classes.cu", [f"-DERI_TU={k}"]))
     return units

@@ -264,6 +264,13 @@ size_t packed_segment_bytes(long long nq, int neri, int bits) {
     return (size_t)((b + 255) / 256 * 256);
 }
 
+// Bytes of one class in the paper's chunk layout: n_CS = ceil(n_eri / floor(512/bits)) 64-byte
+// chunks per quartet (Sec. III-C).
+size_t paper512_segment_bytes(long long nq, int neri, int bits) {
+    const long long F = 512 / bits;
+    return (size_t)nq * (size_t)((neri + F - 1) / F) * 64;
+}
+
 int class_neri(int cls) {
     return ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) * ncart_h(cls & 3);
 }
@@ -700,6 +707,38 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
     }
     if (packed_bytes) *packed_bytes = total;
     if (scales_bytes) *scales_bytes = bits == 0 ? 0 : (size_t)plan->nq * sizeof(float);
+    return ERI_OK;
+}
+
+eri_status_t eri_paper512_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
+                                       size_t *byte_offset, size_t *bytes) {
+    if (!plan || cls < 0 || cls > 256 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    size_t off = 0;
+    for (int c = 0; c < cls; ++c) off += paper512_segment_bytes(plan->count[c], class_neri(c), bits);
+    if (byte_offset) *byte_offset = off;
+    if (bytes) *bytes = cls == 256 ? 0 : paper512_segment_bytes(plan->count[cls], class_neri(cls), bits);
+    return ERI_OK;
+}
+
+eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_packed, void *d_chunks,
+                               void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_chunks)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_chunks) % 4)
+        return ERI_E_INVALID;
+    cudaSetDevice(plan->device);
+    size_t in = 0, out = 0;
+    for (int c = 0; c < 256; ++c) {
+        const int neri = class_neri(c);
+        if (plan->count[c] > 0) {
+            eri_status_t st = eri_pack_paper512_stream(static_cast<const char *>(d_packed) + in,
+                                                       plan->count[c], neri, bits,
+                                                       static_cast<char *>(d_chunks) + out, stream);
+            if (st != ERI_OK) return st;
+        }
+        in += packed_segment_bytes(plan->count[c], neri, bits);
+        out += paper512_segment_bytes(plan->count[c], neri, bits);
+    }
     return ERI_OK;
 }
 

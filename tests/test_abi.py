@@ -37,3 +37,18 @@ def test_host_only_helpers():
     assert api.eri_status_string(_lib.ERI_E_NUMERIC) == "ERI_E_NUMERIC"
     with pytest.raises(_lib.EriError):
         api.eri_class_shape(256)
+
+
+def test_paper512_stream_validates_before_touching_the_device():
+    """Argument errors of the chunk re-layout come back as ERI_E_INVALID from host checks alone
+    (no device call is made), and zero quartets is a no-op."""
+    lib = _lib.load()
+    ok, bad = _lib.ERI_OK, _lib.ERI_E_INVALID
+    assert lib.eri_pack_paper512_stream(None, 0, 10, 16, None, None) == ok
+    assert lib.eri_pack_paper512_stream(4096, 1, 0, 16, 8192, None) == bad      # n_eri < 1
+    assert lib.eri_pack_paper512_stream(4096, 1, 10001, 16, 8192, None) == bad  # n_eri > 10000
+    assert lib.eri_pack_paper512_stream(4096, 1, 10, 1, 8192, None) == bad      # bits < 2
+    assert lib.eri_pack_paper512_stream(4096, 1, 10, 25, 8192, None) == bad     # bits > 24
+    assert lib.eri_pack_paper512_stream(4098, 1, 10, 16, 8192, None) == bad     # misaligned
+    assert lib.eri_pack_paper512_stream(None, 1, 10, 16, 8192, None) == bad     # null
+    assert lib.eri_pack_paper512_stream(4096, -1, 10, 16, 8192, None) == bad    # negative count

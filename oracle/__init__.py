@@ -70,6 +70,8 @@ def _load():
         lib.orc_pack_bits.argtypes = [p, i64, ctypes.c_int, p]
         lib.orc_unpack_bits.restype = None
         lib.orc_unpack_bits.argtypes = [p, i64, ctypes.c_int, p]
+        lib.orc_rys_roots.restype = ctypes.c_int
+        lib.orc_rys_roots.argtypes = [ctypes.c_int, d, p, p]
         lib.orc_pack_paper512.restype = None
         lib.orc_pack_paper512.argtypes = [p, i64, i64, ctypes.c_int, p]
         lib.orc_unpack_paper512.restype = None
@@ -141,7 +143,8 @@ def eri_batch(shells, quartets: np.ndarray, method: str = "md", nthreads: int = 
     centre differences and, checked against an extended-precision build of this same
     source, keeps about 1e-15 relative accuracy), "os" = Obara-Saika + Head-Gordon-Pople
     (the independent cross-check; its horizontal transfer loses up to two digits for
-    well-separated centres).
+    well-separated centres), "rys" = the paper's Rys route of Sec. II-C written out (a check
+    of the readings of Eqs. 6-8, not a reference).
     """
     lib = _load()
     t = _Table(shells)
@@ -151,7 +154,7 @@ def eri_batch(shells, quartets: np.ndarray, method: str = "md", nthreads: int = 
     np.cumsum(sizes, out=offsets[1:])
     out = np.zeros(int(offsets[-1]))
     rc = lib.orc_eri_batch(*t.args(), _ptr(q), len(q), _ptr(offsets), _ptr(out),
-                           0 if method == "os" else 1, int(nthreads))
+                           {"os": 0, "md": 1, "rys": 2}[method], int(nthreads))
     if rc != 0:
         raise ValueError("oracle rejected a quartet")
     return out, offsets
@@ -220,6 +223,15 @@ def unpack_bits(words: np.ndarray, count: int, bits: int) -> np.ndarray:
     q = np.zeros(count, dtype=np.int32)
     _load().orc_unpack_bits(_ptr(words), int(count), int(bits), _ptr(q))
     return q
+
+
+def rys_roots(n: int, T: float):
+    """Rys roots x = t^2 and weights (ascending roots) with sum w x^k = F_k(T), k < 2n."""
+    x = np.zeros(n)
+    w = np.zeros(n)
+    if _load().orc_rys_roots(int(n), float(T), _ptr(x), _ptr(w)) != 0:
+        raise ValueError("n out of range")
+    return x, w
 
 
 def paper512_chunks(n_eri: int, bits: int) -> int:

@@ -15,12 +15,15 @@
  *     q = ANINT(x / eps) (Eq. 10), x~ = q * eps (Eq. 11);
  *   - nuclear-centre and exponent gradients of E = sum G_abcd (ab|cd).
  *
- * The ERIs are NOT evaluated with the paper's Rys scheme.  Two independent
+ * The reference ERIs are NOT evaluated with the paper's Rys scheme.  Two independent
  * exact-in-principle schemes named in Sec. II-C are used instead:
  *   (1) Obara-Saika vertical recursion to [e0|f0] followed by the Head-Gordon-Pople
  *       horizontal transfer (orc_eri_quartet), and
  *   (2) McMurchie-Davidson Hermite expansion (orc_eri_quartet_md).
  * They share only the Boys function, which is pinned on its own by the tests.
+ * A third route, (3) the paper's own Rys scheme written out step by step (orc_eri_quartet_rys,
+ * with roots and weights from orc_rys_roots), checks the readings of Sec. II-C (the B and C
+ * coefficients of Eq. 6, the single weight factor, n_Rys) against (1) and (2).
  *
  * Cartesian component order within a shell of angular momentum L: a_x runs from
  * L down to 0, then a_y from L-a_x down to 0 (xx, xy, xz, yy, yz, zz for L=2).
@@ -537,6 +540,265 @@ int orc_eri_quartet_md(const orc_shell *sa, const orc_shell *sb, const orc_shell
 }
 
 /* ------------------------------------------------------------------------- */
+/* The paper's Rys route (Sec. II-C), a third cross-check of the readings     */
+/* ------------------------------------------------------------------------- */
+
+/* Gauss-Legendre rule on [-1, 1] with n points: Newton iteration on the Legendre polynomial
+ * P_n from the three-term recurrence, weights 2 / ((1 - x^2) P_n'(x)^2). */
+static void gauss_legendre(int n, double *x, double *w)
+{
+    for (int i = 0; i < (n + 1) / 2; ++i) {
+        double z = cos(ORC_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = 0.0;
+            for (int k = 1; k <= n; ++k) {
+                double p2 = p1;
+                p1 = p0;
+                p0 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p2) / k;
+            }
+            dp = n * (z * p0 - p1) / (z * z - 1.0);
+            double dz = p0 / dp;
+            z -= dz;
+            if (fabs(dz) < 1e-17)
+                break;
+        }
+        x[i] = -z;
+        x[n - 1 - i] = z;
+        w[i] = w[n - 1 - i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+/* Eigenvalues of a symmetric n x n matrix (row major, destroyed) by cyclic Jacobi rotations. */
+static void jacobi_eigenvalues(int n, double *a, double *ev)
+{
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0, diag = 0.0;
+        for (int i = 0; i < n; ++i) {
+            diag += a[i * n + i] * a[i * n + i];
+            for (int j = i + 1; j < n; ++j)
+                off += a[i * n + j] * a[i * n + j];
+        }
+        if (off <= 1e-36 * diag)
+            break;
+        for (int p = 0; p < n; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                double apq = a[p * n + q];
+                if (apq == 0.0)
+                    continue;
+                double theta = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+                double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                double c = 1.0 / sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) { /* columns p, q */
+                    double akp = a[k * n + p], akq = a[k * n + q];
+                    a[k * n + p] = c * akp - sn * akq;
+                    a[k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) { /* rows p, q */
+                    double apk = a[p * n + k], aqk = a[q * n + k];
+                    a[p * n + k] = c * apk - sn * aqk;
+                    a[q * n + k] = sn * apk + c * aqk;
+                }
+            }
+    }
+    for (int i = 0; i < n; ++i)
+        ev[i] = a[i * n + i];
+}
+
+#define RYS_PANELS 8
+#define RYS_GAUSS 32
+#define RYS_NMAX 16
+
+/* Rys roots x_mu = t_mu^2 in (0, 1) and weights w_mu > 0, mu = 1..n, at argument T: the n-point
+ * Gauss rule of the measure on (0, 1) whose moments are the Boys values,
+ * sum_mu w_mu x_mu^k = F_k(T) = int_0^1 t^{2k} exp(-T t^2) dt for k < 2n (Sec. II-C).
+ * Here the measure is discretised by composite Gauss-Legendre in t on [0, b] (b = 1, or
+ * 13 / sqrt(T) when smaller: beyond it exp(-T t^2) < 1e-73), its orthonormal polynomials are
+ * generated by the Stieltjes procedure, the roots are the eigenvalues of their Jacobi matrix
+ * and the weights the Christoffel numbers 1 / sum_k q_k(x_mu)^2.  Returns -1 if n is out of
+ * range. */
+int orc_rys_roots(int n, double T, double *x, double *w)
+{
+    if (n < 1 || n > RYS_NMAX || !(T >= 0.0))
+        return -1;
+    enum { M = RYS_PANELS * RYS_GAUSS };
+    double gx[RYS_GAUSS], gw[RYS_GAUSS], nx[M], nw[M];
+    gauss_legendre(RYS_GAUSS, gx, gw);
+    double b = 1.0;
+    if (T > 169.0)
+        b = 13.0 / sqrt(T);
+    double h = b / RYS_PANELS;
+    for (int pnl = 0; pnl < RYS_PANELS; ++pnl)
+        for (int g = 0; g < RYS_GAUSS; ++g) {
+            double t = h * (pnl + 0.5 * (gx[g] + 1.0));
+            nx[pnl * RYS_GAUSS + g] = t * t;
+            nw[pnl * RYS_GAUSS + g] = 0.5 * h * gw[g] * exp(-T * t * t);
+        }
+    /* Stieltjes procedure with orthonormal polynomials q_k evaluated on the nodes */
+    double q_prev[M], q_cur[M], alpha[RYS_NMAX], beta[RYS_NMAX + 1];
+    double mass = 0.0;
+    for (int j = 0; j < M; ++j)
+        mass += nw[j];
+    for (int j = 0; j < M; ++j) {
+        q_prev[j] = 0.0;
+        q_cur[j] = 1.0 / sqrt(mass);
+    }
+    beta[0] = 0.0;
+    for (int k = 0; k < n; ++k) {
+        double a = 0.0;
+        for (int j = 0; j < M; ++j)
+            a += nw[j] * nx[j] * q_cur[j] * q_cur[j];
+        alpha[k] = a;
+        double r[M], nrm = 0.0;
+        for (int j = 0; j < M; ++j) {
+            r[j] = (nx[j] - a) * q_cur[j] - beta[k] * q_prev[j];
+            nrm += nw[j] * r[j] * r[j];
+        }
+        beta[k + 1] = sqrt(nrm);
+        for (int j = 0; j < M; ++j) {
+            q_prev[j] = q_cur[j];
+            q_cur[j] = r[j] / beta[k + 1];
+        }
+    }
+    /* Jacobi matrix: alpha on the diagonal, beta[1..n-1] beside it */
+    double J[RYS_NMAX * RYS_NMAX];
+    memset(J, 0, sizeof(J));
+    for (int k = 0; k < n; ++k) {
+        J[k * n + k] = alpha[k];
+        if (k + 1 < n)
+            J[k * n + k + 1] = J[(k + 1) * n + k] = beta[k + 1];
+    }
+    jacobi_eigenvalues(n, J, x);
+    for (int mu = 0; mu < n; ++mu) { /* Christoffel numbers from the same recurrence */
+        double qp = 0.0, qc = 1.0 / sqrt(mass), s = qc * qc;
+        for (int k = 0; k + 1 < n; ++k) {
+            double qn = ((x[mu] - alpha[k]) * qc - beta[k] * qp) / beta[k + 1];
+            qp = qc;
+            qc = qn;
+            s += qc * qc;
+        }
+        w[mu] = 1.0 / s;
+    }
+    /* ascending roots */
+    for (int i = 1; i < n; ++i)
+        for (int j = i; j > 0 && x[j] < x[j - 1]; --j) {
+            double tx = x[j]; x[j] = x[j - 1]; x[j - 1] = tx;
+            double tw = w[j]; w[j] = w[j - 1]; w[j - 1] = tw;
+        }
+    return 0;
+}
+
+/* (ab|cd) of contracted shells by Rys quadrature, following Sec. II-C step by step:
+ * per primitive quartet p = a + b, q = c + d, P, Q, rho = p q / (p + q), T = rho |P - Q|^2;
+ * n_Rys = floor(L / 2) + 1 roots; per root the B and C coefficients of the standard Rys
+ * definitions, B00 = x / (2(p+q)), B10 = (1 - q x / (p+q)) / (2p), B01 = (1 - p x / (p+q)) / (2q),
+ * C00 = (P - A) - (q x / (p+q)) (P - Q), C00' = (Q - C) + (p x / (p+q)) (P - Q);
+ * the 2-D integrals I(i, k) per Cartesian direction by the vertical recursion of Eq. 6 from
+ * I(0, 0) = 1 (x and y) and I(0, 0) = 2 pi^{5/2} / (p q sqrt(p+q)) K_AB K_CD w_mu (z), the weight
+ * counted once; the horizontal transfer of Eq. 7 to I(i, j, k, l) with A - B and C - D; the
+ * quadrature of Eq. 8, sum over roots of Ix Iy Iz; and the sum over primitives with
+ * c N(alpha, L) per shell. */
+#define RYS_L 12
+int orc_eri_quartet_rys(const orc_shell *sa, const orc_shell *sb, const orc_shell *sc,
+                        const orc_shell *sd, double *out)
+{
+    int La = sa->L, Lb = sb->L, Lc = sc->L, Ld = sd->L;
+    if (La < 0 || Lb < 0 || Lc < 0 || Ld < 0 || La + Lb > RYS_L || Lc + Ld > RYS_L)
+        return -1;
+    int na = ncart(La), nb = ncart(Lb), nc = ncart(Lc), nd = ncart(Ld);
+    memset(out, 0, (size_t)na * nb * nc * nd * sizeof(double));
+    int eh = La + Lb, fh = Lc + Ld, nrys = (La + Lb + Lc + Ld) / 2 + 1;
+    const double *A = sa->center, *B = sb->center, *C = sc->center, *D = sd->center;
+    /* 2-D integrals G[i][k] and the transferred H[i][j][k][l] of one direction */
+    double G[RYS_L + 1][RYS_L + 1];
+    double X[RYS_L + 1][RYS_L + 1][RYS_L + 1]; /* X[i][j][k]: bra transferred, k <= fh */
+    double *H = (double *)malloc(sizeof(double) * 3 * (La + 1) * (Lb + 1) * (Lc + 1) * (Ld + 1));
+    for (int i = 0; i < sa->nprim; ++i)
+        for (int j = 0; j < sb->nprim; ++j)
+            for (int k = 0; k < sc->nprim; ++k)
+                for (int l = 0; l < sd->nprim; ++l) {
+                    double ea = sa->exps[i], eb = sb->exps[j], ec = sc->exps[k], ed = sd->exps[l];
+                    double cw = sa->coefs[i] * orc_norm(ea, La) * sb->coefs[j] * orc_norm(eb, Lb) *
+                                sc->coefs[k] * orc_norm(ec, Lc) * sd->coefs[l] * orc_norm(ed, Ld);
+                    double p = ea + eb, q = ec + ed, P[3], Q[3], AB2 = 0.0, CD2 = 0.0, PQ2 = 0.0;
+                    for (int x = 0; x < 3; ++x) {
+                        P[x] = (ea * A[x] + eb * B[x]) / p;
+                        Q[x] = (ec * C[x] + ed * D[x]) / q;
+                        AB2 += (A[x] - B[x]) * (A[x] - B[x]);
+                        CD2 += (C[x] - D[x]) * (C[x] - D[x]);
+                        PQ2 += (P[x] - Q[x]) * (P[x] - Q[x]);
+                    }
+                    double rho = p * q / (p + q), T = rho * PQ2;
+                    double pref = 2.0 * pow(ORC_PI, 2.5) / (p * q * sqrt(p + q)) *
+                                  exp(-ea * eb / p * AB2) * exp(-ec * ed / q * CD2);
+                    double rt[RYS_NMAX], wt[RYS_NMAX];
+                    orc_rys_roots(nrys, T, rt, wt);
+                    for (int mu = 0; mu < nrys; ++mu) {
+                        double x = rt[mu];
+                        double B00 = x / (2.0 * (p + q));
+                        double B10 = (1.0 - q * x / (p + q)) / (2.0 * p);
+                        double B01 = (1.0 - p * x / (p + q)) / (2.0 * q);
+                        for (int dir = 0; dir < 3; ++dir) {
+                            double C00 = (P[dir] - A[dir]) - q * x / (p + q) * (P[dir] - Q[dir]);
+                            double C00p = (Q[dir] - C[dir]) + p * x / (p + q) * (P[dir] - Q[dir]);
+                            /* Eq. 6: first along k with i = 0, then along i for every k */
+                            G[0][0] = dir == 2 ? pref * wt[mu] : 1.0;
+                            for (int kk = 0; kk < fh; ++kk)
+                                G[0][kk + 1] = kk * B01 * (kk > 0 ? G[0][kk - 1] : 0.0) +
+                                               C00p * G[0][kk];
+                            for (int ii = 0; ii < eh; ++ii)
+                                for (int kk = 0; kk <= fh; ++kk)
+                                    G[ii + 1][kk] = ii * B10 * (ii > 0 ? G[ii - 1][kk] : 0.0) +
+                                                    kk * B00 * (kk > 0 ? G[ii][kk - 1] : 0.0) +
+                                                    C00 * G[ii][kk];
+                            /* Eq. 7 on the bra: X(i, j) = X(i+1, j-1) + (A - B) X(i, j-1) */
+                            double ABd = A[dir] - B[dir], CDd = C[dir] - D[dir];
+                            for (int kk = 0; kk <= fh; ++kk) {
+                                for (int ii = 0; ii <= eh; ++ii)
+                                    X[ii][0][kk] = G[ii][kk];
+                                for (int jj = 1; jj <= Lb; ++jj)
+                                    for (int ii = 0; ii <= eh - jj; ++ii)
+                                        X[ii][jj][kk] = X[ii + 1][jj - 1][kk] + ABd * X[ii][jj - 1][kk];
+                            }
+                            /* Eq. 7 on the ket, per (i <= La, j <= Lb) */
+                            for (int ii = 0; ii <= La; ++ii)
+                                for (int jj = 0; jj <= Lb; ++jj) {
+                                    double Y[RYS_L + 1][RYS_L + 1];
+                                    for (int kk = 0; kk <= fh; ++kk)
+                                        Y[kk][0] = X[ii][jj][kk];
+                                    for (int ll = 1; ll <= Ld; ++ll)
+                                        for (int kk = 0; kk <= fh - ll; ++kk)
+                                            Y[kk][ll] = Y[kk + 1][ll - 1] + CDd * Y[kk][ll - 1];
+                                    for (int kk = 0; kk <= Lc; ++kk)
+                                        for (int ll = 0; ll <= Ld; ++ll)
+                                            H[(((dir * (La + 1) + ii) * (Lb + 1) + jj) * (Lc + 1) + kk) *
+                                                  (Ld + 1) + ll] = Y[kk][ll];
+                                }
+                        }
+                        /* Eq. 8: one term of the quadrature per root */
+#define HIDX(dir, a, b, c, d) \
+    H[((((dir) * (La + 1) + (a)) * (Lb + 1) + (b)) * (Lc + 1) + (c)) * (Ld + 1) + (d)]
+                        for (int ia = 0; ia < na; ++ia)
+                            for (int ib = 0; ib < nb; ++ib)
+                                for (int ic = 0; ic < nc; ++ic)
+                                    for (int id = 0; id < nd; ++id) {
+                                        int ca[3], cb[3], cc[3], cd[3];
+                                        cart_comp(La, ia, ca);
+                                        cart_comp(Lb, ib, cb);
+                                        cart_comp(Lc, ic, cc);
+                                        cart_comp(Ld, id, cd);
+                                        double v = HIDX(0, ca[0], cb[0], cc[0], cd[0]) *
+                                                   HIDX(1, ca[1], cb[1], cc[1], cd[1]) *
+                                                   HIDX(2, ca[2], cb[2], cc[2], cd[2]);
+                                        out[((size_t)(ia * nb + ib) * nc + ic) * nd + id] += cw * v;
+                                    }
+#undef HIDX
+                    }
+                }
+    free(H);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------- */
 /* Gradients of E = sum_abcd G_abcd (ab|cd)                                   */
 /* ------------------------------------------------------------------------- */
 
@@ -705,7 +967,7 @@ static void table_shell(const orc_table *t, int32_t i, orc_shell *s)
 }
 
 /* ERIs of n_quartets shell quartets; quartet q writes at out + offsets[q].  method 0 = OS/HGP,
- * 1 = McMurchie-Davidson.  nthreads <= 0 uses the OpenMP default.  Returns 0 on success. */
+ * 1 = McMurchie-Davidson, 2 = the paper's Rys route (cross-check).  nthreads <= 0 uses the OpenMP default.  Returns 0 on success. */
 int orc_eri_batch(const double *centers, const int32_t *L, const int32_t *nprim,
                   const int64_t *pofs, const double *exps, const double *coefs,
                   const int32_t *quartets, int64_t n_quartets, const int64_t *offsets,
@@ -722,8 +984,9 @@ int orc_eri_batch(const double *centers, const int32_t *L, const int32_t *nprim,
         orc_shell s[4];
         for (int x = 0; x < 4; ++x)
             table_shell(&t, quartets[4 * q + x], &s[x]);
-        int rc = method == 0 ? orc_eri_quartet(&s[0], &s[1], &s[2], &s[3], out + offsets[q])
-                             : orc_eri_quartet_md(&s[0], &s[1], &s[2], &s[3], out + offsets[q]);
+        int rc = method == 0   ? orc_eri_quartet(&s[0], &s[1], &s[2], &s[3], out + offsets[q])
+                 : method == 1 ? orc_eri_quartet_md(&s[0], &s[1], &s[2], &s[3], out + offsets[q])
+                               : orc_eri_quartet_rys(&s[0], &s[1], &s[2], &s[3], out + offsets[q]);
         err |= (rc != 0);
     }
     return err ? -1 : 0;

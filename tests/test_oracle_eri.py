@@ -213,3 +213,66 @@ def test_contraction_linearity():
         p = shells_from(sh.centers, list(cls), exps, coefs)
         total += oracle.eri_quartet(p, [0, 1, 2, 3])
     np.testing.assert_allclose(v, total, rtol=0, atol=1e-14)
+
+
+# ---------------------------------------------------------------- the paper's Rys route
+
+@pytest.mark.parametrize("n", range(1, 8))
+def test_rys_roots_reproduce_boys_moments(n):
+    """Sec. II-C: the n roots x = t^2 and weights integrate x^k exactly against the Rys weight,
+    sum w x^k = F_k(T) for k < 2n (F_k from the oracle's pinned Boys function); 0 < x < 1,
+    w > 0.  T spans the small-T series, the erf branch and the far tail."""
+    for T in [0.0, 1e-8, 0.5, 3.0, 17.0, 39.9, 40.1, 100.0, 169.0, 170.0, 1e3, 1e5, 1e7]:
+        x, w = oracle.rys_roots(n, T)
+        F = oracle.boys(2 * n - 1, T)
+        mom = np.array([np.sum(w * x ** k) for k in range(2 * n)])
+        np.testing.assert_allclose(mom, F, rtol=1e-13, atol=0, err_msg=f"n={n} T={T}")
+        assert np.all((x > 0) & (x < 1)) and np.all(w > 0)
+
+
+def test_rys_one_root_closed_form():
+    """n = 1: w = F_0(T) and x = F_1(T) / F_0(T); at T = 0 that is w = 1, x = 1/3 (to the
+    rounding of the 256-node sums, a few 1e-15)."""
+    x, w = oracle.rys_roots(1, 0.0)
+    assert abs(w[0] - 1.0) < 1e-14 and abs(x[0] - 1.0 / 3.0) < 1e-14
+    for T in [0.3, 5.0, 60.0]:
+        x, w = oracle.rys_roots(1, T)
+        F = oracle.boys(1, T)
+        assert abs(w[0] - F[0]) <= 1e-14 * F[0] and abs(x[0] - F[1] / F[0]) <= 1e-14 * x[0]
+
+
+@pytest.mark.parametrize("n", [1, 3, 5, 7])
+def test_rys_large_T_gauss_hermite_limit(n):
+    """For large T the weight exp(-T t^2) on (0, 1) is the half-line Gaussian up to exp(-T):
+    t_mu sqrt(T) are the positive nodes u of the 2n-point Gauss-Hermite rule and
+    w_mu = W(u) / sqrt(T) (numpy's hermgauss, an independent routine)."""
+    T = 400.0
+    u, W_ = np.polynomial.hermite.hermgauss(2 * n)
+    pos = u > 0
+    x, w = oracle.rys_roots(n, T)
+    np.testing.assert_allclose(x, np.sort(u[pos] ** 2 / T), rtol=1e-11)
+    np.testing.assert_allclose(w, W_[pos][np.argsort(u[pos])] / math.sqrt(T), rtol=1e-11)
+
+
+@pytest.mark.parametrize("cls", all_classes())
+def test_paper_rys_route_matches_md_all_classes(cls):
+    """The paper's scheme written out (roots and weights, B and C of Eq. 6 as read, the weight
+    counted once, Eq. 7 transfer, Eq. 8 quadrature) reproduces the McMurchie-Davidson ERIs on
+    every class: a check of those readings by a route that shares only the Boys function.
+    (A sign flipped in C00' moves results by 1e-10 to 1e-4 of the largest ERI.)"""
+    rng = np.random.default_rng(1000 + W.class_id(*cls))
+    pool = W.random_primitive_pool(rng, 4)
+    q = W.random_class_quartets(rng, cls, 2, 4)
+    a, _ = oracle.eri_batch(pool, q, "rys")
+    b, _ = oracle.eri_batch(pool, q, "md")
+    assert np.max(np.abs(a - b)) <= 1e-13 * max(1.0, np.max(np.abs(b)))
+
+
+def test_paper_rys_route_matches_md_contracted():
+    rng = np.random.default_rng(8)
+    pool = W.random_contracted_pool(rng, 3, K=3, Ls=(0, 1, 2, 3))
+    for cls in [(1, 1, 1, 1), (2, 1, 2, 0), (3, 2, 1, 3), (3, 3, 3, 3)]:
+        q = W.random_class_quartets(rng, cls, 2, 3, Ls=(0, 1, 2, 3))
+        a, _ = oracle.eri_batch(pool, q, "rys")
+        b, _ = oracle.eri_batch(pool, q, "md")
+        assert np.max(np.abs(a - b)) <= 1e-13 * max(1.0, np.max(np.abs(b)))

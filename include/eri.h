@@ -113,10 +113,13 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
 /* Frees the plan and its device memory.  NULL is ignored. */
 void eri_plan_destroy(eri_plan_t plan);
 
-/* Changes the precision used by later compute calls (ERI_FP64 or ERI_MIXED). */
+/* Changes the precision used by later compute calls (ERI_FP64 or ERI_MIXED).  Host only;
+ * ERI_E_INVALID for a NULL plan or another value. */
 eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);
 
-/* Precision of one class, overriding the plan's (ERI_FP64, ERI_MIXED, or -1 to follow the plan). */
+/* Precision of one class, overriding the plan's (ERI_FP64, ERI_MIXED, or -1 to follow the plan).
+ * Host only (drops the cached graph of eri_compute_compressed_batched); ERI_E_INVALID for a NULL
+ * plan, cls outside 0..255 or another value. */
 eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision);
 
 /* Chooses the precision of every class of the plan for `bits`-bit output: FP32 recurrences
@@ -130,33 +133,39 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
                                           float max_err_steps, void *stream);
 
 /* Effective precision of a class and the error measured by eri_plan_calibrate_precision
- * (-1 when not measured).  Either output may be NULL. */
+ * (-1 when not measured).  Either output may be NULL.  ERI_E_INVALID for a NULL plan or cls
+ * outside 0..255. */
 eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *precision,
                                       float *mixed_err);
 
 /* Kernel launches eri_compute_class / eri_compute_compressed_class make for class cls in its
  * current precision: 1 for the fused kernels, 2 per chunk of 2^20 quartets (setup and
- * recurrence kernels) on the split path of primitive plans, 0 for an empty class. */
+ * recurrence kernels) on the split path of primitive plans, 0 for an empty class.
+ * ERI_E_INVALID for a NULL plan or output, or cls outside 0..255. */
 eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches);
 
-/* Total quartets in the plan. */
+/* Total quartets in the plan.  ERI_E_INVALID if either argument is NULL. */
 eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);
 
 /* Per-class layout.  cls = ((La*4 + Lb)*4 + Lc)*4 + Ld.  Any output pointer may be NULL.
  *   n_quartets          quartets of this class in the plan
  *   n_eri_per_quartet   n_ga n_gb n_gc n_gd (Sec. II-A shell sizes)
  *   first_quartet       index of the class's first quartet in class-sorted order
- *   fp64_offset         offset (in doubles) of the class's first ERI in eri_compute's output */
+ *   fp64_offset         offset (in doubles) of the class's first ERI in eri_compute's output
+ * Host only; ERI_E_INVALID for a NULL plan or cls outside 0..255. */
 eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quartets,
                                  int32_t *n_eri_per_quartet, int64_t *first_quartet,
                                  int64_t *fp64_offset);
 
 /* perm_out[i] = caller's index of the quartet at class-sorted position i (host array of
- * eri_plan_num_quartets entries).  For ERI_ALL, index = ((i*n + j)*n + k)*n + l. */
+ * eri_plan_num_quartets entries).  For ERI_ALL, index = ((i*n + j)*n + k)*n + l.
+ * Synchronous (reads the plan's device permutation); ERI_E_INVALID for a NULL plan, or a NULL
+ * perm_out when the plan has quartets; ERI_E_CUDA if the copy fails. */
 eri_status_t eri_plan_quartet_order(eri_plan_t plan, int64_t *perm_out);
 
 /* Sizes of the outputs of eri_compute_compressed for a bitwidth (bits = 0: eri_compute's FP64
- * output).  packed_bytes covers all classes; scales_bytes = 4 * n_quartets. */
+ * output).  packed_bytes covers all classes; scales_bytes = 4 * n_quartets.  Host only;
+ * ERI_E_INVALID for a NULL plan or bits other than 0 and 2..24.  Either output may be NULL. */
 eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_bytes,
                               size_t *scales_bytes);
 
@@ -165,7 +174,8 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
  * first stream of n-bit two's complement fields: ERI v of the class (v = quartet-in-class *
  * n_eri + index-in-quartet) occupies stream bits [v*bits, (v+1)*bits), stream bit s being
  * bit s%32 of 32-bit word s/32.  For bits = 8 and 16 this is a plain int8/int16 array.
- * Bits past the class's last field up to the segment end are zero. */
+ * Bits past the class's last field up to the segment end are zero.  Host only; ERI_E_INVALID
+ * for a NULL plan, bits outside 2..24 or cls outside 0..255.  Either output may be NULL. */
 eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                      size_t *byte_offset, size_t *bytes);
 
@@ -200,7 +210,9 @@ eri_status_t eri_pack_paper512_stream(const void *d_stream, int64_t n_quartets, 
 
 /* FP64 ERIs of every quartet (Eqs. 5-8 per primitive quartet, summed over primitives) into
  * d_out (eri_output_bytes(plan, 0, ...) bytes, class-sorted, see fp64_offset).
- * Asynchronous on `stream`; the launches per class are given by eri_plan_class_launches. */
+ * Asynchronous on `stream`; the launches per class are given by eri_plan_class_launches.
+ * ERI_E_INVALID for a NULL plan, a NULL d_out when the plan has quartets, or a d_out that is not
+ * 8-byte aligned; ERI_E_CUDA if a launch fails.  Non-finite results are latched (eri_sync). */
 eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream);
 
 /* Same as eri_compute for one class only (cls as in eri_plan_class_info); d_out is the
@@ -214,7 +226,8 @@ eri_status_t eri_compute_class(eri_plan_t plan, int32_t cls, double *d_out, void
  *   bits       2..24 (eps has a 24-bit significand; wider codes would exceed +-(2^{n-1}-1))
  *   d_packed   eri_output_bytes(plan, bits, ...).packed bytes, layout of eri_packed_class_offset
  *   d_scales   one float eps per quartet, class-sorted
- * Asynchronous on `stream`. */
+ * Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits outside 2..24, or NULL or
+ * not 4-byte-aligned buffers when the plan has quartets; ERI_E_CUDA if a launch fails. */
 eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,
                                     void *stream);
 

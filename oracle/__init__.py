@@ -72,6 +72,8 @@ def _load():
         lib.orc_unpack_bits.argtypes = [p, i64, ctypes.c_int, p]
         lib.orc_rys_roots.restype = ctypes.c_int
         lib.orc_rys_roots.argtypes = [ctypes.c_int, d, p, p]
+        lib.orc_digest_jk.restype = None
+        lib.orc_digest_jk.argtypes = [p, p, p, i64, p, p, i64, p, p, p]
         lib.orc_pack_paper512.restype = None
         lib.orc_pack_paper512.argtypes = [p, i64, i64, ctypes.c_int, p]
         lib.orc_unpack_paper512.restype = None
@@ -232,6 +234,64 @@ def rys_roots(n: int, T: float):
     if _load().orc_rys_roots(int(n), float(T), _ptr(x), _ptr(w)) != 0:
         raise ValueError("n out of range")
     return x, w
+
+
+def basis_offsets(shells) -> np.ndarray:
+    """First basis function of every shell (shells in order, ncart(L) functions each)."""
+    n = np.array([ncart(int(l)) for l in shells.L], dtype=np.int64)
+    off = np.zeros(len(n) + 1, dtype=np.int64)
+    np.cumsum(n, out=off[1:])
+    return off
+
+
+def digest_jk(shells, quartets: np.ndarray, values: np.ndarray, offsets: np.ndarray, D: np.ndarray):
+    """Coulomb J[mu,nu] = sum (mu nu|lam sig) D[lam,sig] and exchange K[mu,lam] =
+    sum (mu nu|lam sig) D[nu,sig] over the listed quartets, each counted once as listed;
+    values/offsets as eri_batch returns them.  Returns (J, K)."""
+    t = _Table(shells)
+    bf = basis_offsets(shells)
+    nbf = int(bf[-1])
+    q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+    x = np.ascontiguousarray(values, dtype=np.float64)
+    off = np.ascontiguousarray(offsets, dtype=np.int64)
+    D = np.ascontiguousarray(D, dtype=np.float64)
+    assert D.shape == (nbf, nbf) and len(off) >= len(q)
+    J = np.zeros((nbf, nbf))
+    K = np.zeros((nbf, nbf))
+    _load().orc_digest_jk(_ptr(x), _ptr(off), _ptr(q), len(q), _ptr(t.L), _ptr(bf), nbf,
+                          _ptr(D), _ptr(J), _ptr(K))
+    return J, K
+
+
+# The eight index permutations of (ab|cd) under which a real ERI is invariant (Sec. II-B):
+# position i of the permuted quartet holds position PERM8[k][i] of the original.
+PERM8 = ((0, 1, 2, 3), (1, 0, 2, 3), (0, 1, 3, 2), (1, 0, 3, 2),
+         (2, 3, 0, 1), (3, 2, 0, 1), (2, 3, 1, 0), (3, 2, 1, 0))
+
+
+def expand_unique8(shells, quartets: np.ndarray, values: np.ndarray, offsets: np.ndarray):
+    """Every distinct ordered quartet reachable from the listed ones by the 8-fold symmetry,
+    each once, with its ERI block (the listed block with its axes permuted alike).  Applied to
+    the unique quartets (a >= b, c >= d, pair ab >= pair cd) it yields every ordered quartet
+    once.  Returns (quartets, values, offsets) in the layout of eri_batch."""
+    q = np.asarray(quartets).reshape(-1, 4)
+    L = np.asarray(shells.L)
+    seen = set()
+    out_q, blocks = [], []
+    for i, row in enumerate(q):
+        shape = tuple(ncart(int(L[s])) for s in row)
+        block = np.asarray(values[offsets[i]:offsets[i + 1]]).reshape(shape)
+        for perm in PERM8:
+            t = tuple(int(row[k]) for k in perm)
+            if t in seen:
+                continue
+            seen.add(t)
+            out_q.append(t)
+            blocks.append(np.transpose(block, perm).ravel())
+    off = np.zeros(len(blocks) + 1, dtype=np.int64)
+    np.cumsum([len(b) for b in blocks], out=off[1:])
+    vals = np.concatenate(blocks) if blocks else np.zeros(0)
+    return np.array(out_q, dtype=np.int32).reshape(-1, 4), vals, off
 
 
 def paper512_chunks(n_eri: int, bits: int) -> int:

@@ -13,7 +13,8 @@
  *   - the Boys function F_m(T) = int_0^1 t^{2m} exp(-T t^2) dt;
  *   - the lossy compression of Sec. II-D: eps = b_max / (2^{n-1}-1) (Eq. 9),
  *     q = ANINT(x / eps) (Eq. 10), x~ = q * eps (Eq. 11);
- *   - nuclear-centre and exponent gradients of E = sum G_abcd (ab|cd).
+ *   - nuclear-centre and exponent gradients of E = sum G_abcd (ab|cd);
+ *   - the Coulomb and exchange matrices J and K of a density matrix (orc_digest_jk).
  *
  * The reference ERIs are NOT evaluated with the paper's Rys scheme.  Two independent
  * exact-in-principle schemes named in Sec. II-C are used instead:
@@ -1023,6 +1024,44 @@ int orc_eri_grad_batch(const double *centers, const int32_t *L, const int32_t *n
         }
     }
     return 0;
+}
+
+/* ------------------------------------------------------------------------- */
+/* Coulomb and exchange digestion of ERI blocks                               */
+/* ------------------------------------------------------------------------- */
+
+/* What the ERIs, and their compressed copies, are computed for (Sec. I: the Hartree-Fock
+ * exchange of hybrid DFT in AIMD; Sec. II-D: ERIs kept compressed in memory between uses) is
+ * their contraction with a density matrix D.  For every listed shell quartet (a b | c d), with
+ * its ERI block x laid out as eri_batch writes it, and basis functions mu of a, nu of b, lam of
+ * c, sig of d:
+ *   J[mu][nu]  += sum_{lam, sig} (mu nu | lam sig) D[lam][sig]   (Coulomb)
+ *   K[mu][lam] += sum_{nu, sig}  (mu nu | lam sig) D[nu][sig]    (exchange)
+ * Every listed quartet counts once, as listed: no permutation of it is implied.  bf_off[s] is the
+ * first basis function of shell s; D, J and K are n_bf x n_bf, row major; J and K accumulate. */
+void orc_digest_jk(const double *x, const int64_t *offsets, const int32_t *quartets,
+                   int64_t n_quartets, const int32_t *L, const int64_t *bf_off, int64_t n_bf,
+                   const double *D, double *J, double *K)
+{
+    for (int64_t q = 0; q < n_quartets; ++q) {
+        const int32_t *s = quartets + 4 * q;
+        int n[4];
+        int64_t o[4];
+        for (int i = 0; i < 4; ++i) {
+            n[i] = ncart(L[s[i]]);
+            o[i] = bf_off[s[i]];
+        }
+        const double *v = x + offsets[q];
+        for (int a = 0; a < n[0]; ++a)
+            for (int b = 0; b < n[1]; ++b)
+                for (int c = 0; c < n[2]; ++c)
+                    for (int d = 0; d < n[3]; ++d) {
+                        double e = v[((a * n[1] + b) * n[2] + c) * n[3] + d];
+                        int64_t mu = o[0] + a, nu = o[1] + b, lam = o[2] + c, sig = o[3] + d;
+                        J[mu * n_bf + nu] += e * D[lam * n_bf + sig];
+                        K[mu * n_bf + lam] += e * D[nu * n_bf + sig];
+                    }
+    }
 }
 
 /* ------------------------------------------------------------------------- */

@@ -52,3 +52,46 @@ def test_paper512_stream_validates_before_touching_the_device():
     assert lib.eri_pack_paper512_stream(4098, 1, 10, 16, 8192, None) == bad     # misaligned
     assert lib.eri_pack_paper512_stream(None, 1, 10, 16, 8192, None) == bad     # null
     assert lib.eri_pack_paper512_stream(4096, -1, 10, 16, 8192, None) == bad    # negative count
+
+
+C_CLIENT = r"""
+#include <stdio.h>
+#include <string.h>
+#include "eri.h"
+int main(void) {
+    int32_t ne = 0, nr = 0;
+    if (eri_class_id(3, 3, 3, 3) != 255 || eri_class_id(4, 0, 0, 0) != -1) return 1;
+    if (eri_class_shape(255, &ne, &nr) != ERI_OK || ne != 10000 || nr != 7) return 2;
+    if (eri_class_shape(256, &ne, &nr) != ERI_E_INVALID) return 3;
+    if (strcmp(eri_status_string(ERI_E_NUMERIC), "ERI_E_NUMERIC") != 0) return 4;
+    if (eri_pack_paper512_stream(NULL, 0, 10, 16, NULL, NULL) != ERI_OK) return 5;
+    if (eri_pack_paper512_stream((const void *)4096, 1, 10, 25, (void *)8192, NULL) != ERI_E_INVALID)
+        return 6;
+    if (eri_plan_num_quartets(NULL, NULL) != ERI_E_INVALID) return 7;
+    eri_plan_destroy(NULL);
+    puts("ok");
+    return 0;
+}
+"""
+
+
+def test_header_is_plain_c_and_links(tmp_path):
+    """A C99 program includes eri.h under -pedantic -Werror, links the library by name and calls
+    the host-only entry points (no device needed): the boundary is a plain C ABI."""
+    import shutil
+    import subprocess
+    from paper_2303_13632_gb300 import build
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("gcc not available")
+    lib = build.build()
+    src = tmp_path / "client.c"
+    src.write_text(C_CLIENT)
+    exe = tmp_path / "client"
+    libdir = os.path.dirname(lib)
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", os.path.join(ROOT, "include"), str(src), "-L", libdir, "-leri_gb300",
+                        f"-Wl,-rpath,{libdir}", "-o", str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "ok", (r.returncode, r.stdout, r.stderr)

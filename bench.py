@@ -106,6 +106,35 @@ def read_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
+def measure_alu_peaks(api, torch, stream, device_index):
+    """FP32 and FP64 fused multiply-add throughput measured with the library's probe kernel
+    (eri_fma_probe: 8 independent FMA chains per thread, 1216 x 256-thread blocks = 8 CTAs per SM),
+    best of 3 launches timed with CUDA events on the launching stream, with the SM clock sampled
+    during the FP64 probe.  Returns {"fp32_tflops", "fp64_tflops", "clocks"}."""
+    n_threads = 152 * 8 * 256
+    sink = torch.empty(n_threads, dtype=torch.float64, device=torch.device("cuda", device_index))
+    out = {}
+    for prec, iters in (("mixed", 4096), ("fp64", 96)):
+        best = None
+        clk = ClockSampler(device_index) if prec == "fp64" else None
+        if clk:
+            clk.start()
+        for rep in range(4):  # first launch warms up
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            api.eri_fma_probe(prec, n_threads, iters, sink, stream)
+            b.record(stream)
+            b.synchronize()
+            if rep:
+                ms = a.elapsed_time(b)
+                best = ms if best is None else min(best, ms)
+        if clk:
+            out["clocks"] = clk.stop()
+        tflops = 256.0 * iters * n_threads / (best * 1e-3) / 1e12
+        out["fp32_tflops" if prec == "mixed" else "fp64_tflops"] = tflops
+    return out
+
+
 class ClockSampler:
     """nvidia-smi samples (every 200 ms) of SM clock and throttle reasons."""
 
@@ -306,12 +335,20 @@ def run_ours(args):
     choice16 = class_choices(api, plan)
     launches = sum(api.eri_plan_class_launches(plan, c) for c in range(256))
 
+    # ---- measured ALU peaks (the roofline denominators of the FP-bound kernels) ----
+    alu = measure_alu_peaks(api, torch, stream, local)
+    p32, p64 = alu["fp32_tflops"], alu["fp64_tflops"]
+
     # ---- headline: all 256 classes per step, FP32 recurrences where calibrated ----
     ms, clk = timed_steps(args.warmup, args.steps, ClockSampler(local))
     value = job_geris(total_eris, world, ms)
     # every class in FP32 (no calibration), for context
     apply_choices(api, plan, None)
     ms_all32, _ = timed_steps(1, args.steps)
+    # the plain FP64 path as a timed step of the same call (every class in FP64)
+    api.eri_plan_set_precision(plan, "fp64")
+    ms_fp64_step, _ = timed_steps(1, args.steps)
+    api.eri_plan_set_precision(plan, "mixed")
 
     # ---- per-class timing, mixed and FP64 (events on the launching stream) ----
     def per_class_ms(precision):
@@ -331,36 +368,47 @@ def run_ours(args):
     ms_mixed = per_class_ms("mixed")
     ms_fp64 = per_class_ms("fp64")
     api.eri_plan_set_precision(plan, "mixed")
-    fp64_total_ms = sum(ms_fp64.values())
     # per-class time and precision of the headline configuration
     ms_cal = {c: (ms_mixed[c] if choice16[c] == "mixed" else ms_fp64[c]) for c in ms_mixed}
 
-    # ---- roofline of the dominant kernel (largest share of the mixed step) ----
+    # ---- roofline: per class, per kernel instantiation, and weighted over the step ----
     peaks, peak_kind = read_peaks()
-    dom = max(ms_cal, key=lambda c: ms_cal[c])
-    dcls = cls_list[dom]
-    dprec = choice16[dom]
-    flops = perfmodel.fp32_equivalent_flops(dcls, dprec) * counts[dom]
-    achieved = flops / (ms_cal[dom] * 1e-3) / 1e12
-    t_roof = perfmodel.roofline_seconds(dcls, counts[dom], dprec, BITS, peaks["hbm_gbs"])
-    roof = {"bound": "alu", "kernel": f"class {W.class_id(*dcls)} {fmt_class(dcls)} {dprec}",
-            "achieved": achieved, "peak": perfmodel.PEAK_FP32_TFLOPS, "unit": "TFLOP/s",
-            "frac": t_roof / (ms_cal[dom] * 1e-3), "traffic": None,
-            "peak_kind": "nominal FP32 (152 SMs x 128 lanes x 2 x 2.07 GHz); FP64 work weighted "
-                         "by the FP32/FP64 peak ratio (1.25 TFLOP/s FP64)",
-            "share": ms_cal[dom] / sum(ms_cal.values())}
+    apply_choices(api, plan, choice16)
+    t_roof = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], choice16[c], BITS, peaks["hbm_gbs"], p32, p64)
+              for c in ms_cal}
+    frac_all = {c: t_roof[c] / (ms_cal[c] * 1e-3) for c in ms_cal}
+    # generic classes served by the same kernel instantiation(s) (canonical class, precision,
+    # kernel form) are one kernel in the launch list: group them, and take the instantiation
+    # with the largest share of the step as the dominant kernel
+    groups = {}
+    for c in ms_cal:
+        groups.setdefault(api.eri_plan_class_kernels(plan, c), []).append(c)
+    dom_name = max(groups, key=lambda k: sum(ms_cal[c] for c in groups[k]))
+    dom = groups[dom_name]
+    t_dom = sum(ms_cal[c] for c in dom) * 1e-3
+    flops = sum(perfmodel.fp32_equivalent_flops(cls_list[c], choice16[c], p32, p64) * counts[c] for c in dom)
+    roof = {"bound": "alu", "kernel": dom_name, "classes": [fmt_class(cls_list[c]) for c in dom],
+            "achieved": flops / t_dom / 1e12, "peak": p32, "unit": "TFLOP/s",
+            "frac": sum(t_roof[c] for c in dom) / t_dom, "traffic": None,
+            "peak_source": "measured: eri_fma_probe FP32 and FP64 FMA loops in this run "
+                           f"({p32:.1f} / {p64:.3f} TFLOP/s); FP64 work weighted by their ratio",
+            "fp64_peak_tflops": p64, "probe_clocks": alu.get("clocks"),
+            "share": t_dom / (sum(ms_cal.values()) * 1e-3),
+            "frac_step_weighted": sum(t_roof.values()) / (sum(ms_cal.values()) * 1e-3),
+            "frac_of_ms_per_step": sum(t_roof.values()) / (ms * 1e-3),
+            "frac_nominal_peaks": sum(perfmodel.roofline_seconds(cls_list[c], counts[c], choice16[c], BITS,
+                                                                 peaks["hbm_gbs"]) for c in dom) / t_dom}
     # DRAM traffic of the dominant kernel: bytes per quartet from the committed ncu capture of
-    # the same kernel (a smaller case of the class), scaled to this launch's quartets
+    # the same instantiation (a smaller case of one of its classes), scaled to this step's quartets
     try:
         with open(os.path.join(ROOT, "profiles", "dram_bytes_per_quartet.json")) as f:
             tr = json.load(f)
-        if tr["class"] == dom and tr["precision"] == dprec:
-            roof["traffic"] = tr["dram_bytes_per_quartet"] * counts[dom]
-            roof["traffic_source"] = tr["source"] + f", scaled to {counts[dom]} quartets"
+        if tr["kernel"] == dom_name:
+            nq_dom = sum(counts[c] for c in dom)
+            roof["traffic"] = tr["dram_bytes_per_quartet"] * nq_dom
+            roof["traffic_source"] = tr["source"] + f", scaled to the {nq_dom} quartets of its classes"
     except (OSError, KeyError, ValueError):
         pass
-    frac_all = {c: perfmodel.roofline_seconds(cls_list[c], counts[c], choice16[c], BITS, peaks["hbm_gbs"])
-                / (ms_cal[c] * 1e-3) for c in ms_cal}
 
     # ---- accuracy on a sample, and the CPU oracle baseline ----
     line_extra = {}
@@ -482,11 +530,13 @@ def run_ours(args):
                                   f"per class stays below {CALIB_STEPS} quantisation steps (16-bit)"},
             "mixed_all_fp32": {"value": total_eris / (ms_all32 * 1e-3) / 1e9, "unit": "GERIS",
                                "ms_per_step": ms_all32},
-            "fp64": {"value": total_eris / (fp64_total_ms * 1e-3) / 1e9, "unit": "GERIS",
-                     "ms_per_step": fp64_total_ms, "speedup_mixed_over_fp64": fp64_total_ms / ms},
+            "fp64": {"value": total_eris / (ms_fp64_step * 1e-3) / 1e9, "unit": "GERIS",
+                     "ms_per_step": ms_fp64_step, "speedup_mixed_over_fp64": ms_fp64_step / ms,
+                     "how": "timed steps of eri_compute_compressed with every class in FP64"},
             "roofline": roof,
             "roofline_frac_per_class": {"min": min(frac_all.values()), "median": statistics.median(frac_all.values()),
-                                        "max": max(frac_all.values())},
+                                        "max": max(frac_all.values()),
+                                        "step_weighted": sum(t_roof.values()) / (sum(ms_cal.values()) * 1e-3)},
             "clocks": clk, "gpu_launches": launches * args.steps,
             "per_class_geris": {"mixed": geris_mixed, "fp64": geris_fp64},
         }
@@ -636,41 +686,38 @@ def run_lattice(args):
 
 def run_molecule(args):
     """Batched mixed workload: 200 atoms in a 20-bohr box (min separation 1.8 bohr), shells
-    s, s, p, p, d, f per atom, contraction degree 1..6, all unique (8-fold) shell quartets
-    surviving Schwarz screening at 1e-10 counted; a seeded budget of about 2^30 ERIs of them
-    computed in one CUDA-graph launch of persistent kernels (mixed precision, 16-bit)."""
+    s, s, p, p, d, f per atom, contraction degree 1..6.  The library enumerates the 8-fold unique
+    shell quartets surviving Schwarz screening at 1e-10 on the device (ERI_UNIQUE8) and keeps an
+    even 1-in-s shard of that enumeration sized to about 2^30 ERIs; the shard is computed in one
+    CUDA-graph launch of persistent kernels (mixed precision, 16-bit), and its compressed output
+    is digested into Coulomb and exchange matrices (eri_digest_jk, 8-fold expansion)."""
     import torch
 
     import oracle
-    from paper_2303_13632_gb300 import api, screening as S
+    from paper_2303_13632_gb300 import api
 
     torch.cuda.set_device(0)
     dev = torch.device("cuda", 0)
     stream = torch.cuda.current_stream()
     basis = W.molecule_basis()
-    pairs = S.unique_pairs(basis)
-    t0 = time.perf_counter()
-    qdiag = np.stack([pairs[:, 0], pairs[:, 1], pairs[:, 0], pairs[:, 1]], axis=1).astype(np.int32)
-    dplan = api.eri_plan_create(basis, qdiag, precision="fp64")
-    nb, sb = api.eri_output_bytes(dplan, 8)
-    pk = torch.empty(nb // 4, dtype=torch.int32, device=dev)
-    sc = torch.empty(sb // 4, dtype=torch.float32, device=dev)
-    api.eri_compute_compressed(dplan, 8, pk, sc, stream)
-    api.eri_sync(dplan, stream)
-    bmax = np.zeros(len(pairs))
-    bmax[api.eri_plan_quartet_order(dplan)] = sc.cpu().numpy().astype(np.float64) * 127.0
-    dplan.destroy()
-    t_schwarz = time.perf_counter() - t0
     tau = 1e-10
-    sq = S.ScreenedQuartets(basis, pairs, np.sqrt(bmax), tau)
-    counts = sq.class_counts()
-    n_unique = int(sum(counts.values()))
-    eris_all = int(sum(v * W.quartet_size(*W.class_of_id(k)) for k, v in counts.items()))
-    rng = np.random.default_rng(W.SEED_BASE + 4)
     budget = int(2 ** 30 * args.scale)
-    q = sq.sample(rng, budget)
-    plan = api.eri_plan_create(basis, q, precision="mixed")
-    n_eri = int(oracle.quartet_sizes(basis, q).sum())
+    t0 = time.perf_counter()
+    probe = api.eri_plan_create(basis, None, mode="unique8", schwarz_threshold=tau, shard=(0, 1 << 62))
+    n_cand, n_kept = api.eri_plan_screening(probe)
+    probe.destroy()
+    t_screen = time.perf_counter() - t0
+    # ERIs per quartet of the screened set, from a 1-in-s0 shard of about 2^20 quartets
+    s0 = max(1, n_kept // (1 << 20))
+    p0 = api.eri_plan_create(basis, None, mode="unique8", schwarz_threshold=tau, shard=(0, s0))
+    eri_per_q = api.eri_output_bytes(p0, 0)[0] / 8 / max(1, api.eri_plan_num_quartets(p0))
+    p0.destroy()
+    eris_all = int(round(n_kept * eri_per_q))
+    shard_count = max(1, int(round(n_kept * eri_per_q / budget)))
+    plan = api.eri_plan_create(basis, None, precision="mixed", mode="unique8", schwarz_threshold=tau,
+                               shard=(0, shard_count))
+    q = api.eri_plan_quartets(plan)
+    n_eri = api.eri_output_bytes(plan, 0)[0] // 8
     nb, sb = api.eri_output_bytes(plan, BITS)
     packed = torch.empty(nb // 4, dtype=torch.int32, device=dev)
     scales = torch.empty(sb // 4, dtype=torch.float32, device=dev)
@@ -688,6 +735,19 @@ def run_molecule(args):
     apply_choices(api, plan, choice)
     api.eri_compute_compressed_batched(plan, BITS, packed, scales, stream)
     api.eri_sync(plan, stream)
+    # Coulomb/exchange digestion of the compressed shard (8-fold expansion of each quartet)
+    nbf = api.eri_plan_num_basis_functions(plan)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(W.SEED_BASE + 44)
+    D = torch.randn((nbf, nbf), dtype=torch.float64, device=dev, generator=gen)
+    D = (D + D.T) / 2
+    J = torch.empty_like(D)
+    K = torch.empty_like(D)
+    ms_digest = _events(torch, stream, lambda: api.eri_digest_jk(plan, BITS, packed, scales, D, J, K,
+                                                                 unique8=True, stream=stream), reps=3)
+    api.eri_sync(plan, stream)
+    digest_bytes = nb + sb + 16 * len(q)  # codes, scales and the quartet table read once
+    peaks, _ = read_peaks()
     out = {"impl": "ours", "workload": "molecule",
            "metric": "GERIS, batched persistent CUDA-graph launch, mixed precision, 16-bit",
            "precision": {"classes_fp32": sum(v == "mixed" for v in choice.values()),
@@ -695,29 +755,32 @@ def run_molecule(args):
            "value": n_eri / (ms_graph * 1e-3) / 1e9, "unit": "GERIS",
            "per_class_launches_geris": n_eri / (ms_plain * 1e-3) / 1e9,
            "fp64_batched_geris": n_eri / (ms_fp64 * 1e-3) / 1e9,
-           "budget": {"quartets": int(len(q)), "eris": n_eri},
-           "screened_unique_quartets": n_unique, "screened_unique_eris": eris_all,
-           "shells": int(basis.n), "pairs": int(len(pairs)), "schwarz_s": t_schwarz, "tau": tau}
+           "budget": {"quartets": int(len(q)), "eris": int(n_eri), "shard": f"1 in {shard_count}"},
+           "screened_unique_quartets": int(n_kept), "unique_quartets_before_screening": int(n_cand),
+           "screened_unique_eris_estimate": eris_all,
+           "shells": int(basis.n), "basis_functions": int(nbf), "screening_s": t_screen, "tau": tau,
+           "digest_jk": {"geris": n_eri / (ms_digest * 1e-3) / 1e9, "ms": ms_digest,
+                         "hbm_gbs": digest_bytes / (ms_digest * 1e-3) / 1e9,
+                         "hbm_frac": digest_bytes / (ms_digest * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "algorithmic_bytes": int(digest_bytes),
+                         "note": "compressed ERIs of the shard -> J, K with the 8-fold expansion"}}
     if not args.no_check:
         # parity on sampled quartets of modest primitive count
         L = np.asarray(basis.L)
         kprod = np.prod([basis.nprim[q[:, x]] for x in range(4)], axis=0)
         cost = kprod * oracle.quartet_sizes(basis, q)
+        rng = np.random.default_rng(W.SEED_BASE + 4)
         cand = np.nonzero(cost <= 200000)[0]
         pick = np.sort(rng.choice(cand, size=min(200, len(cand)), replace=False))
         ref, offs = oracle.eri_batch(basis, q[pick])
-        order = api.eri_plan_quartet_order(plan)
-        pos = np.empty(len(order), dtype=np.int64)
-        pos[order] = np.arange(len(order))
         words = packed.cpu().numpy().view(np.uint32)
         scl = scales.cpu().numpy()
         worst_rel = 0.0
-        for j, i in enumerate(pick):
-            cls = W.class_id(*[int(L[s]) for s in q[i]])
+        for j, i in enumerate(pick):  # i: class-sorted position (the plan's own order)
+            cls = W.class_id(*[int(L[s_]) for s_ in q[i]])
             nq_c, neri, fq, _ = api.eri_plan_class_info(plan, cls)
             off_b, _ = api.eri_packed_class_offset(plan, BITS, cls)
-            k = int(pos[i] - fq)
-            x = unpack(words, off_b, np.array([k]), neri, BITS)[0] * float(scl[pos[i]])
+            x = unpack(words, off_b, np.array([i - fq]), neri, BITS)[0] * float(scl[i])
             r = ref[offs[j]:offs[j + 1]]
             bm = max(np.max(np.abs(r)), 1e-300)
             worst_rel = max(worst_rel, float(np.max(np.abs(x - r)) / bm))

@@ -51,7 +51,8 @@ typedef enum {
     ERI_E_UNSUPPORTED = 2, /* valid request this build does not serve */
     ERI_E_NOMEM = 3,       /* device or host allocation failed */
     ERI_E_CUDA = 4,        /* a CUDA runtime call failed (launch, copy, sync) */
-    ERI_E_TIMEOUT = 5,     /* a bounded device wait gave up (latched, see eri_sync) */
+                           /* 5 is not used: no kernel of this library waits on a flag or a
+                              peer, so no bounded wait can give up */
     ERI_E_NUMERIC = 6      /* a non-finite ERI was produced (latched, see eri_sync) */
 } eri_status_t;
 
@@ -69,7 +70,14 @@ enum {
 /* How eri_plan_create obtains the quartet list. */
 enum {
     ERI_EXPLICIT = 0, /* the caller's list of n_quartets x 4 shell ids */
-    ERI_ALL = 1       /* every ordered quartet (i, j, k, l) of the n_shells shells */
+    ERI_ALL = 1,      /* every ordered quartet (i, j, k, l) of the n_shells shells */
+    ERI_UNIQUE8 = 2   /* one quartet per class of the 8-fold permutational symmetry (Sec. II-B,
+                         (ij|kl) = (ji|kl) = (ij|lk) = (kl|ij) = ...), enumerated on the device:
+                         the unordered shell pairs (i >= j) are ranked by decreasing Schwarz
+                         factor Q_ij (ties by increasing i (i+1)/2 + j; all Q are equal without
+                         screening), and every pair of ranks r <= s gives the quartet
+                         (i_r, j_r, i_s, j_s), listed by r, then s; see schwarz_threshold and
+                         shard_count.  `quartets` and n_quartets are ignored. */
 };
 
 /* Flags of eri_plan_opts_t.flags */
@@ -89,9 +97,19 @@ typedef struct {
 
 typedef struct {
     int32_t precision;    /* ERI_FP64 or ERI_MIXED */
-    int32_t quartet_mode; /* ERI_EXPLICIT or ERI_ALL */
+    int32_t quartet_mode; /* ERI_EXPLICIT, ERI_ALL or ERI_UNIQUE8 */
     int32_t device;       /* CUDA device ordinal the plan lives on */
     int32_t flags;        /* ERI_QUARTETS_ON_DEVICE | ERI_NO_PAIR_TABLE */
+    double schwarz_threshold; /* > 0: keep only quartets with Q_ij Q_kl >= threshold, where
+                                 Q_ij = sqrt(max |(ab|ab)|) over the components of the pair (the
+                                 Cauchy-Schwarz bound |(ij|kl)| <= Q_ij Q_kl), the diagonal ERIs
+                                 computed in FP64 by this library's kernels; applies to every
+                                 quartet mode.  0 = no screening. */
+    int64_t shard_index;  /* ERI_UNIQUE8 only: with shard_count > 1 the plan keeps the quartets */
+    int64_t shard_count;  /* at positions shard_index, shard_index + shard_count, ... of the
+                             screened enumeration (an even 1-in-shard_count subset, e.g. one
+                             replica's share of a job, or a bounded sample of a workload too
+                             large to hold).  0 or 1 = all. */
 } eri_plan_opts_t;
 
 /* Builds a plan: validates and normalises the shells, classifies and sorts the quartets by
@@ -103,10 +121,21 @@ typedef struct {
  * rounding order).
  *   shells      n_shells entries (host)
  *   quartets    n_quartets x 4 int32 shell ids, row major (host unless
- *               ERI_QUARTETS_ON_DEVICE), or NULL with ERI_ALL
- *   opts        NULL for defaults (ERI_FP64, ERI_EXPLICIT, device 0, no flags)
+ *               ERI_QUARTETS_ON_DEVICE), or NULL with ERI_ALL / ERI_UNIQUE8
+ *   opts        NULL for defaults (ERI_FP64, ERI_EXPLICIT, device 0, no flags, no screening)
  *   out         receives the plan; untouched on error
- * Synchronous.  Errors: ERI_E_INVALID (bad shell, id out of range), ERI_E_NOMEM, ERI_E_CUDA. */
+ * With a Schwarz threshold the plan first computes the FP64 diagonal ERIs (ij|ij) of all
+ * n_shells (n_shells + 1) / 2 pairs (temporary device memory of at most 256 MiB for them, plus
+ * the pair-table rule above) and drops the quartets below the threshold before classifying.
+ * At most 2^31 - 2 quartets per plan (after screening and sharding).
+ * For tests of the error paths, the environment variable ERI_INJECT_NOMEM=k (k >= 1) makes the
+ * k-th allocation of each call fail as if memory were exhausted (the host plan object is the
+ * first, then the device buffers in program order; the internal plan of diagonal quartets used
+ * for screening counts its own allocations the same way): the call then returns ERI_E_NOMEM,
+ * frees what it had allocated and leaves *out untouched.
+ * Synchronous.  Errors: ERI_E_INVALID (bad shell, id out of range, unknown mode or flag, negative
+ * or non-finite threshold, shard_index outside 0..shard_count-1, sharding outside
+ * ERI_UNIQUE8), ERI_E_UNSUPPORTED (too many quartets or pairs), ERI_E_NOMEM, ERI_E_CUDA. */
 eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const int32_t *quartets,
                              int64_t n_quartets, const eri_plan_opts_t *opts, eri_plan_t *out);
 
@@ -144,6 +173,13 @@ eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *pre
  * ERI_E_INVALID for a NULL plan or output, or cls outside 0..255. */
 eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches);
 
+/* Names of the kernel instantiation(s) eri_compute_compressed_class launches for class cls in
+ * its current precision (for reports that group time by kernel, e.g. "eri_setup_kernel<Cfg<2, 1,
+ * 1, 0, float>> + eri_class_kernel<Cfg<2, 1, 1, 0, float>, 0, 1>"), NUL-terminated into buf of
+ * len bytes.  Host only; ERI_E_INVALID for a NULL plan or buffer, cls outside 0..255 or a buffer
+ * too short. */
+eri_status_t eri_plan_class_kernels(eri_plan_t plan, int32_t cls, char *buf, size_t len);
+
 /* Total quartets in the plan.  ERI_E_INVALID if either argument is NULL. */
 eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);
 
@@ -158,10 +194,23 @@ eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quarte
                                  int64_t *fp64_offset);
 
 /* perm_out[i] = caller's index of the quartet at class-sorted position i (host array of
- * eri_plan_num_quartets entries).  For ERI_ALL, index = ((i*n + j)*n + k)*n + l.
+ * eri_plan_num_quartets entries).  For ERI_ALL, index = ((i*n + j)*n + k)*n + l; for ERI_UNIQUE8,
+ * the quartet's position among the plan's quartets in enumeration order (after screening and
+ * sharding).  A screened ERI_EXPLICIT / ERI_ALL plan keeps the index into the unscreened list.
  * Synchronous (reads the plan's device permutation); ERI_E_INVALID for a NULL plan, or a NULL
  * perm_out when the plan has quartets; ERI_E_CUDA if the copy fails. */
 eri_status_t eri_plan_quartet_order(eri_plan_t plan, int64_t *perm_out);
+
+/* The plan's quartets (n_quartets x 4 shell ids, host array) in class-sorted order, i.e. the
+ * order of every output; the shell order within each quartet is the one the outputs use (for
+ * ERI_UNIQUE8 the enumeration's).  Synchronous.  ERI_E_INVALID for a NULL plan, or a NULL
+ * quartets_out when the plan has quartets. */
+eri_status_t eri_plan_quartets(eri_plan_t plan, int32_t *quartets_out);
+
+/* Quartets before Schwarz screening (for ERI_UNIQUE8: n_pairs (n_pairs + 1) / 2) and quartets
+ * that pass it, before sharding (without a threshold the two are equal).  Either output may be
+ * NULL.  Host only; ERI_E_INVALID for a NULL plan. */
+eri_status_t eri_plan_screening(eri_plan_t plan, int64_t *candidates, int64_t *kept);
 
 /* Sizes of the outputs of eri_compute_compressed for a bitwidth (bits = 0: eri_compute's FP64
  * output).  packed_bytes covers all classes; scales_bytes = 4 * n_quartets.  Host only;
@@ -282,6 +331,47 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
                           void *stream);
 
+/* ---- consumer side: decompression fused with Coulomb/exchange digestion ---- */
+
+/* Flags of eri_digest_jk. */
+enum {
+    ERI_DIGEST_UNIQUE8 = 1,    /* each quartet stands for its 8-fold symmetric images (Sec. II-B) */
+    ERI_DIGEST_ACCUMULATE = 2  /* add to d_J / d_K instead of overwriting them */
+};
+
+/* Basis functions of the plan: shells in the order given to eri_plan_create, each contributing
+ * its (L+1)(L+2)/2 Cartesian components in the order stated at the top of this header, so
+ * function index = (sum of the sizes of the earlier shells) + component.  ERI_E_INVALID if
+ * either argument is NULL. */
+eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf);
+
+/* Coulomb and exchange matrices from the compressed ERIs of the plan, the use for which Sec. I
+ * and Sec. II-D store them: each ERI is decompressed as q * eps (Eq. 11) and contracted with the
+ * density matrix,
+ *     J[mu][nu]  += (mu nu | lam sig) D[lam][sig],      K[mu][lam] += (mu nu | lam sig) D[nu][sig],
+ * summed over the plan's quartets.  With ERI_DIGEST_UNIQUE8 every quartet (i j | k l) also
+ * contributes through the seven other index permutations under which a real ERI is invariant
+ * ((ji|kl), (ij|lk), (ji|lk), (kl|ij), (lk|ij), (kl|ji), (lk|ji); Sec. II-B), each distinct
+ * ordered shell quartet once (permutations that map the quartet onto itself, e.g. when i = j,
+ * are not repeated), so a plan of the unique quartets (i >= j, k >= l, pair ij >= pair kl)
+ * yields the J and K of the full ERI tensor.  Without it each quartet counts once as listed.
+ *   bits       2..24, the width d_packed / d_scales were written with
+ *   d_packed   output of eri_compute_compressed (or _batched / _to_host's device staging) for
+ *              this plan and bits, layout of eri_packed_class_offset
+ *   d_scales   one eps per quartet, class-sorted
+ *   d_D        n_bf x n_bf FP64, row major (D[lam][sig] at lam * n_bf + sig); need not be
+ *              symmetric
+ *   d_J, d_K   n_bf x n_bf FP64, row major; overwritten unless ERI_DIGEST_ACCUMULATE
+ * Arithmetic: codes times D in FP32 (D is rounded to FP32 once per call; codes up to 24 bits
+ * are exact), the sums over the two contracted indices of a quartet in FP32, scaled by eps and
+ * added to J and K in FP64 with device atomics (the order of the FP64 additions, hence the last
+ * bits, can vary between runs).  The plan keeps an n_bf x n_bf FP32 buffer for the rounded D
+ * (allocated on the first call).  Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits
+ * outside 2..24, unknown flags, NULL buffers where the plan needs them, or buffers not aligned
+ * to their element size; ERI_E_NOMEM / ERI_E_CUDA from allocation or launch failures. */
+eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, const float *d_scales,
+                           const double *d_D, double *d_J, double *d_K, int32_t flags, void *stream);
+
 /* ---- no-allocation entry point (no counterpart in the paper) ---- */
 
 /* Largest n_quartets eri_compute_class_noalloc accepts. */
@@ -320,7 +410,7 @@ eri_status_t eri_compute_class_noalloc(int32_t cls, int32_t precision, const dou
                                        double *d_out, int32_t *d_err, void *stream);
 
 /* Waits for the plan's work on `stream` and returns the first latched device error
- * (ERI_E_NUMERIC, ERI_E_TIMEOUT) or a CUDA error; clears the latch. */
+ * (ERI_E_NUMERIC) or a CUDA error; clears the latch. */
 eri_status_t eri_sync(eri_plan_t plan, void *stream);
 
 /* Human-readable name of a status. */
@@ -344,6 +434,14 @@ eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double
  * d_back[i] = (double)d_f[i].  Asynchronous on `stream`. */
 eri_status_t eri_convert_device(const double *d_in, int64_t n, float *d_f, double *d_back,
                                 void *stream);
+
+/* Fused multiply-add throughput probe (no counterpart in the paper): n_threads threads (a
+ * multiple of 256) each run 8 independent chains of 16 * iters FMAs in FP64 (ERI_FP64) or FP32
+ * (ERI_MIXED) and store one value each to d_sink (n_threads doubles or floats), so a timed launch
+ * does 256 * iters * n_threads floating-point operations: the measured ALU peak the roofline of
+ * the FP-bound kernels is quoted against.  Asynchronous on `stream`; ERI_E_INVALID for other
+ * arguments. */
+eri_status_t eri_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, void *d_sink, void *stream);
 
 /* Class helpers (no device needed). */
 int32_t eri_class_id(int32_t La, int32_t Lb, int32_t Lc, int32_t Ld);

@@ -17,20 +17,22 @@ ERI_E_INVALID = 1
 ERI_E_UNSUPPORTED = 2
 ERI_E_NOMEM = 3
 ERI_E_CUDA = 4
-ERI_E_TIMEOUT = 5
 ERI_E_NUMERIC = 6
 
 ERI_FP64 = 0
 ERI_MIXED = 1
 ERI_EXPLICIT = 0
 ERI_ALL = 1
+ERI_UNIQUE8 = 2
 ERI_QUARTETS_ON_DEVICE = 1
 ERI_NO_PAIR_TABLE = 2
 ERI_NOALLOC_MAX_QUARTETS = 16384
+ERI_DIGEST_UNIQUE8 = 1
+ERI_DIGEST_ACCUMULATE = 2
 
 STATUS_NAMES = {
     ERI_OK: "ERI_OK", ERI_E_INVALID: "ERI_E_INVALID", ERI_E_UNSUPPORTED: "ERI_E_UNSUPPORTED",
-    ERI_E_NOMEM: "ERI_E_NOMEM", ERI_E_CUDA: "ERI_E_CUDA", ERI_E_TIMEOUT: "ERI_E_TIMEOUT",
+    ERI_E_NOMEM: "ERI_E_NOMEM", ERI_E_CUDA: "ERI_E_CUDA",
     ERI_E_NUMERIC: "ERI_E_NUMERIC",
 }
 
@@ -50,7 +52,9 @@ class eri_shell_t(ctypes.Structure):
 
 class eri_plan_opts_t(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("quartet_mode", ctypes.c_int32),
-                ("device", ctypes.c_int32), ("flags", ctypes.c_int32)]
+                ("device", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("schwarz_threshold", ctypes.c_double), ("shard_index", ctypes.c_int64),
+                ("shard_count", ctypes.c_int64)]
 
 
 SIGNATURES = {
@@ -62,9 +66,13 @@ SIGNATURES = {
     "eri_plan_calibrate_precision": (_i32, [_p, _i32, _i64, ctypes.c_float, _p]),
     "eri_plan_class_precision": (_i32, [_p, _i32, _i32p, ctypes.POINTER(ctypes.c_float)]),
     "eri_plan_class_launches": (_i32, [_p, _i32, _i32p]),
+    "eri_plan_class_kernels": (_i32, [_p, _i32, ctypes.c_char_p, ctypes.c_size_t]),
+    "eri_fma_probe": (_i32, [_i32, _i64, _i32, _p, _p]),
     "eri_plan_num_quartets": (_i32, [_p, _i64p]),
     "eri_plan_class_info": (_i32, [_p, _i32, _i64p, _i32p, _i64p, _i64p]),
     "eri_plan_quartet_order": (_i32, [_p, _i64p]),
+    "eri_plan_quartets": (_i32, [_p, _p]),
+    "eri_plan_screening": (_i32, [_p, _i64p, _i64p]),
     "eri_output_bytes": (_i32, [_p, _i32, _szp, _szp]),
     "eri_packed_class_offset": (_i32, [_p, _i32, _i32, _szp, _szp]),
     "eri_paper512_class_offset": (_i32, [_p, _i32, _i32, _szp, _szp]),
@@ -80,6 +88,8 @@ SIGNATURES = {
     "eri_compute_compressed_batched": (_i32, [_p, _i32, _p, _p, _p]),
     "eri_autotune": (_i32, [_p, _i32, _p, _p, ctypes.c_char_p, _p]),
     "eri_status_string": (ctypes.c_char_p, [_i32]),
+    "eri_plan_num_basis_functions": (_i32, [_p, _i64p]),
+    "eri_digest_jk": (_i32, [_p, _i32, _p, _p, _p, _p, _p, _i32, _p]),
     "eri_compute_class_noalloc": (_i32, [_i32, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _i64, _p, _p, _p]),
     "eri_boys_device": (_i32, [_i32, _p, _i64, _p, _p]),
     "eri_rys_device": (_i32, [_i32, _p, _i64, _p, _p, _p]),

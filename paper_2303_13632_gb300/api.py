@@ -9,8 +9,8 @@ import ctypes
 import numpy as np
 
 from . import _lib
-from ._lib import (ERI_ALL, ERI_EXPLICIT, ERI_FP64, ERI_MIXED, ERI_QUARTETS_ON_DEVICE, EriError,  # noqa: F401
-                   check)
+from ._lib import (ERI_ALL, ERI_EXPLICIT, ERI_FP64, ERI_MIXED, ERI_QUARTETS_ON_DEVICE, ERI_UNIQUE8,  # noqa: F401
+                   EriError, check)
 
 PRECISIONS = {"fp64": ERI_FP64, "mixed": ERI_MIXED}
 
@@ -51,11 +51,15 @@ class Plan:
             pass
 
 
+MODES = {"explicit": ERI_EXPLICIT, "all": ERI_ALL, "unique8": ERI_UNIQUE8}
+
+
 def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = "explicit",
-                    device: int = 0, pair_table: bool = True) -> Plan:
+                    device: int = 0, pair_table: bool = True, schwarz_threshold: float = 0.0,
+                    shard: tuple[int, int] = (0, 0)) -> Plan:
     """shells: a ShellSet (workloads.py); quartets: [n, 4] int32 numpy array (host), a
-    contiguous int32 CUDA tensor (device), or None with mode="all"; pair_table=False sets
-    ERI_NO_PAIR_TABLE."""
+    contiguous int32 CUDA tensor (device), or None with mode="all" / "unique8"; pair_table=False
+    sets ERI_NO_PAIR_TABLE; shard = (shard_index, shard_count) of a unique8 enumeration."""
     lib = _lib.load()
     n = len(shells.L)
     arr = (_lib.eri_shell_t * max(n, 1))()
@@ -72,8 +76,9 @@ def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = 
         off = int(shells.pofs[s]) * 8
         sh.exps = ctypes.cast(base_e + off, _lib.c_double_p)
         sh.coefs = ctypes.cast(base_c + off, _lib.c_double_p)
-    opts = _lib.eri_plan_opts_t(PRECISIONS[precision], ERI_ALL if mode == "all" else ERI_EXPLICIT,
-                                device, 0 if pair_table else _lib.ERI_NO_PAIR_TABLE)
+    opts = _lib.eri_plan_opts_t(PRECISIONS[precision], MODES[mode], device,
+                                0 if pair_table else _lib.ERI_NO_PAIR_TABLE, float(schwarz_threshold),
+                                int(shard[0]), int(shard[1]))
     if quartets is None:
         qptr, nq = ctypes.c_void_p(0), 0
     elif isinstance(quartets, np.ndarray):
@@ -126,6 +131,18 @@ def eri_plan_class_launches(plan: Plan, cls: int) -> int:
     return int(n.value)
 
 
+def eri_plan_class_kernels(plan: Plan, cls: int) -> str:
+    buf = ctypes.create_string_buffer(256)
+    check(_lib.load().eri_plan_class_kernels(plan.handle, cls, buf, 256), "eri_plan_class_kernels")
+    return buf.value.decode()
+
+
+def eri_fma_probe(precision: str, n_threads: int, iters: int, sink, stream=None) -> None:
+    """Launches the FMA throughput probe: 256 * iters * n_threads flops (see include/eri.h)."""
+    check(_lib.load().eri_fma_probe(PRECISIONS[precision], n_threads, iters, _dev_ptr(sink),
+                                    _stream_handle(stream)), "eri_fma_probe")
+
+
 def eri_plan_num_quartets(plan: Plan) -> int:
     n = ctypes.c_int64()
     check(_lib.load().eri_plan_num_quartets(plan.handle, ctypes.byref(n)), "eri_plan_num_quartets")
@@ -146,6 +163,21 @@ def eri_plan_quartet_order(plan: Plan) -> np.ndarray:
     check(_lib.load().eri_plan_quartet_order(plan.handle, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))),
           "eri_plan_quartet_order")
     return out
+
+
+def eri_plan_quartets(plan: Plan) -> np.ndarray:
+    """The plan's quartets [n, 4] (int32) in class-sorted order (the order of every output)."""
+    n = eri_plan_num_quartets(plan)
+    out = np.zeros((n, 4), dtype=np.int32)
+    check(_lib.load().eri_plan_quartets(plan.handle, ctypes.c_void_p(out.ctypes.data)), "eri_plan_quartets")
+    return out
+
+
+def eri_plan_screening(plan: Plan):
+    """(quartets before Schwarz screening, quartets kept before sharding)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    check(_lib.load().eri_plan_screening(plan.handle, ctypes.byref(a), ctypes.byref(b)), "eri_plan_screening")
+    return a.value, b.value
 
 
 def eri_output_bytes(plan: Plan, bits: int):
@@ -237,6 +269,22 @@ def eri_compute_class_noalloc(cls: int, precision: str, cx, cy, cz, pofs, nprim,
         cls, PRECISIONS[precision], _dev_ptr(cx), _dev_ptr(cy), _dev_ptr(cz), _dev_ptr(pofs),
         _dev_ptr(nprim), _dev_ptr(exps), _dev_ptr(cn), _dev_ptr(quartets), n, _dev_ptr(out),
         _dev_ptr(err), _stream_handle(stream)), "eri_compute_class_noalloc")
+
+
+def eri_plan_num_basis_functions(plan: Plan) -> int:
+    n = ctypes.c_int64()
+    check(_lib.load().eri_plan_num_basis_functions(plan.handle, ctypes.byref(n)),
+          "eri_plan_num_basis_functions")
+    return n.value
+
+
+def eri_digest_jk(plan: Plan, bits: int, packed, scales, D, J, K, unique8: bool = False,
+                  accumulate: bool = False, stream=None) -> None:
+    """J and K (n_bf x n_bf float64 CUDA tensors) from the compressed ERIs and the density D."""
+    flags = (_lib.ERI_DIGEST_UNIQUE8 if unique8 else 0) | (_lib.ERI_DIGEST_ACCUMULATE if accumulate else 0)
+    check(_lib.load().eri_digest_jk(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales), _dev_ptr(D),
+                                    _dev_ptr(J), _dev_ptr(K), flags, _stream_handle(stream)),
+          "eri_digest_jk")
 
 
 def eri_sync(plan: Plan, stream=None) -> None:

@@ -49,7 +49,9 @@ def _sources_digest() -> str:
 def _units():
     units = [("eri_tables", "eri_tables.cu", []), ("eri_plan", "eri_plan.cu", []),
              ("eri_backward", "eri_backward.cu", []), ("eri_noalloc", "eri_noalloc.cu", []),
-             ("eri_layout", "eri_layout.cu", [])]
+             ("eri_layout", "eri_layout.cu", []),
+             ("eri_digest", "eri_digest.cu", []),
+             ("eri_screen", "eri_screen.cu", [])]
     for k in range(NUM_TU):
         units.append((f"eri_classes_{k}", "eri_classes.cu", [f"-DERI_TU={k}"]))
     return units

@@ -1,0 +1,250 @@
+// eri_digest.cu -- consumer side of the compressed ERIs: decompression (Sec. II-D, Eq. 11)
+// fused with their contraction against a density matrix into the Coulomb and exchange
+// matrices,
+//   J[mu, nu]  += (mu nu | lam sig) D[lam, sig],     K[mu, lam] += (mu nu | lam sig) D[nu, sig],
+// the use Sec. I and Sec. II-D give for computing and storing ERIs compressed (the matrices
+// an SCF or AIMD step rebuilds from the stored integrals).
+//
+// A quartet's block e[a][b][c][d] (codes q times the quartet's eps) contributes through each of
+// the eight index permutations of Sec. II-B that give a distinct ordered shell quartet
+// (permutations that map the quartet onto itself are counted once).  For the eight
+// permutations the twelve contractions needed fall into six "index-pair passes": a pass fixes
+// two positions (x, y) of the block and sums over the other two (u, w) against the D block
+// D[u, w] and its transpose D[w, u]:
+//   pass (a,b): T1 = sum e D[c,d] -> J[a,b] (perm 1), J[b,a] (perm 2);
+//               T2 = sum e D[d,c] -> J[a,b] (perm 3), J[b,a] (perm 4)
+//   pass (c,d): T3 = sum e D[a,b] -> J[c,d] (5), J[d,c] (6); T4 = sum e D[b,a] -> J[c,d] (7), J[d,c] (8)
+//   pass (a,c): sum e D[b,d] -> K[a,c] (1);  sum e D[d,b] -> K[c,a] (5)
+//   pass (b,c): sum e D[a,d] -> K[b,c] (2);  sum e D[d,a] -> K[c,b] (7)
+//   pass (a,d): sum e D[b,c] -> K[a,d] (3);  sum e D[c,b] -> K[d,a] (6)
+//   pass (b,d): sum e D[a,c] -> K[b,d] (4);  sum e D[c,a] -> K[d,b] (8)
+// with the permutations 1..8 = (abcd), (bacd), (abdc), (badc), (cdab), (dcab), (cdba), (dcba).
+//
+// GPU mapping: one CTA per tile of quartets of one class.  The tile's codes are decoded into
+// shared memory as FP32 integers (exact for widths <= 24), the twelve D blocks between the
+// quartet's four shells are staged in FP32, and each thread takes (quartet, pass, x, y) items,
+// forms both sums in FP32, scales them by eps and adds them to J and K in FP64 (device
+// atomics, so the summation order of the FP64 accumulation varies between runs).
+#include "eri_internal.h"
+
+namespace eri {
+
+namespace {
+
+constexpr int kDigestThreads = 256;
+constexpr int kDigestSmem = 48 * 1024;
+
+// pass p fixes positions (PX, PY) and sums over (PU, PW)
+__constant__ int c_px[6] = {0, 2, 0, 1, 0, 1};
+__constant__ int c_py[6] = {1, 3, 2, 2, 3, 3};
+__constant__ int c_pu[6] = {2, 0, 1, 0, 1, 0};
+__constant__ int c_pw[6] = {3, 1, 3, 3, 2, 2};
+
+struct DigestArgs {
+    const int4 *quartets;  // class-sorted shell ids of the class
+    long long nq;
+    const uint32_t *packed;  // class segment of the packed stream
+    const float *scales;     // eps of the class's quartets
+    const int *bfoff;        // first basis function of every shell
+    const float *D;          // density matrix, FP32, row major
+    long long nbf;
+    double *J, *K;
+    int bits;
+    int unique8;
+    int n[4];      // Cartesian components of the four positions
+    int st[4];     // strides of the four positions in the quartet's block
+    int neri;
+    int T;         // quartets per tile
+    int nD;        // staged D values per quartet
+    int boff[16];  // offset of D block (x, y) (index x*4 + y) in a quartet's D area
+    int NI;        // items per quartet
+    int ioff[7];   // first item of each pass
+};
+
+// Which of the eight permutations give a distinct ordered shell quartet (bit p-1 for
+// permutation p): a permutation equal, as a tuple of shell ids, to an earlier one is dropped.
+__device__ __forceinline__ int perm_mask(int4 s, bool unique8) {
+    if (!unique8) return 1;
+    const int t[8][4] = {{s.x, s.y, s.z, s.w}, {s.y, s.x, s.z, s.w}, {s.x, s.y, s.w, s.z},
+                         {s.y, s.x, s.w, s.z}, {s.z, s.w, s.x, s.y}, {s.w, s.z, s.x, s.y},
+                         {s.z, s.w, s.y, s.x}, {s.w, s.z, s.y, s.x}};
+    int mask = 0;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        bool fresh = true;
+#pragma unroll
+        for (int r = 0; r < p; ++r)
+            fresh &= !(t[p][0] == t[r][0] && t[p][1] == t[r][1] && t[p][2] == t[r][2] &&
+                       t[p][3] == t[r][3]);
+        mask |= fresh ? (1 << p) : 0;
+    }
+    return mask;
+}
+
+// Coefficients (0 or 1) of the two sums of pass p in its two destinations:
+// dest 1 = M[x, y] gets c[0] S + c[1] S', dest 2 = M[y, x] gets c[2] S + c[3] S'.
+__device__ __forceinline__ void pass_coefs(int p, int m, int c[4]) {
+    auto b = [m](int perm) { return (m >> (perm - 1)) & 1; };
+    switch (p) {
+        case 0: c[0] = b(1); c[1] = b(3); c[2] = b(2); c[3] = b(4); break;
+        case 1: c[0] = b(5); c[1] = b(7); c[2] = b(6); c[3] = b(8); break;
+        case 2: c[0] = b(1); c[1] = 0; c[2] = 0; c[3] = b(5); break;
+        case 3: c[0] = b(2); c[1] = 0; c[2] = 0; c[3] = b(7); break;
+        case 4: c[0] = b(3); c[1] = 0; c[2] = 0; c[3] = b(6); break;
+        default: c[0] = b(4); c[1] = 0; c[2] = 0; c[3] = b(8); break;
+    }
+}
+
+__global__ void __launch_bounds__(kDigestThreads) digest_kernel(DigestArgs A) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    int *meta = reinterpret_cast<int *>(smem);               // T x 8: bf offsets, mask, eps
+    float *e_s = reinterpret_cast<float *>(meta + A.T * 8);  // T x neri codes
+    float *d_s = e_s + (size_t)A.T * A.neri;                 // T x nD D values
+    const long long q0 = (long long)blockIdx.x * A.T;
+    const int tn = (int)((A.nq - q0) < A.T ? (A.nq - q0) : A.T);
+    const int tid = threadIdx.x;
+
+    for (int t = tid; t < tn; t += kDigestThreads) {
+        const int4 s = A.quartets[q0 + t];
+        int *m = meta + t * 8;
+        m[0] = A.bfoff[s.x];
+        m[1] = A.bfoff[s.y];
+        m[2] = A.bfoff[s.z];
+        m[3] = A.bfoff[s.w];
+        m[4] = perm_mask(s, A.unique8 != 0);
+        m[5] = __float_as_int(A.scales[q0 + t]);
+    }
+    // codes of the tile: fields q0*neri .. (q0+tn)*neri of the class's stream (Eq. 11 without
+    // the scale, which is applied once per sum)
+    const int nv = tn * A.neri;
+    const long long f0 = q0 * A.neri;
+    const uint32_t fmask = (1u << A.bits) - 1u;
+    for (int v = tid; v < nv; v += kDigestThreads) {
+        const unsigned long long bit = (unsigned long long)(f0 + v) * (unsigned)A.bits;
+        const long long w = (long long)(bit >> 5);
+        const int off = (int)(bit & 31);
+        uint32_t raw = __ldg(A.packed + w) >> off;
+        if (off + A.bits > 32) raw |= __ldg(A.packed + w + 1) << (32 - off);
+        raw &= fmask;
+        const int code = (int)(raw << (32 - A.bits)) >> (32 - A.bits);  // sign extension
+        e_s[v] = (float)code;
+    }
+    __syncthreads();
+    // the D blocks between the quartet's shells, D[o_x + i][o_y + j] for x != y
+    for (int idx = tid; idx < tn * A.nD; idx += kDigestThreads) {
+        const int t = idx / A.nD;
+        const int r = idx - t * A.nD;
+        int x = 0, y = 1;
+#pragma unroll 1
+        for (int b = 0; b < 16; ++b) {
+            const int bx = b >> 2, by = b & 3;
+            if (bx == by) continue;
+            if (r >= A.boff[b] && r < A.boff[b] + A.n[bx] * A.n[by]) {
+                x = bx;
+                y = by;
+            }
+        }
+        const int loc = r - A.boff[x * 4 + y];
+        const int i = loc / A.n[y], j = loc - (loc / A.n[y]) * A.n[y];
+        const int *m = meta + t * 8;
+        d_s[idx] = __ldg(A.D + (long long)(m[x] + i) * A.nbf + (m[y] + j));
+    }
+    __syncthreads();
+    for (int it = tid; it < tn * A.NI; it += kDigestThreads) {
+        const int t = it / A.NI;
+        const int r = it - t * A.NI;
+        int p = 0;
+#pragma unroll
+        for (int k = 1; k < 6; ++k) p += r >= A.ioff[k];
+        const int *m = meta + t * 8;
+        int c[4];
+        pass_coefs(p, m[4], c);
+        if ((c[0] | c[1] | c[2] | c[3]) == 0) continue;
+        const int x = c_px[p], y = c_py[p], u = c_pu[p], w = c_pw[p];
+        const int loc = r - A.ioff[p];
+        const int ix = loc / A.n[y], iy = loc - (loc / A.n[y]) * A.n[y];
+        const int nu = A.n[u], nw = A.n[w], su = A.st[u], sw = A.st[w];
+        const float *ep = e_s + t * A.neri + ix * A.st[x] + iy * A.st[y];
+        const float *d1 = d_s + t * A.nD + A.boff[u * 4 + w];  // D[u][w], row length nw
+        const float *d2 = d_s + t * A.nD + A.boff[w * 4 + u];  // D[w][u], row length nu
+        float S = 0.0f, S2 = 0.0f;
+#pragma unroll 1
+        for (int iu = 0; iu < nu; ++iu)
+#pragma unroll 2
+            for (int iw = 0; iw < nw; ++iw) {
+                const float e = ep[iu * su + iw * sw];
+                S = fmaf(e, d1[iu * nw + iw], S);
+                S2 = fmaf(e, d2[iw * nu + iu], S2);
+            }
+        const float eps = __int_as_float(m[5]);
+        double *M = p < 2 ? A.J : A.K;
+        const long long row = m[x] + ix, col = m[y] + iy;
+        const float v1 = (c[0] ? S : 0.0f) + (c[1] ? S2 : 0.0f);
+        const float v2 = (c[2] ? S : 0.0f) + (c[3] ? S2 : 0.0f);
+        if (c[0] | c[1]) atomicAdd(M + row * A.nbf + col, f32_to_f64(v1 * eps));
+        if (c[2] | c[3]) atomicAdd(M + col * A.nbf + row, f32_to_f64(v2 * eps));
+    }
+}
+
+__global__ void density_to_f32_kernel(const double *__restrict__ D, long long n, float *__restrict__ out) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        out[i] = f64_to_f32(D[i]);
+}
+
+int ncart_d(int L) { return (L + 1) * (L + 2) / 2; }
+
+}  // namespace
+
+cudaError_t digest_density_f32(const double *D, long long n, float *out, cudaStream_t stream) {
+    if (n <= 0) return cudaSuccess;
+    long long blocks = (n + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    density_to_f32_kernel<<<(unsigned)blocks, 256, 0, stream>>>(D, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int *bfoff,
+                         const float *D32, long long nbf, double *J, double *K, cudaStream_t stream) {
+    if (c.nq <= 0) return cudaSuccess;
+    DigestArgs A{};
+    A.quartets = c.quartets;
+    A.nq = c.nq;
+    A.packed = c.packed;
+    A.scales = c.scales;
+    A.bfoff = bfoff;
+    A.D = D32;
+    A.nbf = nbf;
+    A.J = J;
+    A.K = K;
+    A.bits = bits;
+    A.unique8 = unique8 ? 1 : 0;
+    const int L[4] = {(c.cls >> 6) & 3, (c.cls >> 4) & 3, (c.cls >> 2) & 3, c.cls & 3};
+    for (int x = 0; x < 4; ++x) A.n[x] = ncart_d(L[x]);
+    A.st[3] = 1;
+    for (int x = 2; x >= 0; --x) A.st[x] = A.st[x + 1] * A.n[x + 1];
+    A.neri = A.st[0] * A.n[0];
+    int o = 0;
+    for (int b = 0; b < 16; ++b) {
+        const int x = b >> 2, y = b & 3;
+        A.boff[b] = o;
+        if (x != y) o += A.n[x] * A.n[y];
+    }
+    A.nD = o;
+    const int px[6] = {0, 2, 0, 1, 0, 1}, py[6] = {1, 3, 2, 2, 3, 3};
+    A.ioff[0] = 0;
+    for (int p = 0; p < 6; ++p) A.ioff[p + 1] = A.ioff[p] + A.n[px[p]] * A.n[py[p]];
+    A.NI = A.ioff[6];
+    const int perq = 4 * (8 + A.neri + A.nD);
+    int T = kDigestSmem / perq;
+    T = T < 1 ? 1 : (T > 128 ? 128 : T);
+    A.T = T;
+    const size_t smem = (size_t)T * perq;
+    if (smem > (size_t)kDigestSmem) return cudaErrorInvalidValue;
+    const long long tiles = (c.nq + T - 1) / T;
+    if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    digest_kernel<<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
+    return cudaGetLastError();
+}
+
+}  // namespace eri

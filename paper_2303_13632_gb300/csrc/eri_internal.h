@@ -38,6 +38,39 @@ struct KernelInfo {
     bool setup;  // primitive (K = 1) plans run it through the setup kernel: the caller passes
                  // LaunchOpts::scratch and at most kSetupChunk quartets per launch
 };
+// One class of a plan's compressed output, as the Coulomb/exchange digestion reads it.
+struct DigestClass {
+    int cls;               // generic class id
+    const int4 *quartets;  // class-sorted shell ids (the caller's orientation)
+    long long nq;
+    const uint32_t *packed;  // first word of the class segment
+    const float *scales;     // eps of the class's first quartet
+};
+// D (FP64, n values) rounded to FP32 into out.
+cudaError_t digest_density_f32(const double *D, long long n, float *out, cudaStream_t stream);
+// Adds the class's contributions to J and K (see eri_digest.cu).
+cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int *bfoff,
+                         const float *D32, long long nbf, double *J, double *K, cudaStream_t stream);
+
+// Device quartet lists (eri_screen.cu).  Diagonal quartets (i j | i j) of every unordered pair
+// P = i (i + 1) / 2 + j, i >= j.
+cudaError_t screen_diag_quartets(long long npairs, int4 *out, cudaStream_t s);
+// out[q] = sqrt(max_v |x[q * neri + v]|) for n quartets.
+cudaError_t screen_absmax_sqrt(const double *x, long long n, int neri, double *out, cudaStream_t s);
+// out[idx[i]] = v[i].
+cudaError_t screen_scatter(const double *v, const int *idx, long long n, double *out, cudaStream_t s);
+// The 8-fold unique quartets of the pairs with factors d_Q (see eri_screen.cu), screened at tau
+// (tau = 0: none), shard sidx of scount; allocates *d_out (n_out quartets); *total = the count
+// before sharding; cudaErrorNotSupported if more than max_out quartets would be kept.
+// Synchronous on s.
+cudaError_t screen_unique8(const double *d_Q, long long npairs, double tau, long long sidx,
+                           long long scount, int4 **d_out, long long *n_out, long long *total,
+                           long long max_out, cudaStream_t s);
+// Keeps the quartets of d_in with Q_ij Q_kl >= tau, in order; allocates *d_out and *d_idx (the
+// input index of every kept quartet).  Synchronous on s.
+cudaError_t screen_filter(const int4 *d_in, long long n, const double *d_Q, double tau, int4 **d_out,
+                          int **d_idx, long long *n_out, cudaStream_t s);
+
 #define ERI_DECLARE_REGISTER(K) void eri_register_tu_##K(LaunchFn *table, KernelInfo *info);
 ERI_DECLARE_REGISTER(0) ERI_DECLARE_REGISTER(1) ERI_DECLARE_REGISTER(2) ERI_DECLARE_REGISTER(3)
 ERI_DECLARE_REGISTER(4) ERI_DECLARE_REGISTER(5) ERI_DECLARE_REGISTER(6) ERI_DECLARE_REGISTER(7)

@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 #include <new>
@@ -108,6 +109,20 @@ __global__ void gather_kernel(const int4 *__restrict__ src, const int *__restric
     if (i < n) dst[i] = src[idx[i]];
 }
 
+__global__ void check_ids_kernel(const int4 *__restrict__ q, long long n, int n_shells, int *__restrict__ err) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int4 t = q[i];
+    if (t.x < 0 || t.x >= n_shells || t.y < 0 || t.y >= n_shells || t.z < 0 || t.z >= n_shells ||
+        t.w < 0 || t.w >= n_shells)
+        atomicOr(err, 4);
+}
+
+__global__ void compose_kernel(int *__restrict__ perm, const int *__restrict__ orig, long long n) {
+    long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) perm[i] = orig[perm[i]];
+}
+
 __global__ void histogram_kernel(const uint8_t *__restrict__ keys, long long n,
                                  unsigned long long *__restrict__ counts) {
     __shared__ unsigned int h[256];
@@ -180,6 +195,8 @@ struct eri_plan_s {
     int n_shells = 0;
     long long n_prims = 0;
     long long nq = 0;
+    long long screen_candidates = 0;  // quartets before Schwarz screening (and sharding)
+    long long screen_kept = 0;        // quartets passing the screening, before sharding
     int max_nprim = 1;
     // device arrays
     double *d_cx = nullptr, *d_cy = nullptr, *d_cz = nullptr, *d_exps = nullptr, *d_cn = nullptr;
@@ -187,6 +204,9 @@ struct eri_plan_s {
     int4 *d_quartets = nullptr;  // class-sorted
     int *d_perm = nullptr;       // sorted position -> caller's index
     int *d_err = nullptr;
+    int *d_bfoff = nullptr;      // first basis function of every shell
+    long long n_bf = 0;          // basis functions (sum of the shells' Cartesian components)
+    float *d_D32 = nullptr;      // FP32 copy of the density of eri_digest_jk (lazy)
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
     double *d_pairs = nullptr;    // primitive-pair table (n_prims^2 records), or null
     // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
@@ -229,6 +249,8 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_quartets);
     cudaFree(p->d_perm);
     cudaFree(p->d_err);
+    cudaFree(p->d_bfoff);
+    cudaFree(p->d_D32);
     cudaFree(p->d_setup);
     cudaFree(p->d_pairs);
     cudaFree(p->d_counters);
@@ -251,9 +273,31 @@ eri_status_t cuda_status(cudaError_t e) {
     return ERI_E_CUDA;
 }
 
+// Allocation-failure injection for tests of the error paths (no GPU fault involved): with the
+// environment variable ERI_INJECT_NOMEM=k (k >= 1) the k-th allocation made by one
+// eri_plan_create call (the host plan object first, then its device buffers, in program order,
+// including those of the internal plan of diagonal quartets for screening) fails as if memory
+// were exhausted.  Read at the start of every eri_plan_create call; unset or 0 = off.
+thread_local long long g_inject_nomem = 0;
+
+cudaError_t plan_malloc(void **ptr, size_t bytes) {
+    if (g_inject_nomem > 0 && --g_inject_nomem == 0) {
+        *ptr = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc(ptr, bytes);
+}
+template <typename T>
+cudaError_t plan_malloc(T **ptr, size_t bytes) {
+    void *v = nullptr;
+    cudaError_t e = plan_malloc(&v, bytes);
+    *ptr = static_cast<T *>(v);
+    return e;
+}
+
 template <typename T>
 cudaError_t upload(T **dst, const std::vector<T> &src) {
-    cudaError_t e = cudaMalloc(dst, std::max<size_t>(1, src.size()) * sizeof(T));
+    cudaError_t e = plan_malloc(dst, std::max<size_t>(1, src.size()) * sizeof(T));
     if (e != cudaSuccess) return e;
     if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
     return e;
@@ -348,6 +392,63 @@ eri_status_t launch_class_args(eri_plan_s *p, int cls, const ClassArgs &a, int v
     return ERI_OK;
 }
 
+// Schwarz factors Q[P] = sqrt(max |(ij|ij)|) of every unordered shell pair P = i (i + 1) / 2 + j
+// (i >= j): FP64 ERIs of the diagonal quartets by the library's own kernels (a plan of those
+// quartets), computed class by class in chunks of a bounded buffer and reduced on the device.
+// *d_Q (npairs doubles) is allocated here.
+eri_status_t schwarz_factors(const eri_shell_t *shells, int n_shells, int device, int flags, double **d_Q) {
+    *d_Q = nullptr;
+    const long long npairs = (long long)n_shells * (n_shells + 1) / 2;
+    if (npairs == 0) return ERI_OK;
+    constexpr long long kChunkDoubles = 1LL << 25;  // 256 MiB of FP64 output per launch
+    int4 *d_diag = nullptr;
+    double *Qs = nullptr, *buf = nullptr;
+    eri_plan_t sp = nullptr;
+    cudaError_t e = plan_malloc(&d_diag, npairs * sizeof(int4));
+    if (e == cudaSuccess) e = screen_diag_quartets(npairs, d_diag, nullptr);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        cudaFree(d_diag);
+        return cuda_status(e);
+    }
+    eri_plan_opts_t so{ERI_FP64, ERI_EXPLICIT, device, ERI_QUARTETS_ON_DEVICE | flags, 0.0, 0, 0};
+    eri_status_t st = eri_plan_create(shells, n_shells, reinterpret_cast<const int32_t *>(d_diag), npairs, &so, &sp);
+    cudaFree(d_diag);
+    if (st != ERI_OK) return st;
+    long long maxv = 1;
+    for (int c = 0; c < 256; ++c)
+        if (sp->count[c] > 0) maxv = std::max(maxv, std::min(sp->count[c], std::max(1LL, kChunkDoubles / class_neri(c))) * class_neri(c));
+    e = plan_malloc(&Qs, npairs * sizeof(double));
+    if (e == cudaSuccess) e = plan_malloc(&buf, maxv * sizeof(double));
+    if (e == cudaSuccess) e = plan_malloc(d_Q, npairs * sizeof(double));
+    for (int c = 0; e == cudaSuccess && st == ERI_OK && c < 256; ++c) {
+        if (sp->count[c] == 0) continue;
+        const int neri = class_neri(c);
+        const long long chunk = std::max(1LL, kChunkDoubles / neri);
+        for (long long c0 = 0; c0 < sp->count[c] && st == ERI_OK; c0 += chunk) {
+            ClassArgs a = class_args(sp, c, buf, 0, nullptr, nullptr, 0);
+            a.quartets += c0;
+            a.nq = std::min(chunk, sp->count[c] - c0);
+            a.out_fp64 = buf;
+            st = launch_class_args(sp, c, a, 0, nullptr);
+            if (st == ERI_OK) e = screen_absmax_sqrt(buf, a.nq, neri, Qs + sp->first[c] + c0, nullptr);
+            if (e != cudaSuccess) st = cuda_status(e);
+        }
+    }
+    if (st == ERI_OK && e == cudaSuccess) e = screen_scatter(Qs, sp->d_perm, npairs, *d_Q, nullptr);
+    cudaError_t se = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = se;
+    if (st == ERI_OK && e != cudaSuccess) st = cuda_status(e);
+    cudaFree(Qs);
+    cudaFree(buf);
+    eri_plan_destroy(sp);
+    if (st != ERI_OK) {
+        cudaFree(*d_Q);
+        *d_Q = nullptr;
+    }
+    return st;
+}
+
 eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d_packed,
                         float *d_scales, size_t packed_off, cudaStream_t stream) {
     if (p->count[cls] == 0) return ERI_OK;
@@ -421,7 +522,6 @@ const char *eri_status_string(eri_status_t s) {
         case ERI_E_UNSUPPORTED: return "ERI_E_UNSUPPORTED";
         case ERI_E_NOMEM: return "ERI_E_NOMEM";
         case ERI_E_CUDA: return "ERI_E_CUDA";
-        case ERI_E_TIMEOUT: return "ERI_E_TIMEOUT";
         case ERI_E_NUMERIC: return "ERI_E_NUMERIC";
     }
     return "ERI_E_UNKNOWN";
@@ -443,12 +543,24 @@ eri_status_t eri_class_shape(int32_t cls, int32_t *n_eri, int32_t *n_rys) {
 eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const int32_t *quartets,
                              int64_t n_quartets, const eri_plan_opts_t *opts, eri_plan_t *out) {
     if (!out || (!shells && n_shells > 0) || n_shells < 0) return ERI_E_INVALID;
-    eri_plan_opts_t o{ERI_FP64, ERI_EXPLICIT, 0, 0};
+    eri_plan_opts_t o{ERI_FP64, ERI_EXPLICIT, 0, 0, 0.0, 0, 0};
     if (opts) o = *opts;
     if (o.precision != ERI_FP64 && o.precision != ERI_MIXED) return ERI_E_INVALID;
-    if (o.quartet_mode != ERI_EXPLICIT && o.quartet_mode != ERI_ALL) return ERI_E_INVALID;
-    long long nq;
-    if (o.quartet_mode == ERI_ALL) {
+    if (o.quartet_mode != ERI_EXPLICIT && o.quartet_mode != ERI_ALL && o.quartet_mode != ERI_UNIQUE8)
+        return ERI_E_INVALID;
+    if (o.flags & ~(ERI_QUARTETS_ON_DEVICE | ERI_NO_PAIR_TABLE)) return ERI_E_INVALID;
+    if (!(o.schwarz_threshold >= 0.0) || !std::isfinite(o.schwarz_threshold)) return ERI_E_INVALID;
+    const long long scount = o.shard_count > 1 ? o.shard_count : 1;
+    if (o.shard_count < 0 || (scount > 1 && o.quartet_mode != ERI_UNIQUE8) || o.shard_index < 0 ||
+        o.shard_index >= scount)
+        return ERI_E_INVALID;
+    const bool screen = o.schwarz_threshold > 0.0;
+    const long long npairs = (long long)n_shells * (n_shells + 1) / 2;
+    if ((screen || o.quartet_mode == ERI_UNIQUE8) && npairs >= 2147483647LL) return ERI_E_UNSUPPORTED;
+    long long nq = 0;
+    if (o.quartet_mode == ERI_UNIQUE8) {
+        nq = 0;  // known after the enumeration
+    } else if (o.quartet_mode == ERI_ALL) {
         double t = (double)n_shells * n_shells * n_shells * n_shells;
         if (t >= 2147483647.0) return ERI_E_UNSUPPORTED;
         nq = (long long)n_shells * n_shells * n_shells * n_shells;
@@ -459,8 +571,9 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     }
     // host validation and normalisation of the shells
     std::vector<double> cx(n_shells), cy(n_shells), cz(n_shells), ex, cn;
-    std::vector<int> pofs(n_shells), np(n_shells), Ls(n_shells);
+    std::vector<int> pofs(n_shells), np(n_shells), Ls(n_shells), bfoff(n_shells);
     int max_nprim = 1;
+    long long n_bf = 0;
     for (int s = 0; s < n_shells; ++s) {
         const eri_shell_t &sh = shells[s];
         if (sh.L < 0 || sh.L > 3) return sh.L > 3 ? ERI_E_UNSUPPORTED : ERI_E_INVALID;
@@ -473,6 +586,8 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         pofs[s] = (int)ex.size();
         np[s] = sh.nprim;
         Ls[s] = sh.L;
+        bfoff[s] = (int)n_bf;
+        n_bf += ncart_h(sh.L);
         max_nprim = std::max(max_nprim, sh.nprim);
         for (int k = 0; k < sh.nprim; ++k) {
             double a = sh.exps[k], c = sh.coefs[k];
@@ -481,19 +596,48 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
             cn.push_back(c * shell_norm(a, sh.L));
         }
     }
-    if (ex.size() >= 2147483647ull) return ERI_E_UNSUPPORTED;
+    if (ex.size() >= 2147483647ull || n_bf >= 2147483647LL) return ERI_E_UNSUPPORTED;
     std::call_once(g_launch_once, register_all);
-
-    cudaError_t e = cudaSetDevice(o.device);
-    if (e != cudaSuccess) return ERI_E_INVALID;
+    {
+        const char *inj = std::getenv("ERI_INJECT_NOMEM");
+        g_inject_nomem = inj ? std::atoll(inj) : 0;
+    }
+    if (g_inject_nomem > 0 && --g_inject_nomem == 0) return ERI_E_NOMEM;  // the host plan object
     eri_plan_s *p = new (std::nothrow) eri_plan_s();
     if (!p) return ERI_E_NOMEM;
+
+    cudaError_t e = cudaSetDevice(o.device);
+    if (e != cudaSuccess) {
+        delete p;
+        return ERI_E_INVALID;
+    }
+    // Schwarz factors of every shell pair (Sec. II-B bound), for screening and for the ranks of
+    // the unique-quartet enumeration (all zero without screening: ranks in pair order)
+    double *d_Q = nullptr;
+    if (screen) {
+        const long long inject = g_inject_nomem;  // the internal plan restarts the count
+        eri_status_t st = schwarz_factors(shells, n_shells, o.device, o.flags & ERI_NO_PAIR_TABLE, &d_Q);
+        g_inject_nomem = inject;
+        if (st != ERI_OK) {
+            delete p;
+            return st;
+        }
+    } else if (o.quartet_mode == ERI_UNIQUE8 && npairs > 0) {
+        if ((e = plan_malloc(&d_Q, npairs * sizeof(double))) == cudaSuccess)
+            e = cudaMemset(d_Q, 0, npairs * sizeof(double));
+        if (e != cudaSuccess) {
+            cudaFree(d_Q);
+            delete p;
+            return cuda_status(e);
+        }
+    }
     p->device = o.device;
     p->precision = o.precision;
     p->n_shells = n_shells;
     p->n_prims = (long long)ex.size();
     p->nq = nq;
     p->max_nprim = max_nprim;
+    p->n_bf = n_bf;
     for (int c = 0; c < 256; ++c) {
         p->class_prec[c] = -1;
         p->class_err[c] = -1.0f;
@@ -508,12 +652,73 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     if (e == cudaSuccess) e = upload(&p->d_pofs, pofs);
     if (e == cudaSuccess) e = upload(&p->d_nprim, np);
     if (e == cudaSuccess) e = upload(&d_L, Ls);
-    if (e == cudaSuccess) e = cudaMalloc(&p->d_err, sizeof(int));
+    if (e == cudaSuccess) e = upload(&p->d_bfoff, bfoff);
+    if (e == cudaSuccess) e = plan_malloc(&p->d_err, sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(p->d_err, 0, sizeof(int));
-    if (e != cudaSuccess) { cudaFree(d_L); free_plan(p); return cuda_status(e); }
+    if (e != cudaSuccess) { cudaFree(d_L); cudaFree(d_Q); free_plan(p); return cuda_status(e); }
+
+    // the quartet list on the device: d_in (owned unless it is the caller's device list) and,
+    // for a screened caller's list, the caller's index of every kept quartet (d_orig)
+    int4 *d_in = nullptr;
+    int *d_orig = nullptr;
+    bool own_in = true;
+    if (o.quartet_mode == ERI_UNIQUE8) {
+        long long total = 0;
+        e = screen_unique8(d_Q, npairs, o.schwarz_threshold, o.shard_index, scount, &d_in, &nq, &total,
+                           2147483646LL, nullptr);
+        p->screen_candidates = npairs * (npairs + 1) / 2;
+        p->screen_kept = total;
+    } else if (nq > 0) {
+        const unsigned blocks = (unsigned)((nq + 255) / 256);
+        if (o.quartet_mode == ERI_ALL) {
+            if ((e = plan_malloc(&d_in, nq * sizeof(int4))) == cudaSuccess) {
+                all_quartets_kernel<<<blocks, 256>>>(n_shells, nq, d_in);
+                e = cudaGetLastError();
+            }
+        } else if (o.flags & ERI_QUARTETS_ON_DEVICE) {
+            d_in = reinterpret_cast<int4 *>(const_cast<int32_t *>(quartets));
+            own_in = false;
+        } else {
+            if ((e = plan_malloc(&d_in, nq * sizeof(int4))) == cudaSuccess)
+                e = cudaMemcpy(d_in, quartets, nq * sizeof(int4), cudaMemcpyHostToDevice);
+        }
+        p->screen_candidates = nq;
+        p->screen_kept = nq;
+        if (e == cudaSuccess && screen) {
+            // ids are validated before they index the pair factors
+            int *d_verr = nullptr;
+            if ((e = plan_malloc(&d_verr, sizeof(int))) == cudaSuccess &&
+                (e = cudaMemset(d_verr, 0, sizeof(int))) == cudaSuccess) {
+                check_ids_kernel<<<blocks, 256>>>(d_in, nq, n_shells, d_verr);
+                int verr = 0;
+                if ((e = cudaMemcpy(&verr, d_verr, sizeof(int), cudaMemcpyDeviceToHost)) == cudaSuccess && verr)
+                    e = cudaErrorInvalidValue;
+            }
+            cudaFree(d_verr);
+            int4 *d_f = nullptr;
+            long long nf = 0;
+            if (e == cudaSuccess) e = screen_filter(d_in, nq, d_Q, o.schwarz_threshold, &d_f, &d_orig, &nf, nullptr);
+            if (e == cudaSuccess) {
+                if (own_in) cudaFree(d_in);
+                d_in = d_f;
+                own_in = true;
+                nq = nf;
+                p->screen_kept = nf;
+            }
+        }
+    }
+    cudaFree(d_Q);
+    p->nq = nq;
+    if (e != cudaSuccess) {
+        if (own_in) cudaFree(d_in);
+        cudaFree(d_orig);
+        cudaFree(d_L);
+        free_plan(p);
+        return e == cudaErrorInvalidValue ? ERI_E_INVALID
+                                          : (e == cudaErrorNotSupported ? ERI_E_UNSUPPORTED : cuda_status(e));
+    }
 
     if (nq > 0) {
-        int4 *d_in = nullptr;
         uint8_t *d_keys = nullptr, *d_keys_sorted = nullptr;
         int *d_vals = nullptr;
         unsigned long long *d_counts = nullptr;
@@ -521,25 +726,12 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         size_t tmp_bytes = 0;
         int *d_verr = nullptr;
         const unsigned blocks = (unsigned)((nq + 255) / 256);
-        bool own_in = true;
         do {
-            if (o.quartet_mode == ERI_ALL) {
-                if ((e = cudaMalloc(&d_in, nq * sizeof(int4))) != cudaSuccess) break;
-                all_quartets_kernel<<<blocks, 256>>>(n_shells, nq, d_in);
-            } else if (o.flags & ERI_QUARTETS_ON_DEVICE) {
-                d_in = reinterpret_cast<int4 *>(const_cast<int32_t *>(quartets));
-                own_in = false;
-            } else {
-                if ((e = cudaMalloc(&d_in, nq * sizeof(int4))) != cudaSuccess) break;
-                if ((e = cudaMemcpy(d_in, quartets, nq * sizeof(int4), cudaMemcpyHostToDevice)) !=
-                    cudaSuccess)
-                    break;
-            }
-            if ((e = cudaMalloc(&d_keys, nq)) != cudaSuccess) break;
-            if ((e = cudaMalloc(&d_keys_sorted, nq)) != cudaSuccess) break;
-            if ((e = cudaMalloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
-            if ((e = cudaMalloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
-            if ((e = cudaMalloc(&d_verr, sizeof(int))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_keys, nq)) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_keys_sorted, nq)) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
+            if ((e = plan_malloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_verr, sizeof(int))) != cudaSuccess) break;
             if ((e = cudaMemset(d_verr, 0, sizeof(int))) != cudaSuccess) break;
             classify_kernel<<<blocks, 256>>>(d_in, nq, d_L, n_shells, d_keys, d_vals, d_verr);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -547,13 +739,13 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
             e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_vals,
                                                 p->d_perm, (int)nq, 0, 8);
             if (e != cudaSuccess) break;
-            if ((e = cudaMalloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
             e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_vals,
                                                 p->d_perm, (int)nq, 0, 8);
             if (e != cudaSuccess) break;
-            if ((e = cudaMalloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
+            if ((e = plan_malloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
             gather_kernel<<<blocks, 256>>>(d_in, p->d_perm, nq, p->d_quartets);
-            if ((e = cudaMalloc(&d_counts, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_counts, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
             if ((e = cudaMemset(d_counts, 0, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
             histogram_kernel<<<std::min<unsigned>(blocks, 4096u), 256>>>(d_keys_sorted, nq, d_counts);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
@@ -565,6 +757,10 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
                 break;
             if (verr) e = cudaErrorInvalidValue;  // mapped to ERI_E_INVALID below
             for (int c = 0; c < 256; ++c) p->count[c] = (long long)counts[c];
+            if (d_orig) {  // sorted position -> index in the caller's list
+                compose_kernel<<<blocks, 256>>>(p->d_perm, d_orig, nq);
+                e = cudaGetLastError();
+            }
         } while (false);
         cudaError_t sync_e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = sync_e;
@@ -576,11 +772,15 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         cudaFree(d_tmp);
         cudaFree(d_verr);
         if (e != cudaSuccess) {
+            cudaFree(d_orig);
             cudaFree(d_L);
             free_plan(p);
             return e == cudaErrorInvalidValue ? ERI_E_INVALID : cuda_status(e);
         }
+    } else if (own_in) {
+        cudaFree(d_in);
     }
+    cudaFree(d_orig);
     cudaFree(d_L);
     // primitive-pair table, when it fits: n_prims^2 records of kPairFields doubles
     if (!(o.flags & ERI_NO_PAIR_TABLE) && p->nq > 0) {
@@ -593,7 +793,7 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
                 for (int k = 0; k < shells[s2].nprim; ++k) prim_shell[pofs[s2] + k] = s2;
             int *d_ps = nullptr;
             cudaError_t pe = upload(&d_ps, prim_shell);
-            if (pe == cudaSuccess) pe = cudaMalloc(&p->d_pairs, (size_t)bytes);
+            if (pe == cudaSuccess) pe = plan_malloc(&p->d_pairs, (size_t)bytes);
             if (pe == cudaSuccess) {
                 pair_table_kernel<<<4 * 1024, 256>>>(p->d_cx, p->d_cy, p->d_cz, p->d_exps, p->d_cn,
                                                       d_ps, p->n_prims, p->d_pairs);
@@ -1014,6 +1214,33 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
 }
 
+eri_status_t eri_plan_class_kernels(eri_plan_t plan, int32_t cls, char *buf, size_t len) {
+    if (!plan || cls < 0 || cls > 255 || !buf || len == 0) return ERI_E_INVALID;
+    buf[0] = 0;
+    const int v = class_variant(plan, cls);
+    const Canon c = canonicalise(cls);
+    const int k = c.cls * kNumVariants + v;
+    if (!g_launch[k]) return ERI_E_UNSUPPORTED;
+    const bool split = plan->max_nprim == 1 && g_info[k].setup;
+    const bool tpq = g_info[k].tpq && v != 2;
+    char cfg[64];
+    std::snprintf(cfg, sizeof(cfg), "Cfg<%d, %d, %d, %d, %s>", (c.cls >> 6) & 3, (c.cls >> 4) & 3,
+                  (c.cls >> 2) & 3, c.cls & 3, v == 0 ? "double" : "float");
+    // the launch choice of launch_class (eri_kernels.cuh) for a per-class call
+    std::string name;
+    if (tpq && split)
+        name = std::string("eri_setup_kernel<") + cfg + "> + eri_tpq_kernel<" + cfg + ", 1>";
+    else if (tpq)
+        name = std::string("eri_tpq_kernel<") + cfg + ", 0>";
+    else if (split)
+        name = std::string("eri_setup_kernel<") + cfg + "> + eri_class_kernel<" + cfg + ", 0, 1>";
+    else
+        name = std::string("eri_class_kernel<") + cfg + (v == 2 ? ", 1, 0>" : ", 0, 0>");
+    if (name.size() + 1 > len) return ERI_E_INVALID;
+    std::memcpy(buf, name.c_str(), name.size() + 1);
+    return ERI_OK;
+}
+
 eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches) {
     if (!plan || cls < 0 || cls > 255 || !n_launches) return ERI_E_INVALID;
     *n_launches = 0;
@@ -1089,6 +1316,69 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
     return ERI_OK;
 }
 
+eri_status_t eri_plan_screening(eri_plan_t plan, int64_t *candidates, int64_t *kept) {
+    if (!plan) return ERI_E_INVALID;
+    if (candidates) *candidates = plan->screen_candidates;
+    if (kept) *kept = plan->screen_kept;
+    return ERI_OK;
+}
+
+eri_status_t eri_plan_quartets(eri_plan_t plan, int32_t *quartets_out) {
+    if (!plan || (!quartets_out && plan->nq > 0)) return ERI_E_INVALID;
+    if (plan->nq == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    return cuda_status(cudaMemcpy(quartets_out, plan->d_quartets, plan->nq * sizeof(int4), cudaMemcpyDeviceToHost));
+}
+
+eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf) {
+    if (!plan || !n_bf) return ERI_E_INVALID;
+    *n_bf = plan->n_bf;
+    return ERI_OK;
+}
+
+eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, const float *d_scales,
+                           const double *d_D, double *d_J, double *d_K, int32_t flags, void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (flags & ~(ERI_DIGEST_UNIQUE8 | ERI_DIGEST_ACCUMULATE)) return ERI_E_INVALID;
+    if (plan->n_bf > 0 && (!d_D || !d_J || !d_K)) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4 ||
+        reinterpret_cast<uintptr_t>(d_D) % 8 || reinterpret_cast<uintptr_t>(d_J) % 8 ||
+        reinterpret_cast<uintptr_t>(d_K) % 8)
+        return ERI_E_INVALID;
+    if (plan->n_bf == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long n2 = plan->n_bf * plan->n_bf;
+    cudaError_t e = cudaSuccess;
+    if (!(flags & ERI_DIGEST_ACCUMULATE)) {
+        e = cudaMemsetAsync(d_J, 0, sizeof(double) * (size_t)n2, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(d_K, 0, sizeof(double) * (size_t)n2, s);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    if (plan->nq == 0) return ERI_OK;
+    if (!plan->d_D32 && (e = cudaMalloc(&plan->d_D32, sizeof(float) * (size_t)n2)) != cudaSuccess)
+        return cuda_status(e);
+    if ((e = digest_density_f32(d_D, n2, plan->d_D32, s)) != cudaSuccess) return cuda_status(e);
+    size_t off = 0;
+    for (int c = 0; c < 256; ++c) {
+        const size_t seg = packed_segment_bytes(plan->count[c], class_neri(c), bits);
+        if (plan->count[c] > 0) {
+            DigestClass dc;
+            dc.cls = c;
+            dc.quartets = plan->d_quartets + plan->first[c];
+            dc.nq = plan->count[c];
+            dc.packed = reinterpret_cast<const uint32_t *>(static_cast<const char *>(d_packed) + off);
+            dc.scales = d_scales + plan->first[c];
+            e = digest_class(dc, bits, (flags & ERI_DIGEST_UNIQUE8) != 0, plan->d_bfoff, plan->d_D32,
+                             plan->n_bf, d_J, d_K, s);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        off += seg;
+    }
+    return ERI_OK;
+}
+
 eri_status_t eri_sync(eri_plan_t plan, void *stream) {
     if (!plan) return ERI_E_INVALID;
     cudaSetDevice(plan->device);
@@ -1099,7 +1389,6 @@ eri_status_t eri_sync(eri_plan_t plan, void *stream) {
     if (e != cudaSuccess) return ERI_E_CUDA;
     if (err) cudaMemset(plan->d_err, 0, sizeof(int));
     if (err & 1) return ERI_E_NUMERIC;
-    if (err & 2) return ERI_E_TIMEOUT;
     return ERI_OK;
 }
 

@@ -101,9 +101,44 @@ __global__ void convert_kernel(const double *in, long long n, float *f, double *
     back[i] = f32_to_f64(v);
 }
 
+// FMA throughput probe: kFmaChains independent chains of `iters` fused multiply-adds per
+// thread (operands depend on the thread, the result is stored, so nothing folds away).
+constexpr int kFmaChains = 8;
+template <typename T>
+__global__ void fma_probe_kernel(int iters, T b, T c, T *__restrict__ sink) {
+    const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    T a[kFmaChains];
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) a[k] = (T)(tid % 1024) * (T)1e-3 + (T)k;
+#pragma unroll 1
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int r = 0; r < 16; ++r)
+#pragma unroll
+            for (int k = 0; k < kFmaChains; ++k) a[k] = fma(a[k], b, c);
+    T s = 0;
+#pragma unroll
+    for (int k = 0; k < kFmaChains; ++k) s += a[k];
+    sink[tid] = s;
+}
+
 }  // namespace eri
 
 using namespace eri;
+
+extern "C" eri_status_t eri_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, void *d_sink,
+                                      void *stream) {
+    if ((precision != ERI_FP64 && precision != ERI_MIXED) || n_threads < 256 || n_threads % 256 ||
+        n_threads / 256 > 0x7fffffffLL || iters < 1 || !d_sink)
+        return ERI_E_INVALID;
+    const unsigned blocks = (unsigned)(n_threads / 256);
+    cudaStream_t s = (cudaStream_t)stream;
+    if (precision == ERI_FP64)
+        fma_probe_kernel<double><<<blocks, 256, 0, s>>>(iters, 0.999999, 1e-7, static_cast<double *>(d_sink));
+    else
+        fma_probe_kernel<float><<<blocks, 256, 0, s>>>(iters, 0.9999f, 1e-4f, static_cast<float *>(d_sink));
+    return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}
 
 extern "C" eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t n, double *d_F,
                                         void *stream) {

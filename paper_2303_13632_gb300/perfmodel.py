@@ -60,21 +60,25 @@ def bytes_per_quartet(cls, bits: int) -> int:
     return 16 + out
 
 
-def roofline_seconds(cls, n_quartets: int, precision: str, bits: int, hbm_gbs: float) -> float:
+def roofline_seconds(cls, n_quartets: int, precision: str, bits: int, hbm_gbs: float,
+                     p32: float = PEAK_FP32_TFLOPS, p64: float = PEAK_FP64_TFLOPS) -> float:
+    """Shortest time for n_quartets quartets of class cls: the slower of the ALU time (FP64 flops
+    at the FP64 peak plus FP32 flops at the FP32 peak, TFLOP/s) and the HBM time."""
     f64, rr = flops_per_quartet(cls)
     if precision == "fp64":
-        t_alu = (f64 + rr) / (PEAK_FP64_TFLOPS * 1e12)
+        t_alu = (f64 + rr) / (p64 * 1e12)
     else:
-        t_alu = f64 / (PEAK_FP64_TFLOPS * 1e12) + rr / (PEAK_FP32_TFLOPS * 1e12)
+        t_alu = f64 / (p64 * 1e12) + rr / (p32 * 1e12)
     t_mem = bytes_per_quartet(cls, bits) / (hbm_gbs * 1e9)
     return n_quartets * max(t_alu, t_mem)
 
 
-def fp32_equivalent_flops(cls, precision: str) -> float:
+def fp32_equivalent_flops(cls, precision: str, p32: float = PEAK_FP32_TFLOPS,
+                          p64: float = PEAK_FP64_TFLOPS) -> float:
     """Work of one quartet expressed in FP32-pipe flops (FP64 flops weighted by the peak
     ratio), so that one number and one peak describe a mixed kernel."""
     f64, rr = flops_per_quartet(cls)
-    w = PEAK_FP32_TFLOPS / PEAK_FP64_TFLOPS
+    w = p32 / p64
     return f64 * w + (rr * w if precision == "fp64" else rr)
 
 

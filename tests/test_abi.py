@@ -68,6 +68,29 @@ int main(void) {
     if (eri_pack_paper512_stream((const void *)4096, 1, 10, 25, (void *)8192, NULL) != ERI_E_INVALID)
         return 6;
     if (eri_plan_num_quartets(NULL, NULL) != ERI_E_INVALID) return 7;
+    {
+        /* option checks happen before any device call */
+        eri_plan_opts_t o;
+        eri_plan_t p = NULL;
+        memset(&o, 0, sizeof o);
+        o.quartet_mode = ERI_UNIQUE8;
+        o.schwarz_threshold = -1.0;
+        if (eri_plan_create(NULL, 0, NULL, 0, &o, &p) != ERI_E_INVALID || p != NULL) return 8;
+        o.schwarz_threshold = 1e-10;
+        o.shard_count = 4;
+        o.shard_index = 4;
+        if (eri_plan_create(NULL, 0, NULL, 0, &o, &p) != ERI_E_INVALID) return 9;
+        o.quartet_mode = ERI_EXPLICIT;
+        o.shard_index = 0;
+        if (eri_plan_create(NULL, 0, NULL, 0, &o, &p) != ERI_E_INVALID) return 10;
+        o.quartet_mode = 7;
+        o.shard_count = 0;
+        if (eri_plan_create(NULL, 0, NULL, 0, &o, &p) != ERI_E_INVALID) return 11;
+    }
+    if (eri_plan_screening(NULL, NULL, NULL) != ERI_E_INVALID) return 12;
+    if (eri_plan_num_basis_functions(NULL, NULL) != ERI_E_INVALID) return 13;
+    if (eri_digest_jk(NULL, 16, NULL, NULL, NULL, NULL, NULL, ERI_DIGEST_UNIQUE8, NULL) != ERI_E_INVALID)
+        return 14;
     eri_plan_destroy(NULL);
     puts("ok");
     return 0;

@@ -108,13 +108,14 @@ def read_peaks():
 
 def measure_alu_peaks(api, torch, stream, device_index):
     """FP32 and FP64 fused multiply-add throughput measured with the library's probe kernel
-    (eri_fma_probe: 8 independent FMA chains per thread, 1216 x 256-thread blocks = 8 CTAs per SM),
-    best of 3 launches timed with CUDA events on the launching stream, with the SM clock sampled
-    during the FP64 probe.  Returns {"fp32_tflops", "fp64_tflops", "clocks"}."""
+    (eri_fma_probe: 16 independent FMA chains per thread, 1216 x 256-thread blocks = 8 CTAs per
+    SM, about 30 ms per launch), best of 3 launches timed with CUDA events on the launching
+    stream, with the SM clock sampled during the FP64 probe.
+    Returns {"fp32_tflops", "fp64_tflops", "clocks"}."""
     n_threads = 152 * 8 * 256
     sink = torch.empty(n_threads, dtype=torch.float64, device=torch.device("cuda", device_index))
     out = {}
-    for prec, iters in (("mixed", 4096), ("fp64", 96)):
+    for prec, iters in (("mixed", 4096), ("fp64", 192)):
         best = None
         clk = ClockSampler(device_index) if prec == "fp64" else None
         if clk:
@@ -130,7 +131,7 @@ def measure_alu_peaks(api, torch, stream, device_index):
                 best = ms if best is None else min(best, ms)
         if clk:
             out["clocks"] = clk.stop()
-        tflops = 256.0 * iters * n_threads / (best * 1e-3) / 1e12
+        tflops = 512.0 * iters * n_threads / (best * 1e-3) / 1e12
         out["fp32_tflops" if prec == "mixed" else "fp64_tflops"] = tflops
     return out
 

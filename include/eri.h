@@ -400,8 +400,14 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
  * call writes the records it reads first).  Calls on one device whose device work overlaps
  * (for example on two streams) race on the array: serialise them.  The first call
  * on a device looks up the device addresses of the array and of the library's constant
- * tables (cudaGetSymbolAddress, with that device current); make that first call before any
- * stream capture.  Asynchronous on `stream` afterwards. */
+ * tables (cudaGetSymbolAddress, with that device current) and copies FP32 copies of two table
+ * parts from host memory into further file-scope device arrays (about 280 KB; a copy, not an
+ * allocation); make that first call before any stream capture.  CUDA loads a library's device
+ * code and data lazily by default (CUDA_MODULE_LOADING=LAZY), so the arrays and each class's
+ * kernels become resident on their first use, not when the library is loaded: an application
+ * that reserves nearly all device memory up front should either make one call per class and
+ * precision it will use before that, or run with CUDA_MODULE_LOADING=EAGER.  Asynchronous on
+ * `stream` afterwards. */
 eri_status_t eri_compute_class_noalloc(int32_t cls, int32_t precision, const double *d_cx,
                                        const double *d_cy, const double *d_cz,
                                        const int32_t *d_pofs, const int32_t *d_nprim,
@@ -429,6 +435,13 @@ eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t n, double 
 eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
                             double *d_w, void *stream);
 
+/* eri_rys_device as the mixed-precision setup evaluates it (ERI_MIXED, whose roots and weights
+ * are rounded to FP32 afterwards): the polynomial terms from the fifth on and the Taylor terms of
+ * F_0 / F_1 from the third on in FP32, reciprocals and 1/sqrt from the FP32 approximation with
+ * one Newton-Raphson step in FP64; about 1e-9 relative to eri_rys_device.  Same arguments. */
+eri_status_t eri_rys_device_mixed(int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                                  double *d_w, void *stream);
+
 /* The binary64 -> binary32 -> binary64 conversions the setup stages use (integer arithmetic,
  * IEEE round to nearest, ties to even; no counterpart in the paper): d_f[i] = (float)d_in[i],
  * d_back[i] = (double)d_f[i].  Asynchronous on `stream`. */
@@ -436,9 +449,9 @@ eri_status_t eri_convert_device(const double *d_in, int64_t n, float *d_f, doubl
                                 void *stream);
 
 /* Fused multiply-add throughput probe (no counterpart in the paper): n_threads threads (a
- * multiple of 256) each run 8 independent chains of 16 * iters FMAs in FP64 (ERI_FP64) or FP32
+ * multiple of 256) each run 16 independent chains of 16 * iters FMAs in FP64 (ERI_FP64) or FP32
  * (ERI_MIXED) and store one value each to d_sink (n_threads doubles or floats), so a timed launch
- * does 256 * iters * n_threads floating-point operations: the measured ALU peak the roofline of
+ * does 512 * iters * n_threads floating-point operations: the measured ALU peak the roofline of
  * the FP-bound kernels is quoted against.  Asynchronous on `stream`; ERI_E_INVALID for other
  * arguments. */
 eri_status_t eri_fma_probe(int32_t precision, int64_t n_threads, int32_t iters, void *d_sink, void *stream);

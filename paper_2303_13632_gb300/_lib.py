@@ -93,6 +93,7 @@ SIGNATURES = {
     "eri_compute_class_noalloc": (_i32, [_i32, _i32, _p, _p, _p, _p, _p, _p, _p, _p, _i64, _p, _p, _p]),
     "eri_boys_device": (_i32, [_i32, _p, _i64, _p, _p]),
     "eri_rys_device": (_i32, [_i32, _p, _i64, _p, _p, _p]),
+    "eri_rys_device_mixed": (_i32, [_i32, _p, _i64, _p, _p, _p]),
     "eri_convert_device": (_i32, [_p, _i64, _p, _p, _p]),
     "eri_class_id": (_i32, [_i32, _i32, _i32, _i32]),
     "eri_class_shape": (_i32, [_i32, _i32p, _i32p]),

@@ -138,7 +138,7 @@ def eri_plan_class_kernels(plan: Plan, cls: int) -> str:
 
 
 def eri_fma_probe(precision: str, n_threads: int, iters: int, sink, stream=None) -> None:
-    """Launches the FMA throughput probe: 256 * iters * n_threads flops (see include/eri.h)."""
+    """Launches the FMA throughput probe: 512 * iters * n_threads flops (see include/eri.h)."""
     check(_lib.load().eri_fma_probe(PRECISIONS[precision], n_threads, iters, _dev_ptr(sink),
                                     _stream_handle(stream)), "eri_fma_probe")
 
@@ -303,6 +303,11 @@ def eri_boys_device(mmax: int, T, F, stream=None) -> None:
 def eri_rys_device(nroots: int, T, x, w, stream=None) -> None:
     check(_lib.load().eri_rys_device(nroots, _dev_ptr(T), T.numel(), _dev_ptr(x), _dev_ptr(w),
                                      _stream_handle(stream)), "eri_rys_device")
+
+
+def eri_rys_device_mixed(nroots: int, T, x, w, stream=None) -> None:
+    check(_lib.load().eri_rys_device_mixed(nroots, _dev_ptr(T), T.numel(), _dev_ptr(x), _dev_ptr(w),
+                                           _stream_handle(stream)), "eri_rys_device_mixed")
 
 
 def eri_class_id(La: int, Lb: int, Lc: int, Ld: int) -> int:

@@ -16,6 +16,12 @@ namespace eri {
 constexpr int kRysNmax = 9;
 constexpr int kRysDeg = 12;
 constexpr int kRysTail = 10;  // coefficients j >= kRysTail are evaluated in FP32
+// Mixed-precision setup (the B, C and weights are rounded to FP32 afterwards): coefficients
+// j >= kRysTailMixed of the root/weight pieces and j >= kBoysTailMixed of the F_0/F_1 Taylor
+// series in FP32 (tails below 3.5e-3 and 1.3e-3 of the value, so the FP32 rounding of the tail
+// moves the result by about 1e-9 relative, far below the FP32 rounding that follows)
+constexpr int kRysTailMixed = 4;
+constexpr int kBoysTailMixed = 2;
 constexpr int kBoysMmax = 16;
 constexpr int kBoysTaylor = 10;
 constexpr int kBoysCols = kBoysMmax + kBoysTaylor + 1;
@@ -114,6 +120,8 @@ struct Tables {
     const double *herm_w;
     const double *boys_grid;
     const double *boys_t01;  // F_0, F_1 Taylor coefficients divided by j! (kBoysTaylor each)
+    const float *rys_tail_m;  // FP32 copies of coefficients kRysTailMixed..kRysDeg of every piece
+    const float *boys_t01_f;  // FP32 copy of boys_t01
     int tasym[kRysNmax + 1];
     long long offset[kRysNmax + 1];
     int herm_off[kRysNmax + 2];
@@ -231,14 +239,93 @@ __device__ __forceinline__ double poly_eval(const double *__restrict__ a,
     return s;
 }
 
-// Root mu (0-based, ascending) and weight of the order-n Rys rule at T.
+// 1/v and 1/sqrt(v) for the mixed-precision setup: the FP32 approximation of the special-
+// function unit (PTX rcp.approx / rsqrt.approx, relative error below 2^-22) refined by one
+// Newton-Raphson step in FP64, r' = r + r (1 - v r) and r' = r + (r/2)(1 - v r^2), which squares
+// the relative error (to about 1e-13), for v in the FP32 normal range.
+__device__ __forceinline__ float rcp_approx_f32(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ float rsqrt_approx_f32(float v) {
+    float r;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
+    return r;
+}
+__device__ __forceinline__ double recip_nr(double v) {
+    const double r = f32_to_f64(rcp_approx_f32(f64_to_f32(v)));
+    return fma(r, fma(-v, r, 1.0), r);
+}
+__device__ __forceinline__ double rsqrt_nr(double v) {
+    const double r = f32_to_f64(rsqrt_approx_f32(f64_to_f32(v)));
+    const double e = fma(-v * r, r, 1.0);  // 1 - v r^2
+    return fma(0.5 * r, e, r);
+}
+
+// boys_f01 of the mixed-precision setup: terms j >= kBoysTailMixed of the Taylor series in FP32
+// (from boys_t01_f and d rounded to FP32), the rest in FP64; beyond the grid F_0 = sqrt(pi/T)/2
+// with 1/sqrt(T) from rsqrt_nr.
+template <bool WANT1>
+__device__ __forceinline__ void boys_f01_mixed(double T, const double *__restrict__ t01,
+                                               const float *__restrict__ t01f, double &F0, double &F1) {
+    const int k = __float2int_rn(f64_to_f32(T) * (float)(1.0 / kBoysStep));
+    if (k <= (int)(kBoysTmax / kBoysStep)) {
+        const double d = fma(f32_to_f64((float)k), kBoysStep, -T);
+        const float df = f64_to_f32(d);
+        const double *g = t01 + k * (2 * kBoysTaylor);
+        const float *gf = t01f + k * (2 * kBoysTaylor);
+        float s0f = __ldg(gf + kBoysTaylor - 1);
+        float s1f = WANT1 ? __ldg(gf + 2 * kBoysTaylor - 1) : 0.0f;
+#pragma unroll
+        for (int j = kBoysTaylor - 2; j >= kBoysTailMixed; --j) {
+            s0f = fmaf(s0f, df, __ldg(gf + j));
+            if (WANT1) s1f = fmaf(s1f, df, __ldg(gf + kBoysTaylor + j));
+        }
+        double s0 = f32_to_f64(s0f), s1 = WANT1 ? f32_to_f64(s1f) : 0.0;
+#pragma unroll
+        for (int j = kBoysTailMixed - 1; j >= 0; --j) {
+            s0 = fma(s0, d, __ldg(g + j));
+            if (WANT1) s1 = fma(s1, d, __ldg(g + kBoysTaylor + j));
+        }
+        F0 = s0;
+        F1 = s1;
+    } else {
+        const double rs = rsqrt_nr(T);
+        F0 = 0.88622692545275801365 * rs;  // sqrt(pi) / 2
+        F1 = WANT1 ? F0 * (0.5 * rs * rs) : 0.0;
+    }
+}
+
+// poly_eval of the mixed-precision setup: terms j >= kRysTailMixed in FP32.
+__device__ __forceinline__ double poly_eval_mixed(const double *__restrict__ a,
+                                                  const float *__restrict__ at, double u) {
+    const float uf = f64_to_f32(u);
+    float sf = __ldg(at + (kRysDeg - kRysTailMixed));
+#pragma unroll
+    for (int j = kRysDeg - 1; j >= kRysTailMixed; --j) sf = fmaf(sf, uf, __ldg(at + (j - kRysTailMixed)));
+    double s = f32_to_f64(sf);
+#pragma unroll
+    for (int j = kRysTailMixed - 1; j >= 0; --j) s = fma(s, u, __ldg(a + j));
+    return s;
+}
+
+// Root mu (0-based, ascending) and weight of the order-n Rys rule at T.  MIXED: the evaluation
+// of the mixed-precision setup (FP32 tails, Newton-refined reciprocals; about 1e-9 relative).
+template <bool MIXED = false>
 __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double T, double &x,
                                          double &w) {
     if (n == 1) {
         double F0, F1;
-        boys_f01<true>(T, tb.boys_t01, F0, F1);
-        w = F0;
-        x = F1 / F0;
+        if constexpr (MIXED) {
+            boys_f01_mixed<true>(T, tb.boys_t01, tb.boys_t01_f, F0, F1);
+            w = F0;
+            x = F1 * recip_nr(F0);
+        } else {
+            boys_f01<true>(T, tb.boys_t01, F0, F1);
+            w = F0;
+            x = F1 / F0;
+        }
         return;
     }
     // unit interval from an FP32 copy of T (no FP64 conversion instruction); when FP32
@@ -249,13 +336,25 @@ __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double
         double u = 2.0 * (T - f32_to_f64((float)k)) - 1.0;
         const long long f = (tb.offset[n] / (kRysDeg + 1)) + (long long)k * (2 * n) + 2 * mu;
         const double *c = tb.rys_poly + f * (kRysDeg + 1);
-        const float *ct = tb.rys_tail + f * (kRysDeg + 1 - kRysTail);
-        x = poly_eval(c, ct, u);
-        w = poly_eval(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTail), u);
+        if constexpr (MIXED) {
+            const float *ct = tb.rys_tail_m + f * (kRysDeg + 1 - kRysTailMixed);
+            x = poly_eval_mixed(c, ct, u);
+            w = poly_eval_mixed(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTailMixed), u);
+        } else {
+            const float *ct = tb.rys_tail + f * (kRysDeg + 1 - kRysTail);
+            x = poly_eval(c, ct, u);
+            w = poly_eval(c + (kRysDeg + 1), ct + (kRysDeg + 1 - kRysTail), u);
+        }
     } else {
         int h = tb.herm_off[n] + mu;
-        x = __ldg(tb.herm_x2 + h) / T;
-        w = __ldg(tb.herm_w + h) * rsqrt(T);
+        if constexpr (MIXED) {
+            const double rs = rsqrt_nr(T);
+            x = __ldg(tb.herm_x2 + h) * (rs * rs);
+            w = __ldg(tb.herm_w + h) * rs;
+        } else {
+            x = __ldg(tb.herm_x2 + h) / T;
+            w = __ldg(tb.herm_w + h) * rsqrt(T);
+        }
     }
 }
 

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include <vector>
+
 #include "../../include/eri.h"
 #include "eri_device.cuh"
 
@@ -10,6 +12,8 @@ namespace eri {
 
 // Device addresses of the constant tables on the current device (uploaded on first use).
 cudaError_t tables_for_current_device(Tables *out);
+// FP32 copies of the table parts the mixed-precision setup reads (eri_tables.cu).
+void mixed_table_copies(std::vector<float> &tail_m, std::vector<float> &t01_f);
 
 // Quartets per launch of the split setup/recurrence path (a multiple of 32 so that every chunk
 // starts on a 32-bit word of the packed stream) and the widest setup record (n_Rys = 7).

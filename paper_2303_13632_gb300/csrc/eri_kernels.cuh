@@ -304,11 +304,16 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
     double x, w;
     if constexpr (LTOT == 0) {
         double F0, F1;
-        boys_f01<false>(geo[G_T], tb.boys_t01, F0, F1);
+        if constexpr (sizeof(R) == 4)
+            boys_f01_mixed<false>(geo[G_T], tb.boys_t01, tb.boys_t01_f, F0, F1);
+        else
+            boys_f01<false>(geo[G_T], tb.boys_t01, F0, F1);
         w = F0;
         x = 0.0;
     } else {
-        rys_root(tb, C::NRYS, mu, geo[G_T], x, w);
+        // mixed precision: the values are rounded to FP32 below, so the root evaluation of the
+        // mixed setup (about 1e-9 relative) serves
+        rys_root<sizeof(R) == 4>(tb, C::NRYS, mu, geo[G_T], x, w);
     }
     bc[S_WZ] = to_r<R>(geo[G_PREF] * w);
     if constexpr (LTOT > 0) {

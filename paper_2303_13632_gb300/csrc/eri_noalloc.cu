@@ -33,6 +33,10 @@ namespace {
 // held by every GPU that loads the library until the process exits).
 static __device__ __align__(256) double g_noalloc_scratch[(size_t)ERI_NOALLOC_MAX_QUARTETS *
                                                           kSetupFieldsMax];
+// FP32 copies of table parts read by the mixed-precision setup, written once per device at
+// set-up from host memory (a copy into these arrays, no allocation)
+static __device__ float g_rys_tail_m[(RYS_POLY_LEN / (RYS_DEG + 1)) * (RYS_DEG + 1 - kRysTailMixed)];
+static __device__ float g_boys_t01_f[BOYS_T01_LEN];
 
 struct DeviceState {
     bool ready = false;
@@ -84,6 +88,16 @@ cudaError_t device_state(DeviceState **out) {
         t.boys_t01 = static_cast<const double *>(p);
         if ((e = cudaGetSymbolAddress(&p, device_tables::rys_tail_f_h)) != cudaSuccess) return e;
         t.rys_tail = static_cast<const float *>(p);
+        std::vector<float> tail_m, t01_f;
+        mixed_table_copies(tail_m, t01_f);
+        if (tail_m.size() * sizeof(float) != sizeof(g_rys_tail_m) || t01_f.size() * sizeof(float) != sizeof(g_boys_t01_f))
+            return cudaErrorInvalidValue;
+        if ((e = cudaGetSymbolAddress(&p, g_rys_tail_m)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(p, tail_m.data(), sizeof(g_rys_tail_m), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        t.rys_tail_m = static_cast<const float *>(p);
+        if ((e = cudaGetSymbolAddress(&p, g_boys_t01_f)) != cudaSuccess) return e;
+        if ((e = cudaMemcpy(p, t01_f.data(), sizeof(g_boys_t01_f), cudaMemcpyHostToDevice)) != cudaSuccess) return e;
+        t.boys_t01_f = static_cast<const float *>(p);
         for (int i = 0; i <= kRysNmax; ++i) {
             t.tasym[i] = host_tables::rys_tasym_h[i];
             t.offset[i] = host_tables::rys_offset_h[i];

@@ -1,6 +1,7 @@
 // eri_tables.cu -- device copies of the generated Rys/Boys tables and the component
 // diagnostics eri_boys_device / eri_rys_device (same device code as the ERI kernels).
 #include <mutex>
+#include <vector>
 
 #include "eri_device.cuh"
 #include "eri_internal.h"
@@ -24,6 +25,19 @@ bool g_tables_ready[kMaxDevices];
 Tables g_tables[kMaxDevices];
 }  // namespace
 
+// FP32 copies for the mixed-precision setup: coefficients kRysTailMixed..kRysDeg of every
+// root/weight piece, and the F_0/F_1 Taylor table (round to nearest).
+void mixed_table_copies(std::vector<float> &tail_m, std::vector<float> &t01_f) {
+    const int pieces = RYS_POLY_LEN / (RYS_DEG + 1);
+    const int keep = RYS_DEG + 1 - kRysTailMixed;
+    tail_m.resize((size_t)pieces * keep);
+    for (int f = 0; f < pieces; ++f)
+        for (int j = 0; j < keep; ++j)
+            tail_m[(size_t)f * keep + j] = (float)rys_poly_h[(size_t)f * (RYS_DEG + 1) + kRysTailMixed + j];
+    t01_f.resize(BOYS_T01_LEN);
+    for (int i = 0; i < BOYS_T01_LEN; ++i) t01_f[i] = (float)boys_t01_h[i];
+}
+
 // Uploads the tables to the current device once; returns the device addresses.
 cudaError_t tables_for_current_device(Tables *out) {
     int dev = 0;
@@ -34,8 +48,11 @@ cudaError_t tables_for_current_device(Tables *out) {
     if (!g_tables_ready[dev]) {
         Tables t{};
         double *buf = nullptr;
+        std::vector<float> tail_m, t01_f;
+        mixed_table_copies(tail_m, t01_f);
         size_t n = (size_t)RYS_POLY_LEN + 2 * (size_t)RYS_HERM_LEN + (size_t)BOYS_GRID_LEN +
-                   (size_t)BOYS_T01_LEN + ((size_t)RYS_TAIL_LEN + 1) / 2;
+                   (size_t)BOYS_T01_LEN + ((size_t)RYS_TAIL_LEN + 1) / 2 + (tail_m.size() + 1) / 2 +
+                   (t01_f.size() + 1) / 2;
         e = cudaMalloc(&buf, n * sizeof(double));
         if (e != cudaSuccess) return e;
         double *p = buf;
@@ -56,6 +73,14 @@ cudaError_t tables_for_current_device(Tables *out) {
         p += BOYS_T01_LEN;
         if (e == cudaSuccess) e = cudaMemcpy(p, rys_tail_f_h, sizeof(rys_tail_f_h), cudaMemcpyHostToDevice);
         t.rys_tail = reinterpret_cast<const float *>(p);
+        p += ((size_t)RYS_TAIL_LEN + 1) / 2;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p, tail_m.data(), tail_m.size() * sizeof(float), cudaMemcpyHostToDevice);
+        t.rys_tail_m = reinterpret_cast<const float *>(p);
+        p += (tail_m.size() + 1) / 2;
+        if (e == cudaSuccess)
+            e = cudaMemcpy(p, t01_f.data(), t01_f.size() * sizeof(float), cudaMemcpyHostToDevice);
+        t.boys_t01_f = reinterpret_cast<const float *>(p);
         if (e != cudaSuccess) {
             cudaFree(buf);
             return e;
@@ -81,6 +106,7 @@ __global__ void boys_kernel(Tables tb, int mmax, const double *__restrict__ T, l
     for (int m = 0; m <= mmax; ++m) F[i * (mmax + 1) + m] = f[m];
 }
 
+template <bool MIXED>
 __global__ void rys_kernel(Tables tb, int nroots, const double *__restrict__ T, long long n,
                            double *__restrict__ X, double *__restrict__ W) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -88,7 +114,7 @@ __global__ void rys_kernel(Tables tb, int nroots, const double *__restrict__ T, 
     long long k = i / nroots;
     int mu = (int)(i % nroots);
     double x, w;
-    rys_root(tb, nroots, mu, T[k], x, w);
+    rys_root<MIXED>(tb, nroots, mu, T[k], x, w);
     X[i] = x;
     W[i] = w;
 }
@@ -101,9 +127,9 @@ __global__ void convert_kernel(const double *in, long long n, float *f, double *
     back[i] = f32_to_f64(v);
 }
 
-// FMA throughput probe: kFmaChains independent chains of `iters` fused multiply-adds per
+// FMA throughput probe: kFmaChains independent chains of 16 * `iters` fused multiply-adds per
 // thread (operands depend on the thread, the result is stored, so nothing folds away).
-constexpr int kFmaChains = 8;
+constexpr int kFmaChains = 16;
 template <typename T>
 __global__ void fma_probe_kernel(int iters, T b, T c, T *__restrict__ sink) {
     const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -151,8 +177,9 @@ extern "C" eri_status_t eri_boys_device(int32_t mmax, const double *d_T, int64_t
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
 }
 
-extern "C" eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
-                                       double *d_w, void *stream) {
+namespace {
+eri_status_t rys_device(bool mixed, int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                        double *d_w, void *stream) {
     if (nroots < 1 || nroots > kRysNmax || n < 0 || (n > 0 && (!d_T || !d_x || !d_w)))
         return ERI_E_INVALID;
     if (n == 0) return ERI_OK;
@@ -160,8 +187,22 @@ extern "C" eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_
     if (tables_for_current_device(&tb) != cudaSuccess) return ERI_E_CUDA;
     long long total = n * nroots;
     long long blocks = (total + 255) / 256;
-    rys_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, nroots, d_T, n, d_x, d_w);
+    if (mixed)
+        rys_kernel<true><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, nroots, d_T, n, d_x, d_w);
+    else
+        rys_kernel<false><<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(tb, nroots, d_T, n, d_x, d_w);
     return cudaGetLastError() == cudaSuccess ? ERI_OK : ERI_E_CUDA;
+}
+}  // namespace
+
+extern "C" eri_status_t eri_rys_device(int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                                       double *d_w, void *stream) {
+    return rys_device(false, nroots, d_T, n, d_x, d_w, stream);
+}
+
+extern "C" eri_status_t eri_rys_device_mixed(int32_t nroots, const double *d_T, int64_t n, double *d_x,
+                                             double *d_w, void *stream) {
+    return rys_device(true, nroots, d_T, n, d_x, d_w, stream);
 }
 
 

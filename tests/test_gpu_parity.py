@@ -124,6 +124,28 @@ def test_rys_roots_reproduce_boys_moments(n):
         np.testing.assert_allclose(mom, F, rtol=2e-13, atol=0, err_msg=f"T={t}")
 
 
+@pytest.mark.parametrize("n", range(1, 10))
+def test_rys_mixed_setup_evaluation(n):
+    """The root/weight evaluation of the mixed-precision setup (FP32 tails, Newton-refined
+    reciprocals) agrees with the FP64 evaluation to 1e-8 relative across both branches (the
+    polynomial pieces and the Gauss-Hermite limit) and every unit interval of T; its values
+    are rounded to FP32 (6e-8) afterwards."""
+    rng = np.random.default_rng(100 + n)
+    Ts = np.concatenate([[0.0, 1e-9, 0.05, 0.5, 1.0, 29.999, 30.0, 49.99, 50.0, 50.01],
+                         rng.uniform(0, 100, 2000), np.arange(0, 95, 1.0) + 0.999999,
+                         np.arange(0, 95, 1.0) + 1e-7, [150.0, 1e4, 1e6]])
+    T = torch.tensor(Ts, dtype=torch.float64, device="cuda")
+    x64, w64 = torch.empty(len(Ts) * n, dtype=torch.float64, device="cuda"), torch.empty(len(Ts) * n, dtype=torch.float64, device="cuda")
+    xm, wm = torch.empty_like(x64), torch.empty_like(w64)
+    api.eri_rys_device(n, T, x64, w64)
+    api.eri_rys_device_mixed(n, T, xm, wm)
+    torch.cuda.synchronize()
+    for a, b in ((xm, x64), (wm, w64)):
+        a, b = a.cpu().numpy(), b.cpu().numpy()
+        rel = np.abs(a - b) / np.abs(b)
+        assert np.max(rel) < 1e-8, (n, float(np.max(rel)), float(Ts[np.argmax(rel) // n]))
+
+
 def test_fp64_all_classes(workload, oracle_values):
     pool, q = workload
     per, _ = gpu_fp64(pool, q, "fp64")

@@ -34,6 +34,9 @@ namespace {
 constexpr int kDigestThreads = 256;
 constexpr int kDigestSmem = 48 * 1024;
 
+// the twelve D blocks (x, y), x != y, in x-major order
+__constant__ int c_bx[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+__constant__ int c_by[12] = {1, 2, 3, 0, 2, 3, 0, 1, 3, 0, 1, 2};
 // pass p fixes positions (PX, PY) and sums over (PU, PW)
 __constant__ int c_px[6] = {0, 2, 0, 1, 0, 1};
 __constant__ int c_py[6] = {1, 3, 2, 2, 3, 3};
@@ -57,6 +60,7 @@ struct DigestArgs {
     int T;         // quartets per tile
     int nD;        // staged D values per quartet
     int boff[16];  // offset of D block (x, y) (index x*4 + y) in a quartet's D area
+    int rstart[13];  // first row of each of the 12 blocks (x != y, in x-major order); [12] = rows
     int NI;        // items per quartet
     int ioff[7];   // first item of each pass
 };
@@ -130,24 +134,22 @@ __global__ void __launch_bounds__(kDigestThreads) digest_kernel(DigestArgs A) {
         e_s[v] = (float)code;
     }
     __syncthreads();
-    // the D blocks between the quartet's shells, D[o_x + i][o_y + j] for x != y
-    for (int idx = tid; idx < tn * A.nD; idx += kDigestThreads) {
-        const int t = idx / A.nD;
-        const int r = idx - t * A.nD;
-        int x = 0, y = 1;
-#pragma unroll 1
-        for (int b = 0; b < 16; ++b) {
-            const int bx = b >> 2, by = b & 3;
-            if (bx == by) continue;
-            if (r >= A.boff[b] && r < A.boff[b] + A.n[bx] * A.n[by]) {
-                x = bx;
-                y = by;
-            }
-        }
-        const int loc = r - A.boff[x * 4 + y];
-        const int i = loc / A.n[y], j = loc - (loc / A.n[y]) * A.n[y];
+    // the D blocks between the quartet's shells, D[o_x + i][o_y + j] for x != y: one thread per
+    // (quartet, block row), whose at most 10 loads are independent
+    const int rows = A.rstart[12];
+    for (int idx = tid; idx < tn * rows; idx += kDigestThreads) {
+        const int t = idx / rows;
+        const int r = idx - t * rows;
+        int b = 0;
+#pragma unroll
+        for (int k = 1; k < 12; ++k) b += r >= A.rstart[k];
+        const int x = c_bx[b], y = c_by[b];
+        const int i = r - A.rstart[b], ny = A.n[y];
         const int *m = meta + t * 8;
-        d_s[idx] = __ldg(A.D + (long long)(m[x] + i) * A.nbf + (m[y] + j));
+        const float *src = A.D + (long long)(m[x] + i) * A.nbf + m[y];
+        float *dst = d_s + t * A.nD + A.boff[x * 4 + y] + i * ny;
+#pragma unroll 10
+        for (int j = 0; j < ny; ++j) dst[j] = __ldg(src + j);
     }
     __syncthreads();
     for (int it = tid; it < tn * A.NI; it += kDigestThreads) {
@@ -231,6 +233,9 @@ cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int
         if (x != y) o += A.n[x] * A.n[y];
     }
     A.nD = o;
+    const int bx[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+    A.rstart[0] = 0;
+    for (int b = 0; b < 12; ++b) A.rstart[b + 1] = A.rstart[b] + A.n[bx[b]];
     const int px[6] = {0, 2, 0, 1, 0, 1}, py[6] = {1, 3, 2, 2, 3, 3};
     A.ioff[0] = 0;
     for (int p = 0; p < 6; ++p) A.ioff[p + 1] = A.ioff[p] + A.n[px[p]] * A.n[py[p]];

@@ -4,7 +4,8 @@ FLOPs are counted like arXiv 2303.13632 counts n_FLOPQ (Sec. III-A: add, multipl
 divide count one each, an FMA two), per primitive quartet of the canonical class the kernel
 evaluates:
   setup       40 + 20 n_Rys     Gaussian-product prefactors and B, C arrays       (FP64)
-  roots       60 n_Rys          Rys roots/weights (done on the host in the paper) (FP64)
+  roots       60 n_Rys          Rys roots/weights (done on the host in the paper) (FP64 on the
+                                plain path; 20 n_Rys FP64 + 40 n_Rys R on the mixed path)
   VRR         5 * 3 n_Rys * ((La+Lb+1)(Lc+Ld+1) - 1)                            (R)
   HRR         2 per produced entry of the bra and ket transfers                 (R)
   quadrature  3 n_Rys n_ERIQ                                                     (R)
@@ -38,20 +39,24 @@ def canonical(cls):
     return bra + ket
 
 
-def flops_per_quartet(cls):
-    """(fp64_flops, rr_flops) per primitive quartet of class cls."""
+def flops_per_quartet(cls, precision: str = "fp64"):
+    """(fp64_flops, rr_flops) per primitive quartet of class cls.  The root/weight evaluation
+    (60 n) is FP64 on the plain path; the mixed path evaluates the polynomial terms beyond the
+    fourth (and the Taylor terms of F_0/F_1 beyond the second) in FP32, a third / two thirds
+    split of the same 60 n, counted 20 n FP64 + 40 n in the recurrence type."""
     La, Lb, Lc, Ld = canonical(cls)
     n = (La + Lb + Lc + Ld) // 2 + 1
     nab, ncd = La + Lb, Lc + Ld
     neri = ncart(La) * ncart(Lb) * ncart(Lc) * ncart(Ld)
-    f64 = 40 + 20 * n + 60 * n
+    roots64 = 60 * n if precision == "fp64" else 20 * n
+    f64 = 40 + 20 * n + roots64
     vrr = 5 * 3 * n * ((nab + 1) * (ncd + 1) - 1)
     hrr_bra = sum((nab - j + 1) * (ncd + 1) for j in range(1, Lb + 1))
     hrr_ket = (La + 1) * (Lb + 1) * sum(ncd - l + 1 for l in range(1, Ld + 1))
     hrr = 2 * 3 * n * (hrr_bra + hrr_ket)
     quad = 3 * n * neri
     comp = 2 * neri + 1
-    return f64, vrr + hrr + quad + comp
+    return f64, vrr + hrr + quad + comp + (60 * n - roots64)
 
 
 def bytes_per_quartet(cls, bits: int) -> int:
@@ -64,7 +69,7 @@ def roofline_seconds(cls, n_quartets: int, precision: str, bits: int, hbm_gbs: f
                      p32: float = PEAK_FP32_TFLOPS, p64: float = PEAK_FP64_TFLOPS) -> float:
     """Shortest time for n_quartets quartets of class cls: the slower of the ALU time (FP64 flops
     at the FP64 peak plus FP32 flops at the FP32 peak, TFLOP/s) and the HBM time."""
-    f64, rr = flops_per_quartet(cls)
+    f64, rr = flops_per_quartet(cls, precision)
     if precision == "fp64":
         t_alu = (f64 + rr) / (p64 * 1e12)
     else:
@@ -77,17 +82,19 @@ def fp32_equivalent_flops(cls, precision: str, p32: float = PEAK_FP32_TFLOPS,
                           p64: float = PEAK_FP64_TFLOPS) -> float:
     """Work of one quartet expressed in FP32-pipe flops (FP64 flops weighted by the peak
     ratio), so that one number and one peak describe a mixed kernel."""
-    f64, rr = flops_per_quartet(cls)
+    f64, rr = flops_per_quartet(cls, precision)
     w = p32 / p64
     return f64 * w + (rr * w if precision == "fp64" else rr)
 
 
 # ---------------------------------------------------------------------------------------------
 # GPU analogue of the paper's throughput model (Eq. 12: f_max n_ERIQ / (max(n_RR, n_GQ, n_CS) +
-# 10), the slowest pipelined stage plus a fixed per-quartet overhead).  On the GPU the stages
-# are the FP64 setup, the FP32 recurrences/quadrature and the output bytes, each at an effective
-# rate, plus a per-quartet overhead that depends on the kernel form the class runs in:
-#     t_q = max(F64 / R64, F32 / R32, B / BW) + o_form
+# 10), the slowest pipelined stage plus a fixed per-quartet overhead).  On the GPU the FP64 setup
+# and the FP32 recurrences/quadrature do not overlap as FPGA pipeline stages do: the split path
+# runs them as two kernels one after the other, and in the inline form they share the warp
+# schedulers.  So their times add, and the output bytes bound the sum from below; each stage runs
+# at an effective rate, plus a per-quartet overhead that depends on the kernel form:
+#     t_q = max(F64 / R64 + F32 / R32, B / BW) + o_form
 # The rates and overheads are fitted to measured per-class times.
 
 def kernel_form(cls) -> str:
@@ -107,8 +114,8 @@ FORMS = ("tpq_inline", "tpq_split", "phase_split")
 
 
 def model_seconds_per_quartet(cls, params, bits: int = 16) -> float:
-    f64, rr = flops_per_quartet(cls)
-    t = max(f64 / params["R64"], rr / params["R32"], bytes_per_quartet(cls, bits) / params["BW"])
+    f64, rr = flops_per_quartet(cls, "mixed")
+    t = max(f64 / params["R64"] + rr / params["R32"], bytes_per_quartet(cls, bits) / params["BW"])
     return t + params["o_" + kernel_form(cls)]
 
 

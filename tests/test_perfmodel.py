@@ -43,10 +43,19 @@ def test_canonical_classes():
         assert P.ncart(k[0]) * P.ncart(k[1]) >= P.ncart(k[2]) * P.ncart(k[3])
 
 
+def test_mixed_split_keeps_the_total():
+    """The mixed path moves two thirds of the root evaluation to the recurrence type; the total
+    count per quartet is the same as the plain path's."""
+    for cls in [(0, 0, 0, 0), (1, 1, 1, 1), (3, 2, 1, 0), (3, 3, 3, 3)]:
+        a, b = P.flops_per_quartet(cls, "fp64"), P.flops_per_quartet(cls, "mixed")
+        n = sum(cls) // 2 + 1
+        assert sum(a) == sum(b) and a[0] - b[0] == 40 * n
+
+
 def test_roofline_time_is_the_larger_bound():
     cls, n = (1, 1, 1, 1), 1000
     t = P.roofline_seconds(cls, n, "mixed", 16, 7000.0)
-    f64, rr = P.flops_per_quartet(cls)
+    f64, rr = P.flops_per_quartet(cls, "mixed")
     t_alu = n * (f64 / (P.PEAK_FP64_TFLOPS * 1e12) + rr / (P.PEAK_FP32_TFLOPS * 1e12))
     t_mem = n * P.bytes_per_quartet(cls, 16) / 7000e9
     assert t == pytest.approx(max(t_alu, t_mem))

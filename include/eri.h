@@ -336,7 +336,13 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
 /* Flags of eri_digest_jk. */
 enum {
     ERI_DIGEST_UNIQUE8 = 1,    /* each quartet stands for its 8-fold symmetric images (Sec. II-B) */
-    ERI_DIGEST_ACCUMULATE = 2  /* add to d_J / d_K instead of overwriting them */
+    ERI_DIGEST_ACCUMULATE = 2, /* add to d_J / d_K instead of overwriting them */
+    ERI_DIGEST_SYMMETRIC = 4   /* with ERI_DIGEST_UNIQUE8 only: the caller's D is symmetric (as an
+                                  SCF density is).  The 8-fold images of every quartet then give
+                                  each pair of transposed J / K entries equal totals, so half the
+                                  sums and half the device atomics are made and the matrices are
+                                  symmetrised at the end, J = (J + J^T) / 2 (with
+                                  ERI_DIGEST_ACCUMULATE the incoming J, K must be symmetric) */
 };
 
 /* Basis functions of the plan: shells in the order given to eri_plan_create, each contributing
@@ -367,8 +373,9 @@ eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf);
  * added to J and K in FP64 with device atomics (the order of the FP64 additions, hence the last
  * bits, can vary between runs).  The plan keeps an n_bf x n_bf FP32 buffer for the rounded D
  * (allocated on the first call).  Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits
- * outside 2..24, unknown flags, NULL buffers where the plan needs them, or buffers not aligned
- * to their element size; ERI_E_NOMEM / ERI_E_CUDA from allocation or launch failures. */
+ * outside 2..24, unknown flags, ERI_DIGEST_SYMMETRIC without ERI_DIGEST_UNIQUE8, NULL buffers
+ * where the plan needs them, or buffers not aligned to their element size; ERI_E_NOMEM /
+ * ERI_E_CUDA from allocation or launch failures. */
 eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, const float *d_scales,
                            const double *d_D, double *d_J, double *d_K, int32_t flags, void *stream);
 

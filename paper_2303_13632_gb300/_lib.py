@@ -29,6 +29,7 @@ ERI_NO_PAIR_TABLE = 2
 ERI_NOALLOC_MAX_QUARTETS = 16384
 ERI_DIGEST_UNIQUE8 = 1
 ERI_DIGEST_ACCUMULATE = 2
+ERI_DIGEST_SYMMETRIC = 4
 
 STATUS_NAMES = {
     ERI_OK: "ERI_OK", ERI_E_INVALID: "ERI_E_INVALID", ERI_E_UNSUPPORTED: "ERI_E_UNSUPPORTED",

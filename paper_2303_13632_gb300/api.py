@@ -279,9 +279,11 @@ def eri_plan_num_basis_functions(plan: Plan) -> int:
 
 
 def eri_digest_jk(plan: Plan, bits: int, packed, scales, D, J, K, unique8: bool = False,
-                  accumulate: bool = False, stream=None) -> None:
-    """J and K (n_bf x n_bf float64 CUDA tensors) from the compressed ERIs and the density D."""
-    flags = (_lib.ERI_DIGEST_UNIQUE8 if unique8 else 0) | (_lib.ERI_DIGEST_ACCUMULATE if accumulate else 0)
+                  accumulate: bool = False, symmetric: bool = False, stream=None) -> None:
+    """J and K (n_bf x n_bf float64 CUDA tensors) from the compressed ERIs and the density D
+    (symmetric=True: the caller asserts D is symmetric, see ERI_DIGEST_SYMMETRIC)."""
+    flags = ((_lib.ERI_DIGEST_UNIQUE8 if unique8 else 0) | (_lib.ERI_DIGEST_ACCUMULATE if accumulate else 0)
+             | (_lib.ERI_DIGEST_SYMMETRIC if symmetric else 0))
     check(_lib.load().eri_digest_jk(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales), _dev_ptr(D),
                                     _dev_ptr(J), _dev_ptr(K), flags, _stream_handle(stream)),
           "eri_digest_jk")

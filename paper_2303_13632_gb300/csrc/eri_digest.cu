@@ -99,6 +99,11 @@ __device__ __forceinline__ void pass_coefs(int p, int m, int c[4]) {
     }
 }
 
+// SYM: the caller's D is symmetric.  Then S = S' in every pass (D[u][w] = D[w][u]) and the two
+// destinations M[x][y], M[y][x] of an item receive equal totals over the whole sum, so each item
+// forms one sum and adds all of its coefficient to M[x][y] alone; the finished matrices are
+// symmetrised afterwards, M = (M + M^T) / 2 (symmetrise_kernel), which restores every entry.
+template <bool SYM>
 __global__ void __launch_bounds__(kDigestThreads) digest_kernel(DigestArgs A) {
     extern __shared__ __align__(16) unsigned char smem[];
     int *meta = reinterpret_cast<int *>(smem);               // T x 8: bf offsets, mask, eps
@@ -169,22 +174,47 @@ __global__ void __launch_bounds__(kDigestThreads) digest_kernel(DigestArgs A) {
         const float *ep = e_s + t * A.neri + ix * A.st[x] + iy * A.st[y];
         const float *d1 = d_s + t * A.nD + A.boff[u * 4 + w];  // D[u][w], row length nw
         const float *d2 = d_s + t * A.nD + A.boff[w * 4 + u];  // D[w][u], row length nu
-        float S = 0.0f, S2 = 0.0f;
-#pragma unroll 1
-        for (int iu = 0; iu < nu; ++iu)
-#pragma unroll 2
-            for (int iw = 0; iw < nw; ++iw) {
-                const float e = ep[iu * su + iw * sw];
-                S = fmaf(e, d1[iu * nw + iw], S);
-                S2 = fmaf(e, d2[iw * nu + iu], S2);
-            }
         const float eps = __int_as_float(m[5]);
         double *M = p < 2 ? A.J : A.K;
         const long long row = m[x] + ix, col = m[y] + iy;
-        const float v1 = (c[0] ? S : 0.0f) + (c[1] ? S2 : 0.0f);
-        const float v2 = (c[2] ? S : 0.0f) + (c[3] ? S2 : 0.0f);
-        if (c[0] | c[1]) atomicAdd(M + row * A.nbf + col, f32_to_f64(v1 * eps));
-        if (c[2] | c[3]) atomicAdd(M + col * A.nbf + row, f32_to_f64(v2 * eps));
+        if constexpr (SYM) {
+            float S = 0.0f;
+#pragma unroll 1
+            for (int iu = 0; iu < nu; ++iu)
+#pragma unroll 2
+                for (int iw = 0; iw < nw; ++iw) S = fmaf(ep[iu * su + iw * sw], d1[iu * nw + iw], S);
+            const float k = (float)(c[0] + c[1] + c[2] + c[3]);
+            atomicAdd(M + row * A.nbf + col, f32_to_f64(S * (k * eps)));
+        } else {
+            float S = 0.0f, S2 = 0.0f;
+#pragma unroll 1
+            for (int iu = 0; iu < nu; ++iu)
+#pragma unroll 2
+                for (int iw = 0; iw < nw; ++iw) {
+                    const float e = ep[iu * su + iw * sw];
+                    S = fmaf(e, d1[iu * nw + iw], S);
+                    S2 = fmaf(e, d2[iw * nu + iu], S2);
+                }
+            const float v1 = (c[0] ? S : 0.0f) + (c[1] ? S2 : 0.0f);
+            const float v2 = (c[2] ? S : 0.0f) + (c[3] ? S2 : 0.0f);
+            if (c[0] | c[1]) atomicAdd(M + row * A.nbf + col, f32_to_f64(v1 * eps));
+            if (c[2] | c[3]) atomicAdd(M + col * A.nbf + row, f32_to_f64(v2 * eps));
+        }
+    }
+}
+
+// M = (M + M^T) / 2 for an n x n row-major matrix, one thread per pair i < j.
+__global__ void symmetrise_kernel(double *__restrict__ M, long long n) {
+    const long long pairs = n * (n - 1) / 2;
+    for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < pairs;
+         t += (long long)gridDim.x * blockDim.x) {
+        long long i = (long long)((sqrt(8.0 * (double)t + 1.0) + 1.0) * 0.5);  // row, i >= 1
+        while (i * (i - 1) / 2 > t) --i;
+        while ((i + 1) * i / 2 <= t) ++i;
+        const long long j = t - i * (i - 1) / 2;  // 0 <= j < i
+        const double v = 0.5 * (M[i * n + j] + M[j * n + i]);
+        M[i * n + j] = v;
+        M[j * n + i] = v;
     }
 }
 
@@ -206,7 +236,16 @@ cudaError_t digest_density_f32(const double *D, long long n, float *out, cudaStr
     return cudaGetLastError();
 }
 
-cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int *bfoff,
+cudaError_t digest_symmetrise(double *M, long long n, cudaStream_t stream) {
+    if (n < 2) return cudaSuccess;
+    const long long pairs = n * (n - 1) / 2;
+    long long blocks = (pairs + 255) / 256;
+    if (blocks > 8192) blocks = 8192;
+    symmetrise_kernel<<<(unsigned)blocks, 256, 0, stream>>>(M, n);
+    return cudaGetLastError();
+}
+
+cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, bool symmetric, const int *bfoff,
                          const float *D32, long long nbf, double *J, double *K, cudaStream_t stream) {
     if (c.nq <= 0) return cudaSuccess;
     DigestArgs A{};
@@ -248,7 +287,10 @@ cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int
     if (smem > (size_t)kDigestSmem) return cudaErrorInvalidValue;
     const long long tiles = (c.nq + T - 1) / T;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
-    digest_kernel<<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
+    if (symmetric)
+        digest_kernel<true><<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
+    else
+        digest_kernel<false><<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
     return cudaGetLastError();
 }
 

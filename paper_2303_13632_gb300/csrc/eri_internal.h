@@ -52,9 +52,12 @@ struct DigestClass {
 };
 // D (FP64, n values) rounded to FP32 into out.
 cudaError_t digest_density_f32(const double *D, long long n, float *out, cudaStream_t stream);
-// Adds the class's contributions to J and K (see eri_digest.cu).
-cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, const int *bfoff,
+// Adds the class's contributions to J and K (see eri_digest.cu); with `symmetric` (D symmetric)
+// each item adds to one of its two transposed destinations, and digest_symmetrise finishes.
+cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, bool symmetric, const int *bfoff,
                          const float *D32, long long nbf, double *J, double *K, cudaStream_t stream);
+// M = (M + M^T) / 2 (n x n, row major).
+cudaError_t digest_symmetrise(double *M, long long n, cudaStream_t stream);
 
 // Device quartet lists (eri_screen.cu).  Diagonal quartets (i j | i j) of every unordered pair
 // P = i (i + 1) / 2 + j, i >= j.

@@ -151,6 +151,15 @@ struct Cfg {
     static constexpr int SETUP_GEO = 8;  // AB, CD, swab, swcd
     static constexpr int SETUP_FIELDS = SETUP_GEO + NRYS * SN;
     static constexpr int TPQ_THREADS = 128;
+    // resident CTAs per SM the thread-per-quartet kernel is compiled for (the register cap):
+    // the inline-setup FP32 kernels wait on two random pair-table records per quartet, so they
+    // need more warps in flight than their natural register use (about 100) allows.  The caps
+    // are the largest at which ptxas reports no spill for these classes (8 CTAs = 64 registers
+    // up to 6 outputs, 7 = 72 up to 10, 6 = 80 up to 18; larger classes keep their own count).
+    // [ss|ss] measured 6% slower at 8 CTAs than with its own count and keeps it.
+    static constexpr int TPQ_MINB = (TPQ_SMALL && sizeof(R) == 4)
+                                        ? (NERI == 1 ? 1 : (NERI <= 6 ? 8 : (NERI <= 10 ? 7 : (NERI <= 18 ? 6 : 1))))
+                                        : 1;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -973,6 +982,10 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
         // holds at most Q * n_ERIQ * bits < 2^31 bits)
         const int head = (int)(bit0 & 31);
         const int qbase = dq * C::NERI + da * st0 + dc * st2;
+        // byte widths: every code owns its byte / halfword of the stage, so a plain store
+        // replaces the shared-memory atomics of the generic bit packing
+        uint16_t *st16 = reinterpret_cast<uint16_t *>(stage) + (head >> 4);
+        uint8_t *st8 = reinterpret_cast<uint8_t *>(stage) + (head >> 3);
 #pragma unroll
         for (int bb = 0; bb < C::BCH; ++bb) {
             int b = dch * C::BCH + bb;
@@ -982,10 +995,17 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                     R v = RTraits<R>::round_away(acc[bb][d] * inv);
                     v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
                     uint32_t code = to_code<R>(v, bits) & mask;
-                    const int s = head + (qbase + b * st1 + d * st3) * bits;
-                    int wi = s >> 5, off = s & 31;
-                    atomicOr(stage + wi, code << off);
-                    if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                    const int e = qbase + b * st1 + d * st3;
+                    if (bits == 16) {
+                        st16[e] = (uint16_t)code;
+                    } else if (bits == 8) {
+                        st8[e] = (uint8_t)code;
+                    } else {
+                        const int s = head + e * bits;
+                        int wi = s >> 5, off = s & 31;
+                        atomicOr(stage + wi, code << off);
+                        if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                    }
                 }
             }
         }
@@ -1281,6 +1301,9 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
         // bit offsets relative to the tile's first stage word, in 32-bit arithmetic
         const int head = (int)(bit0 & 31);
         const int tbase = tid * C::NERI;
+        // byte widths: plain byte / halfword stores (each code owns its slot), else bit packing
+        uint16_t *st16 = reinterpret_cast<uint16_t *>(stage) + (head >> 4);
+        uint8_t *st8 = reinterpret_cast<uint8_t *>(stage) + (head >> 3);
 #pragma unroll
         for (int a = 0; a < C::NA; ++a)
 #pragma unroll
@@ -1292,10 +1315,17 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                         R v = RTraits<R>::round_away(acc[((a * C::NB + b) * C::NC + c) * C::ND + d] * inv);
                         v = v > Mr ? Mr : (v < -Mr ? -Mr : v);
                         uint32_t code = to_code<R>(v, bits) & mask;
-                        const int sb = head + (tbase + a * st0 + b * st1 + c * st2 + d * st3) * bits;
-                        int wi = sb >> 5, off = sb & 31;
-                        atomicOr(stage + wi, code << off);
-                        if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                        const int e = tbase + a * st0 + b * st1 + c * st2 + d * st3;
+                        if (bits == 16) {
+                            st16[e] = (uint16_t)code;
+                        } else if (bits == 8) {
+                            st8[e] = (uint8_t)code;
+                        } else {
+                            const int sb = head + e * bits;
+                            int wi = sb >> 5, off = sb & 31;
+                            atomicOr(stage + wi, code << off);
+                            if (off + bits > 32) atomicOr(stage + wi + 1, code >> (32 - off));
+                        }
                     }
     }
     __syncthreads();
@@ -1321,14 +1351,14 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
 }
 
 template <class C, bool PRESET = false>
-__global__ void __launch_bounds__(C::TPQ_THREADS)
+__global__ void __launch_bounds__(C::TPQ_THREADS, C::TPQ_MINB)
 eri_tpq_kernel(ShellsDev sh, Tables tb, ClassArgs args) {
     extern __shared__ __align__(16) unsigned char smem[];
     tpq_tile<C, PRESET>(sh, tb, args, blockIdx.x, smem);
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::TPQ_THREADS)
+__global__ void __launch_bounds__(C::TPQ_THREADS, C::TPQ_MINB)
 eri_tpq_persistent(ShellsDev sh, Tables tb, ClassArgs args, unsigned long long *counter) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ long long tile_s;

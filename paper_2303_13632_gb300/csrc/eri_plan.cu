@@ -1339,7 +1339,9 @@ eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf) {
 eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, const float *d_scales,
                            const double *d_D, double *d_J, double *d_K, int32_t flags, void *stream) {
     if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
-    if (flags & ~(ERI_DIGEST_UNIQUE8 | ERI_DIGEST_ACCUMULATE)) return ERI_E_INVALID;
+    if (flags & ~(ERI_DIGEST_UNIQUE8 | ERI_DIGEST_ACCUMULATE | ERI_DIGEST_SYMMETRIC)) return ERI_E_INVALID;
+    const bool sym = (flags & ERI_DIGEST_SYMMETRIC) != 0;
+    if (sym && !(flags & ERI_DIGEST_UNIQUE8)) return ERI_E_INVALID;
     if (plan->n_bf > 0 && (!d_D || !d_J || !d_K)) return ERI_E_INVALID;
     if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
     if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4 ||
@@ -1370,11 +1372,15 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
             dc.nq = plan->count[c];
             dc.packed = reinterpret_cast<const uint32_t *>(static_cast<const char *>(d_packed) + off);
             dc.scales = d_scales + plan->first[c];
-            e = digest_class(dc, bits, (flags & ERI_DIGEST_UNIQUE8) != 0, plan->d_bfoff, plan->d_D32,
+            e = digest_class(dc, bits, (flags & ERI_DIGEST_UNIQUE8) != 0, sym, plan->d_bfoff, plan->d_D32,
                              plan->n_bf, d_J, d_K, s);
             if (e != cudaSuccess) return cuda_status(e);
         }
         off += seg;
+    }
+    if (sym) {
+        if ((e = digest_symmetrise(d_J, plan->n_bf, s)) != cudaSuccess) return cuda_status(e);
+        if ((e = digest_symmetrise(d_K, plan->n_bf, s)) != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
 }

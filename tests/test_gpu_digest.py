@@ -152,6 +152,43 @@ def test_as_listed_and_accumulate():
     np.testing.assert_allclose(K.cpu().numpy(), 2 * Kg, rtol=1e-12, atol=1e-300)
 
 
+@pytest.mark.parametrize("shard", [None, 3])
+def test_symmetric_density_mode(shard):
+    """ERI_DIGEST_SYMMETRIC (one sum and one atomic per item, then J = (J + J^T) / 2) equals the
+    general digestion for a symmetric D, and the oracle's digestion of the same values: on all
+    unique quartets and on a subset of them (every third), whose 8-fold images are still closed
+    under the index swaps."""
+    unique8 = True
+    rng = np.random.default_rng(61)
+    pool = W.random_contracted_pool(rng, 2, K=2, Ls=(0, 1, 2, 3))
+    q = unique_quartets(pool.n)
+    if shard:
+        q = q[::shard]
+    nbf = int(oracle.basis_offsets(pool)[-1])
+    D = rng.standard_normal((nbf, nbf))
+    D = D + D.T
+    plan = api.eri_plan_create(pool, q, precision="mixed")
+    packed, scales, codes, eps = gpu_codes(plan, 16, len(q))
+    Dd = torch.tensor(D, device="cuda")
+    out = {}
+    for sym in (False, True):
+        J = torch.full((nbf, nbf), float("nan"), dtype=torch.float64, device="cuda")
+        K = torch.full_like(J, float("nan"))
+        api.eri_digest_jk(plan, 16, packed, scales, Dd, J, K, unique8=unique8, symmetric=sym)
+        api.eri_sync(plan)
+        out[sym] = (J.cpu().numpy(), K.cpu().numpy())
+    dec = [codes[i].astype(np.float64) * float(eps[i]) for i in range(len(q))]
+    Jr, Kr = oracle_digest(pool, q, dec, D, unique8)
+    bJ, bK = oracle_digest(pool, q, [np.abs(d) for d in dec], np.abs(D), unique8)
+    for sym in (False, True):
+        Jg, Kg = out[sym]
+        assert np.all(np.abs(Jg - Jr) <= 1e-5 * bJ + 1e-300), sym
+        assert np.all(np.abs(Kg - Kr) <= 1e-5 * bK + 1e-300), sym
+    # J and K of 8-fold closed quartet sets are symmetric for a symmetric D
+    np.testing.assert_array_equal(out[True][0], out[True][0].T)
+    np.testing.assert_array_equal(out[True][1], out[True][1].T)
+
+
 def test_digest_rejects_bad_arguments():
     rng = np.random.default_rng(51)
     pool = W.random_primitive_pool(rng, 1, Ls=(0, 1))
@@ -167,3 +204,5 @@ def test_digest_rejects_bad_arguments():
             api.eri_digest_jk(plan, bits, packed, scales, D, J, K)
     with pytest.raises(api.EriError):
         api.eri_digest_jk(plan, 16, packed, scales, None, J, K)
+    with pytest.raises(api.EriError):  # the symmetric mode needs the 8-fold expansion
+        api.eri_digest_jk(plan, 16, packed, scales, D, J, K, unique8=False, symmetric=True)

@@ -813,14 +813,21 @@ def run_gradient(args):
     G = torch.randn(nb // 8, dtype=torch.float64, device=dev, generator=gen)
     dR = torch.empty((pool.n, 3), dtype=torch.float64, device=dev)
     da = torch.empty(len(pool.exps), dtype=torch.float64, device=dev)
-    ms_bwd = _events(torch, stream, lambda: api.eri_backward(plan, G, dR, da, stream), reps=1)
     out_t = torch.empty(nb // 8, dtype=torch.float64, device=dev)
-    ms_fwd = _events(torch, stream, lambda: api.eri_compute(plan, out_t, stream), reps=1)
-    api.eri_sync(plan, stream)
     n_eri = nb // 8
+    timing = {}
+    for prec in ("mixed", "fp64"):
+        api.eri_plan_set_precision(plan, prec)
+        ms_b = _events(torch, stream, lambda: api.eri_backward(plan, G, dR, da, stream), reps=1)
+        ms_f = _events(torch, stream, lambda: api.eri_compute(plan, out_t, stream), reps=1)
+        timing[prec] = {"ms_backward": ms_b, "ms_forward": ms_f,
+                        "backward_geris": n_eri / (ms_b * 1e-3) / 1e9, "forward_geris": n_eri / (ms_f * 1e-3) / 1e9,
+                        "backward_over_forward": ms_b / ms_f}
+    api.eri_sync(plan, stream)
     out = {"impl": "ours", "workload": "gradient", "metric": "adjoint: ERI derivatives contracted per second",
-           "value": n_eri / (ms_bwd * 1e-3) / 1e9, "unit": "G ERI/s (backward)", "forward_geris_fp64": n_eri / (ms_fwd * 1e-3) / 1e9,
-           "ms_backward": ms_bwd, "ms_forward": ms_fwd, "quartets": int(len(q)), "eris": int(n_eri), "K": 3}
+           "value": timing["mixed"]["backward_geris"], "unit": "G ERI/s (backward, mixed)",
+           "precisions": timing, "backward_mixed_over_forward_fp64": timing["mixed"]["ms_backward"] / timing["fp64"]["ms_forward"],
+           "quartets": int(len(q)), "eris": int(n_eri), "K": 3}
     if not args.no_check:
         # oracle derivative on a sample: a plan of the sampled quartets alone, same G values
         pick = np.sort(rng.choice(len(q), size=64, replace=False))
@@ -832,14 +839,16 @@ def run_gradient(args):
         splan = api.eri_plan_create(pool, qs, precision="fp64")
         order = api.eri_plan_quartet_order(splan)
         Gd = torch.tensor(np.concatenate([Gs[offs[i]:offs[i + 1]] for i in order]), device=dev)
-        api.eri_backward(splan, Gd, dR, da, stream)
-        api.eri_sync(splan, stream)
         rR, ra = oracle.eri_grad_batch(pool, qs, Gs, offs)
-        gR, ga = dR.cpu().numpy(), da.cpu().numpy()
-        out["oracle_check"] = {"quartets": 64, "max_abs_err_dR": float(np.max(np.abs(gR - rR))),
-                               "max_abs_dR": float(np.max(np.abs(rR))),
-                               "max_abs_err_dalpha": float(np.max(np.abs(ga - ra))),
+        out["oracle_check"] = {"quartets": 64, "max_abs_dR": float(np.max(np.abs(rR))),
                                "max_abs_dalpha": float(np.max(np.abs(ra)))}
+        for prec in ("fp64", "mixed"):
+            api.eri_plan_set_precision(splan, prec)
+            api.eri_backward(splan, Gd, dR, da, stream)
+            api.eri_sync(splan, stream)
+            gR, ga = dR.cpu().numpy(), da.cpu().numpy()
+            out["oracle_check"][prec] = {"max_abs_err_dR": float(np.max(np.abs(gR - rR))),
+                                         "max_abs_err_dalpha": float(np.max(np.abs(ga - ra)))}
     print(json.dumps(out), flush=True)
 
 

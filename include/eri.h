@@ -324,10 +324,14 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
  * using d g_a/dA_xi = 2 alpha g_{a+1_xi} - a_xi g_{a-1_xi} and d g_a/d alpha =
  * (2L+3)/(4 alpha) g_a - sum_xi g_{a+2_xi} (same coefficient and normalisation N(alpha, L));
  * the Rys recurrences (Eqs. 6-7) are recomputed on index ranges extended by two and
- * contracted with d_G (Eq. 8 with G weights).  FP64 throughout.  Both outputs are zeroed and
- * then accumulated on `stream` (device atomics: summation order, hence the last bits, can
- * vary between runs).  Supports shells with L <= 2; a plan containing an f shell returns
- * ERI_E_UNSUPPORTED before any device work. */
+ * contracted with d_G (Eq. 8 with G weights).  Each class runs in its precision (the plan's, or
+ * the per-class override): ERI_FP64 in FP64 throughout, for shells with L <= 2 (the extended
+ * ranges of f shells exceed the per-CTA shared memory in FP64; such a plan returns
+ * ERI_E_UNSUPPORTED before any device work); ERI_MIXED with the 2-D integrals on the extended
+ * ranges by the FP32 four-index recursion, G rounded to FP32, the per-thread sums in FP32 and
+ * the geometry, roots, B and C (rounded once), the per-primitive accumulation and both outputs
+ * in FP64, for every class up to f.  Both outputs are zeroed and then accumulated on `stream`
+ * (device atomics: summation order, hence the last bits, can vary between runs). */
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
                           void *stream);
 
@@ -372,7 +376,8 @@ eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf);
  * are exact), the sums over the two contracted indices of a quartet in FP32, scaled by eps and
  * added to J and K in FP64 with device atomics (the order of the FP64 additions, hence the last
  * bits, can vary between runs).  The plan keeps an n_bf x n_bf FP32 buffer for the rounded D
- * (allocated on the first call).  Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits
+ * and a small table of per-class launch parameters (allocated on the first call, the table
+ * copied from host memory on `stream` at every call: one launch covers every class).  Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits
  * outside 2..24, unknown flags, ERI_DIGEST_SYMMETRIC without ERI_DIGEST_UNIQUE8, NULL buffers
  * where the plan needs them, or buffers not aligned to their element size; ERI_E_NOMEM /
  * ERI_E_CUDA from allocation or launch failures. */

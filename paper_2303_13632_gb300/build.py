@@ -48,12 +48,14 @@ def _sources_digest() -> str:
 
 def _units():
     units = [("eri_tables", "eri_tables.cu", []), ("eri_plan", "eri_plan.cu", []),
-             ("eri_backward", "eri_backward.cu", []), ("eri_noalloc", "eri_noalloc.cu", []),
+             ("eri_noalloc", "eri_noalloc.cu", []),
              ("eri_layout", "eri_layout.cu", []),
              ("eri_digest", "eri_digest.cu", []),
              ("eri_screen", "eri_screen.cu", [])]
     for k in range(NUM_TU):
         units.append((f"eri_classes_{k}", "eri_classes.cu", [f"-DERI_TU={k}"]))
+    for k in range(4):
+        units.append((f"eri_backward_{k}", "eri_backward.cu", [f"-DERI_BTU={k}"]))
     return units
 
 
@@ -82,7 +84,7 @@ def build(verbose: bool = False, jobs: int | None = None) -> str:
         os.replace(obj + ".tmp", obj)
         return obj
 
-    units = sorted(_units(), key=lambda u: 0 if u[0].startswith("eri_classes") else 1)
+    units = sorted(_units(), key=lambda u: 0 if u[0].startswith(("eri_classes", "eri_backward")) else 1)
     with ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
         objs = list(ex.map(compile_unit, units))
     tmp = LIB + f".tmp{os.getpid()}"

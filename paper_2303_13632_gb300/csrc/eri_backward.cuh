@@ -17,47 +17,55 @@
 
 namespace eri {
 
-// 2-D integral configuration on the extended index ranges (all L + 2) of class (La..Ld).
-template <int La0, int Lb0, int Lc0, int Ld0>
+// 2-D integral configuration on the extended index ranges (all L + 2) of class (La..Ld), in
+// the recurrence type R: FP64 keeps the VRR + HRR of Eqs. 6-7; FP32 (the mixed adjoint) uses the
+// four-index recursion of phase_direct, which does not amplify FP32 rounding through the
+// transfer relation (see eri_kernels.cuh), with the B and C values of the mixed setup.
+template <int La0, int Lb0, int Lc0, int Ld0, typename R_ = double>
 struct GCfg {
-    using R = double;
+    using R = R_;
     static constexpr int oLa = La0, oLb = Lb0, oLc = Lc0, oLd = Ld0;
     static constexpr int oNA = ncart(La0), oNB = ncart(Lb0), oNC = ncart(Lc0), oND = ncart(Ld0);
     static constexpr int oNERI = oNA * oNB * oNC * oND;
     static constexpr int La = La0 + 2, Lb = Lb0 + 2, Lc = Lc0 + 2, Ld = Ld0 + 2;
     static constexpr int NAB = La + Lb, NCD = Lc + Ld;
     static constexpr int NRYS = (La0 + Lb0 + Lc0 + Ld0 + 2) / 2 + 1;
+    static constexpr int RB = (int)sizeof(R);
     static constexpr bool FUSE_BC = false;
-    static constexpr bool DIRECT = false;
-    static constexpr bool SWAB_OK = true, SWCD_OK = true;
-    static constexpr int SN = S_N, S_CB = S_N, S_CD = S_N;
+    static constexpr bool DIRECT = sizeof(R) == 4;
+    static constexpr bool SWAB_OK = !DIRECT, SWCD_OK = !DIRECT;
+    static constexpr int S_CB = S_N;
+    static constexpr int S_CD = S_N + (DIRECT ? 3 : 0);
+    static constexpr int SN = S_CD + (DIRECT ? 3 : 0);
     static constexpr int JL = (Lb + 1) * (Ld + 1);
     static constexpr int IBLK = (La + 1) * (Lc + 1) * JL;
     static constexpr int JLP = (JL % 2) ? JL : JL + 1;
     static constexpr int IBLKP = (La + 1) * (Lc + 1) * JLP;
     static constexpr int HBLK = (La + 1) * (Lb + 1) * (NCD + 1);
     static constexpr int GEO_BYTES = G_N * 8;
-    static constexpr int BC_BYTES = NRYS * S_N * 8;
-    static constexpr int H_BYTES = 3 * NRYS * HBLK * 8;
-    static constexpr int I_BYTES = 3 * NRYS * IBLKP * 8;
+    static constexpr int BC_BYTES = NRYS * SN * RB;
+    static constexpr int H_BYTES = DIRECT ? 0 : 3 * NRYS * HBLK * RB;
+    static constexpr int I_BYTES = 3 * NRYS * IBLKP * RB;
     static constexpr int NACC = 17;  // dR[4][3], dalpha-part[4], E
-    static constexpr int PERQ = GEO_BYTES + RG_N * 8 + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 + 64;
+    static constexpr int PERQ = GEO_BYTES + RG_N * RB + BC_BYTES + H_BYTES + I_BYTES + NACC * 8 +
+                                oNERI * RB + 160;
     static constexpr int Q = imax(1, imin(8, (100 * 1024) / PERQ));
     static constexpr int THREADS = 256;
     static constexpr int OFF_GEO = 0;
     static constexpr int OFF_RG = Q * GEO_BYTES;
-    static constexpr int OFF_BC = OFF_RG + Q * RG_N * 8;
-    static constexpr int OFF_ACC = OFF_BC + Q * BC_BYTES;
+    static constexpr int OFF_BC = ((OFF_RG + Q * RG_N * RB + 15) / 16) * 16;
+    static constexpr int OFF_ACC = ((OFF_BC + Q * BC_BYTES + 15) / 16) * 16;
     static constexpr int OFF_DR = OFF_ACC + Q * NACC * 8;        // centre gradients, all primitives
     static constexpr int OFF_PRIM = OFF_DR + Q * 12 * 8;          // primitive ids + exponents
     static constexpr int OFF_H = ((OFF_PRIM + Q * 8 * 8 + 15) / 16) * 16;
     static constexpr int OFF_I = OFF_H + Q * H_BYTES;
     static constexpr int OFF_G = OFF_I + Q * I_BYTES;  // the tile's upstream G, generic order
-    static constexpr int SMEM = OFF_G + Q * oNERI * 8 + 16;
+    static constexpr int SMEM = OFF_G + Q * oNERI * RB + 16;
 };
 
 template <class C>
-__device__ __forceinline__ double gI(const double *Iq, int xi, int mu, int i, int j, int k, int l) {
+__device__ __forceinline__ typename C::R gI(const typename C::R *Iq, int xi, int mu, int i, int j, int k,
+                                            int l) {
     return Iq[i_index<C>(xi, mu, i, k, j, l)];
 }
 
@@ -65,15 +73,16 @@ template <class C>
 __global__ void __launch_bounds__(C::THREADS)
 eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__restrict__ G,
                     double *__restrict__ dR, double *__restrict__ dalpha) {
+    using R = typename C::R;
     extern __shared__ __align__(16) unsigned char smem[];
     double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
-    double *rg_s = reinterpret_cast<double *>(smem + C::OFF_RG);
-    double *bc_s = reinterpret_cast<double *>(smem + C::OFF_BC);
+    R *rg_s = reinterpret_cast<R *>(smem + C::OFF_RG);
+    R *bc_s = reinterpret_cast<R *>(smem + C::OFF_BC);
     double *acc_s = reinterpret_cast<double *>(smem + C::OFF_ACC);
     double *dr_s = reinterpret_cast<double *>(smem + C::OFF_DR);
     double *prim_s = reinterpret_cast<double *>(smem + C::OFF_PRIM);  // [q][0..3] exps, [4..7] prim ids
-    double *H_s = reinterpret_cast<double *>(smem + C::OFF_H);
-    double *I_s = reinterpret_cast<double *>(smem + C::OFF_I);
+    R *H_s = reinterpret_cast<R *>(smem + C::OFF_H);
+    R *I_s = reinterpret_cast<R *>(smem + C::OFF_I);
     __shared__ int maxprim_s;
     __shared__ int4 qt_s[C::Q];
 
@@ -88,8 +97,9 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                             pick(g, args.perm[3]));
     }
     // the tile's G (contiguous in the class's generic layout), read once for all primitives
-    double *G_s = reinterpret_cast<double *>(smem + C::OFF_G);
-    for (int e = tid; e < qn * C::oNERI; e += C::THREADS) G_s[e] = G[q0 * C::oNERI + e];
+    // (rounded to FP32 once for the mixed adjoint)
+    R *G_s = reinterpret_cast<R *>(smem + C::OFF_G);
+    for (int e = tid; e < qn * C::oNERI; e += C::THREADS) G_s[e] = to_r<R>(G[q0 * C::oNERI + e]);
     __syncthreads();
     const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
               st3 = args.ostride[3];
@@ -123,15 +133,15 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                                                                               : (s == G_IPQ ? 0.5 : 0.0);
             }
             if (prim == 0 && np > 1) atomicMax(&maxprim_s, np);
-            double *rg = rg_s + q * RG_N;
-            rg[RG_ABX] = geo[G_ABX];
-            rg[RG_ABY] = geo[G_ABY];
-            rg[RG_ABZ] = geo[G_ABZ];
-            rg[RG_CDX] = geo[G_CDX];
-            rg[RG_CDY] = geo[G_CDY];
-            rg[RG_CDZ] = geo[G_CDZ];
-            rg[RG_SWAB] = geo[G_SWAB];
-            rg[RG_SWCD] = geo[G_SWCD];
+            R *rg = rg_s + q * RG_N;
+            rg[RG_ABX] = to_r<R>(geo[G_ABX]);
+            rg[RG_ABY] = to_r<R>(geo[G_ABY]);
+            rg[RG_ABZ] = to_r<R>(geo[G_ABZ]);
+            rg[RG_CDX] = to_r<R>(geo[G_CDX]);
+            rg[RG_CDY] = to_r<R>(geo[G_CDY]);
+            rg[RG_CDZ] = to_r<R>(geo[G_CDZ]);
+            rg[RG_SWAB] = to_r<R>(geo[G_SWAB]);
+            rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
             if (q >= qn || prim >= np) {
                 for (int k = 0; k < 4; ++k) {
                     prim_s[q * 8 + k] = 1.0;
@@ -142,16 +152,19 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
         __syncthreads();
         for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
             int q = it / C::NRYS, mu = it % C::NRYS;
-            phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * S_N);
+            phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * C::SN);
         }
         __syncthreads();
         for (int it = tid; it < C::Q * C::NRYS * 3; it += C::THREADS) {
             int q = it / (C::NRYS * 3), r = it % (C::NRYS * 3);
-            phase_vrr<C>(bc_s + q * C::NRYS * S_N, rg_s + q * RG_N, r / 3, r % 3,
-                         H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
+            if constexpr (C::DIRECT)
+                phase_direct<C>(bc_s + q * C::NRYS * C::SN, r / 3, r % 3, I_s + (size_t)q * (C::I_BYTES / C::RB));
+            else
+                phase_vrr<C>(bc_s + q * C::NRYS * C::SN, rg_s + q * RG_N, r / 3, r % 3,
+                             H_s + (size_t)q * (C::H_BYTES / C::RB), I_s + (size_t)q * (C::I_BYTES / C::RB));
         }
         __syncthreads();
-        {
+        if constexpr (!C::DIRECT) {
             constexpr int NIJ = (C::La + 1) * (C::Lb + 1);
             for (int it = tid; it < C::Q * C::NRYS * 3 * NIJ; it += C::THREADS) {
                 int q = it / (C::NRYS * 3 * NIJ), r = it % (C::NRYS * 3 * NIJ);
@@ -159,10 +172,10 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                 r %= 3 * NIJ;
                 int xi = r / NIJ, ij = r % NIJ;
                 phase_ket<C>(rg_s + q * RG_N, mu, xi, ij / (C::Lb + 1), ij % (C::Lb + 1),
-                             H_s + (size_t)q * (C::H_BYTES / 8), I_s + (size_t)q * (C::I_BYTES / 8));
+                             H_s + (size_t)q * (C::H_BYTES / C::RB), I_s + (size_t)q * (C::I_BYTES / C::RB));
             }
+            __syncthreads();
         }
-        __syncthreads();
         // contraction with G, grouped by axis: for axis x and the x-components (i0, i1, i2, i3)
         // of the four centres, W = sum of G I_y I_z over the outputs with those x-components
         // (y, z the other two axes); each derivative factor of axis x then multiplies W once
@@ -174,11 +187,15 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
             const int lane = tid & 31;
             for (int q = 0; q < qn; ++q) {
                 const double *ex = prim_s + q * 8;
-                const double *Iq = I_s + (size_t)q * (C::I_BYTES / 8);
-                const double *Gq = G_s + q * C::oNERI;
-                double r[C::NACC];
+                const R *Iq = I_s + (size_t)q * (C::I_BYTES / C::RB);
+                const R *Gq = G_s + q * C::oNERI;
+                R ea[4];
 #pragma unroll
-                for (int k = 0; k < C::NACC; ++k) r[k] = 0.0;
+                for (int k = 0; k < 4; ++k) ea[k] = to_r<R>(2.0 * ex[k]);
+                // the thread's sums (in R; FP64 from the warp reduction on)
+                R r[C::NACC];
+#pragma unroll
+                for (int k = 0; k < C::NACC; ++k) r[k] = (R)0;
                 for (int it = tid; it < ITEMS; it += C::THREADS) {
                     const int mu = it / (3 * WN), rem = it % (3 * WN);
                     const int x = rem / WN;
@@ -189,7 +206,7 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                     w /= W3;
                     const int i1 = w % W2, i0 = w / W2;
                     const int y = x == 2 ? 0 : x + 1, z = x == 0 ? 2 : x - 1;
-                    double W = 0.0;
+                    R W = (R)0;
                     for (int ay = 0; ay <= C::oLa - i0; ++ay)
                         for (int by = 0; by <= C::oLb - i1; ++by)
                             for (int cy = 0; cy <= C::oLc - i2; ++cy)
@@ -206,7 +223,7 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                                     const int ib = (C::oLb - b0) * (C::oLb - b0 + 1) / 2 + (C::oLb - b0 - b1);
                                     const int ic = (C::oLc - c0) * (C::oLc - c0 + 1) / 2 + (C::oLc - c0 - c1);
                                     const int id = (C::oLd - d0) * (C::oLd - d0 + 1) / 2 + (C::oLd - d0 - d1);
-                                    const double g = Gq[ia * st0 + ib * st1 + ic * st2 + id * st3];
+                                    const R g = Gq[ia * st0 + ib * st1 + ic * st2 + id * st3];
                                     W = fma(g * gI<C>(Iq, y, mu, ay, by, cy, dy),
                                             gI<C>(Iq, z, mu, az, bz, cz, dz), W);
                                 }
@@ -214,21 +231,21 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
                     for (int k = 0; k < 4; ++k) {
                         const int nk = k == 0 ? i0 : (k == 1 ? i1 : (k == 2 ? i2 : i3));
                         const int e0 = (k == 0), e1 = (k == 1), e2 = (k == 2), e3 = (k == 3);
-                        const double up = gI<C>(Iq, x, mu, i0 + e0, i1 + e1, i2 + e2, i3 + e3);
-                        const double up2 = gI<C>(Iq, x, mu, i0 + 2 * e0, i1 + 2 * e1, i2 + 2 * e2, i3 + 2 * e3);
-                        const double dn = nk > 0 ? gI<C>(Iq, x, mu, i0 - e0, i1 - e1, i2 - e2, i3 - e3) : 0.0;
-                        const double t = W * (2.0 * ex[k] * up - nk * dn);
+                        const R up = gI<C>(Iq, x, mu, i0 + e0, i1 + e1, i2 + e2, i3 + e3);
+                        const R up2 = gI<C>(Iq, x, mu, i0 + 2 * e0, i1 + 2 * e1, i2 + 2 * e2, i3 + 2 * e3);
+                        const R dn = nk > 0 ? gI<C>(Iq, x, mu, i0 - e0, i1 - e1, i2 - e2, i3 - e3) : (R)0;
+                        const R t = W * (ea[k] * up - (R)nk * dn);
                         // r[k * 3 + x] with x known only at run time: select, no dynamic indexing
-                        r[k * 3 + 0] += x == 0 ? t : 0.0;
-                        r[k * 3 + 1] += x == 1 ? t : 0.0;
-                        r[k * 3 + 2] += x == 2 ? t : 0.0;
+                        r[k * 3 + 0] += x == 0 ? t : (R)0;
+                        r[k * 3 + 1] += x == 1 ? t : (R)0;
+                        r[k * 3 + 2] += x == 2 ? t : (R)0;
                         r[12 + k] -= W * up2;
                     }
                     if (x == 0) r[16] += W * gI<C>(Iq, 0, mu, i0, i1, i2, i3);
                 }
 #pragma unroll
                 for (int k = 0; k < C::NACC; ++k) {
-                    double v = r[k];
+                    double v = RTraits<R>::to_f64(r[k]);
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
                     if (lane == 0 && v != 0.0) atomicAdd(acc_s + q * C::NACC + k, v);
@@ -259,10 +276,10 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
     }
 }
 
-template <int La, int Lb, int Lc, int Ld>
+template <int La, int Lb, int Lc, int Ld, typename R = double>
 cudaError_t launch_backward(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
                             const double *G, double *dR, double *dalpha, cudaStream_t stream) {
-    using C = GCfg<La, Lb, Lc, Ld>;
+    using C = GCfg<La, Lb, Lc, Ld, R>;
     static_assert(C::SMEM <= 227 * 1024, "adjoint tile exceeds shared memory");
     if (args.nq <= 0) return cudaSuccess;
     auto kern = eri_backward_kernel<C>;

@@ -25,6 +25,9 @@
 // quartet's four shells are staged in FP32, and each thread takes (quartet, pass, x, y) items,
 // forms both sums in FP32, scales them by eps and adds them to J and K in FP64 (device
 // atomics, so the summation order of the FP64 accumulation varies between runs).
+#include <algorithm>
+#include <vector>
+
 #include "eri_internal.h"
 
 namespace eri {
@@ -32,7 +35,9 @@ namespace eri {
 namespace {
 
 constexpr int kDigestThreads = 256;
-constexpr int kDigestSmem = 48 * 1024;
+// dynamic shared memory of a tile: 47 KB, so that with the kernel's static shared memory (the
+// class parameters) a CTA stays within the 48 KB available without an opt-in
+constexpr int kDigestSmem = 47 * 1024;
 
 // the twelve D blocks (x, y), x != y, in x-major order
 __constant__ int c_bx[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
@@ -103,13 +108,39 @@ __device__ __forceinline__ void pass_coefs(int p, int m, int c[4]) {
 // destinations M[x][y], M[y][x] of an item receive equal totals over the whole sum, so each item
 // forms one sum and adds all of its coefficient to M[x][y] alone; the finished matrices are
 // symmetrised afterwards, M = (M + M^T) / 2 (symmetrise_kernel), which restores every entry.
+//
+// One launch covers every class: CTA b takes tile b - tile_start[c] of the class c with
+// tile_start[c] <= b < tile_start[c + 1] (the classes' parameters in `args`, copied to shared
+// memory by the CTA), so small classes do not leave the GPU idle between launches.
 template <bool SYM>
-__global__ void __launch_bounds__(kDigestThreads) digest_kernel(DigestArgs A) {
+__global__ void __launch_bounds__(kDigestThreads)
+digest_kernel(const DigestArgs *__restrict__ args, const long long *__restrict__ tile_start, int n_classes) {
     extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ DigestArgs A;
+    __shared__ long long tile_s;
+    if (threadIdx.x == 0) {
+        int lo = 0, hi = n_classes - 1;  // last class with tile_start <= blockIdx.x
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) / 2;
+            if (tile_start[mid] <= (long long)blockIdx.x)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        tile_s = ((long long)blockIdx.x - tile_start[lo]) | ((long long)lo << 40);
+    }
+    __syncthreads();
+    {
+        const int c = (int)(tile_s >> 40);
+        const int *src = reinterpret_cast<const int *>(args + c);
+        int *dst = reinterpret_cast<int *>(&A);
+        for (int i = threadIdx.x; i < (int)(sizeof(DigestArgs) / 4); i += kDigestThreads) dst[i] = src[i];
+    }
+    __syncthreads();
     int *meta = reinterpret_cast<int *>(smem);               // T x 8: bf offsets, mask, eps
     float *e_s = reinterpret_cast<float *>(meta + A.T * 8);  // T x neri codes
     float *d_s = e_s + (size_t)A.T * A.neri;                 // T x nD D values
-    const long long q0 = (long long)blockIdx.x * A.T;
+    const long long q0 = (tile_s & ((1LL << 40) - 1)) * A.T;
     const int tn = (int)((A.nq - q0) < A.T ? (A.nq - q0) : A.T);
     const int tid = threadIdx.x;
 
@@ -245,52 +276,72 @@ cudaError_t digest_symmetrise(double *M, long long n, cudaStream_t stream) {
     return cudaGetLastError();
 }
 
-cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, bool symmetric, const int *bfoff,
-                         const float *D32, long long nbf, double *J, double *K, cudaStream_t stream) {
-    if (c.nq <= 0) return cudaSuccess;
-    DigestArgs A{};
-    A.quartets = c.quartets;
-    A.nq = c.nq;
-    A.packed = c.packed;
-    A.scales = c.scales;
-    A.bfoff = bfoff;
-    A.D = D32;
-    A.nbf = nbf;
-    A.J = J;
-    A.K = K;
-    A.bits = bits;
-    A.unique8 = unique8 ? 1 : 0;
-    const int L[4] = {(c.cls >> 6) & 3, (c.cls >> 4) & 3, (c.cls >> 2) & 3, c.cls & 3};
-    for (int x = 0; x < 4; ++x) A.n[x] = ncart_d(L[x]);
-    A.st[3] = 1;
-    for (int x = 2; x >= 0; --x) A.st[x] = A.st[x + 1] * A.n[x + 1];
-    A.neri = A.st[0] * A.n[0];
-    int o = 0;
-    for (int b = 0; b < 16; ++b) {
-        const int x = b >> 2, y = b & 3;
-        A.boff[b] = o;
-        if (x != y) o += A.n[x] * A.n[y];
+size_t digest_table_bytes() { return 256 * sizeof(DigestArgs) + 257 * sizeof(long long); }
+
+cudaError_t digest_all(const DigestClass *classes, int n_classes, int bits, bool unique8, bool symmetric,
+                       const int *bfoff, const float *D32, long long nbf, double *J, double *K,
+                       void *d_table, cudaStream_t stream) {
+    if (n_classes <= 0) return cudaSuccess;
+    if (n_classes > 256) return cudaErrorInvalidValue;
+    std::vector<DigestArgs> args(n_classes);
+    std::vector<long long> start(n_classes + 1);
+    size_t smem_max = 0;
+    long long tiles = 0;
+    for (int k = 0; k < n_classes; ++k) {
+        const DigestClass &c = classes[k];
+        DigestArgs &A = args[k];
+        A = DigestArgs{};
+        A.quartets = c.quartets;
+        A.nq = c.nq;
+        A.packed = c.packed;
+        A.scales = c.scales;
+        A.bfoff = bfoff;
+        A.D = D32;
+        A.nbf = nbf;
+        A.J = J;
+        A.K = K;
+        A.bits = bits;
+        A.unique8 = unique8 ? 1 : 0;
+        const int L[4] = {(c.cls >> 6) & 3, (c.cls >> 4) & 3, (c.cls >> 2) & 3, c.cls & 3};
+        for (int x = 0; x < 4; ++x) A.n[x] = ncart_d(L[x]);
+        A.st[3] = 1;
+        for (int x = 2; x >= 0; --x) A.st[x] = A.st[x + 1] * A.n[x + 1];
+        A.neri = A.st[0] * A.n[0];
+        int o = 0;
+        for (int b = 0; b < 16; ++b) {
+            const int x = b >> 2, y = b & 3;
+            A.boff[b] = o;
+            if (x != y) o += A.n[x] * A.n[y];
+        }
+        A.nD = o;
+        const int bx[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
+        A.rstart[0] = 0;
+        for (int b = 0; b < 12; ++b) A.rstart[b + 1] = A.rstart[b] + A.n[bx[b]];
+        const int px[6] = {0, 2, 0, 1, 0, 1}, py[6] = {1, 3, 2, 2, 3, 3};
+        A.ioff[0] = 0;
+        for (int p = 0; p < 6; ++p) A.ioff[p + 1] = A.ioff[p] + A.n[px[p]] * A.n[py[p]];
+        A.NI = A.ioff[6];
+        const int perq = 4 * (8 + A.neri + A.nD);
+        int T = kDigestSmem / perq;
+        T = T < 1 ? 1 : (T > 128 ? 128 : T);
+        A.T = T;
+        if ((size_t)T * perq > (size_t)kDigestSmem) return cudaErrorInvalidValue;
+        smem_max = std::max(smem_max, (size_t)T * perq);
+        start[k] = tiles;
+        tiles += (c.nq + T - 1) / T;
     }
-    A.nD = o;
-    const int bx[12] = {0, 0, 0, 1, 1, 1, 2, 2, 2, 3, 3, 3};
-    A.rstart[0] = 0;
-    for (int b = 0; b < 12; ++b) A.rstart[b + 1] = A.rstart[b] + A.n[bx[b]];
-    const int px[6] = {0, 2, 0, 1, 0, 1}, py[6] = {1, 3, 2, 2, 3, 3};
-    A.ioff[0] = 0;
-    for (int p = 0; p < 6; ++p) A.ioff[p + 1] = A.ioff[p] + A.n[px[p]] * A.n[py[p]];
-    A.NI = A.ioff[6];
-    const int perq = 4 * (8 + A.neri + A.nD);
-    int T = kDigestSmem / perq;
-    T = T < 1 ? 1 : (T > 128 ? 128 : T);
-    A.T = T;
-    const size_t smem = (size_t)T * perq;
-    if (smem > (size_t)kDigestSmem) return cudaErrorInvalidValue;
-    const long long tiles = (c.nq + T - 1) / T;
+    start[n_classes] = tiles;
     if (tiles > 0x7fffffffLL) return cudaErrorInvalidValue;
+    DigestArgs *d_args = static_cast<DigestArgs *>(d_table);
+    long long *d_start = reinterpret_cast<long long *>(static_cast<char *>(d_table) + 256 * sizeof(DigestArgs));
+    cudaError_t e = cudaMemcpyAsync(d_args, args.data(), n_classes * sizeof(DigestArgs), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_start, start.data(), (n_classes + 1) * sizeof(long long), cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return e;
     if (symmetric)
-        digest_kernel<true><<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
+        digest_kernel<true><<<(unsigned)tiles, kDigestThreads, smem_max, stream>>>(d_args, d_start, n_classes);
     else
-        digest_kernel<false><<<(unsigned)tiles, kDigestThreads, smem, stream>>>(A);
+        digest_kernel<false><<<(unsigned)tiles, kDigestThreads, smem_max, stream>>>(d_args, d_start, n_classes);
     return cudaGetLastError();
 }
 

@@ -32,7 +32,11 @@ constexpr int kNumVariants = 3;
 // Launcher of one canonical class's adjoint kernel (FP64).
 using BackwardFn = cudaError_t (*)(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
                                    const double *G, double *dR, double *dalpha, cudaStream_t stream);
-void eri_register_backward(BackwardFn *table);
+// Each adjoint unit fills the FP64 and the mixed-precision table for its classes.
+void eri_register_backward_0(BackwardFn *table, BackwardFn *table_mixed);
+void eri_register_backward_1(BackwardFn *table, BackwardFn *table_mixed);
+void eri_register_backward_2(BackwardFn *table, BackwardFn *table_mixed);
+void eri_register_backward_3(BackwardFn *table, BackwardFn *table_mixed);
 
 // Each class translation unit fills table[cls * kNumVariants + variant] for its classes.
 constexpr int kNumTU = 16;
@@ -52,10 +56,14 @@ struct DigestClass {
 };
 // D (FP64, n values) rounded to FP32 into out.
 cudaError_t digest_density_f32(const double *D, long long n, float *out, cudaStream_t stream);
-// Adds the class's contributions to J and K (see eri_digest.cu); with `symmetric` (D symmetric)
-// each item adds to one of its two transposed destinations, and digest_symmetrise finishes.
-cudaError_t digest_class(const DigestClass &c, int bits, bool unique8, bool symmetric, const int *bfoff,
-                         const float *D32, long long nbf, double *J, double *K, cudaStream_t stream);
+// Bytes of the device table digest_all needs (per-class parameters and tile offsets).
+size_t digest_table_bytes();
+// Adds the contributions of the n_classes classes to J and K in one launch (see eri_digest.cu);
+// with `symmetric` (D symmetric) each item adds to one of its two transposed destinations, and
+// digest_symmetrise finishes.  d_table: digest_table_bytes() of device memory, written on `stream`.
+cudaError_t digest_all(const DigestClass *classes, int n_classes, int bits, bool unique8, bool symmetric,
+                       const int *bfoff, const float *D32, long long nbf, double *J, double *K,
+                       void *d_table, cudaStream_t stream);
 // M = (M + M^T) / 2 (n x n, row major).
 cudaError_t digest_symmetrise(double *M, long long n, cudaStream_t stream);
 

@@ -23,10 +23,14 @@ namespace {
 LaunchFn g_launch[256 * kNumVariants];
 KernelInfo g_info[256 * kNumVariants];
 BackwardFn g_backward[256];
+BackwardFn g_backward_mixed[256];
 std::once_flag g_launch_once;
 
 void register_all() {
-    eri_register_backward(g_backward);
+    eri_register_backward_0(g_backward, g_backward_mixed);
+    eri_register_backward_1(g_backward, g_backward_mixed);
+    eri_register_backward_2(g_backward, g_backward_mixed);
+    eri_register_backward_3(g_backward, g_backward_mixed);
     eri_register_tu_0(g_launch, g_info); eri_register_tu_1(g_launch, g_info);
     eri_register_tu_2(g_launch, g_info); eri_register_tu_3(g_launch, g_info);
     eri_register_tu_4(g_launch, g_info); eri_register_tu_5(g_launch, g_info);
@@ -207,6 +211,7 @@ struct eri_plan_s {
     int *d_bfoff = nullptr;      // first basis function of every shell
     long long n_bf = 0;          // basis functions (sum of the shells' Cartesian components)
     float *d_D32 = nullptr;      // FP32 copy of the density of eri_digest_jk (lazy)
+    void *d_digest = nullptr;    // per-class parameters of eri_digest_jk's launch (lazy)
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
     double *d_pairs = nullptr;    // primitive-pair table (n_prims^2 records), or null
     // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
@@ -251,6 +256,7 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_err);
     cudaFree(p->d_bfoff);
     cudaFree(p->d_D32);
+    cudaFree(p->d_digest);
     cudaFree(p->d_setup);
     cudaFree(p->d_pairs);
     cudaFree(p->d_counters);
@@ -1044,8 +1050,14 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
     if (reinterpret_cast<uintptr_t>(d_G) % 8 || reinterpret_cast<uintptr_t>(d_dR) % 8 ||
         reinterpret_cast<uintptr_t>(d_dalpha) % 8)
         return ERI_E_INVALID;
+    // the adjoint of a class runs in that class's precision: FP64, or FP32 recurrences with FP64
+    // geometry, roots and accumulation (the mixed adjoint)
+    auto backward_of = [&](int c) -> BackwardFn {
+        const int cc = canonicalise(c).cls;
+        return class_precision(plan, c) == ERI_FP64 ? g_backward[cc] : g_backward_mixed[cc];
+    };
     for (int c = 0; c < 256; ++c)
-        if (plan->count[c] > 0 && !g_backward[canonicalise(c).cls]) return ERI_E_UNSUPPORTED;
+        if (plan->count[c] > 0 && !backward_of(c)) return ERI_E_UNSUPPORTED;
     cudaSetDevice(plan->device);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_dR, 0, sizeof(double) * 3 * (size_t)plan->n_shells, st);
@@ -1063,7 +1075,7 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
         a.quartets = plan->d_quartets + plan->first[c];
         a.nq = plan->count[c];
         a.err = plan->d_err;
-        e = g_backward[cn.cls](sh, plan->tables, a, d_G + plan->fp64_off[c], d_dR, d_dalpha, st);
+        e = backward_of(c)(sh, plan->tables, a, d_G + plan->fp64_off[c], d_dR, d_dalpha, st);
         if (e != cudaSuccess) return cuda_status(e);
     }
     return ERI_OK;
@@ -1361,7 +1373,10 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
     if (plan->nq == 0) return ERI_OK;
     if (!plan->d_D32 && (e = cudaMalloc(&plan->d_D32, sizeof(float) * (size_t)n2)) != cudaSuccess)
         return cuda_status(e);
+    if (!plan->d_digest && (e = cudaMalloc(&plan->d_digest, digest_table_bytes())) != cudaSuccess)
+        return cuda_status(e);
     if ((e = digest_density_f32(d_D, n2, plan->d_D32, s)) != cudaSuccess) return cuda_status(e);
+    std::vector<DigestClass> dcs;
     size_t off = 0;
     for (int c = 0; c < 256; ++c) {
         const size_t seg = packed_segment_bytes(plan->count[c], class_neri(c), bits);
@@ -1372,12 +1387,13 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
             dc.nq = plan->count[c];
             dc.packed = reinterpret_cast<const uint32_t *>(static_cast<const char *>(d_packed) + off);
             dc.scales = d_scales + plan->first[c];
-            e = digest_class(dc, bits, (flags & ERI_DIGEST_UNIQUE8) != 0, sym, plan->d_bfoff, plan->d_D32,
-                             plan->n_bf, d_J, d_K, s);
-            if (e != cudaSuccess) return cuda_status(e);
+            dcs.push_back(dc);
         }
         off += seg;
     }
+    e = digest_all(dcs.data(), (int)dcs.size(), bits, (flags & ERI_DIGEST_UNIQUE8) != 0, sym, plan->d_bfoff,
+                   plan->d_D32, plan->n_bf, d_J, d_K, plan->d_digest, s);
+    if (e != cudaSuccess) return cuda_status(e);
     if (sym) {
         if ((e = digest_symmetrise(d_J, plan->n_bf, s)) != cudaSuccess) return cuda_status(e);
         if ((e = digest_symmetrise(d_K, plan->n_bf, s)) != cudaSuccess) return cuda_status(e);

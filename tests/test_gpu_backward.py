@@ -31,8 +31,8 @@ def to_sorted(plan, q, G, offs, pool):
     return np.concatenate([G[offs[i]:offs[i + 1]] for i in order])
 
 
-def gpu_grad(pool, q, G, offs):
-    plan = api.eri_plan_create(pool, q, precision="fp64")
+def gpu_grad(pool, q, G, offs, precision="fp64"):
+    plan = api.eri_plan_create(pool, q, precision=precision)
     Gs = torch.tensor(to_sorted(plan, q, G, offs, pool), device="cuda")
     dR = torch.empty((pool.n, 3), dtype=torch.float64, device="cuda")
     da = torch.empty(len(pool.exps), dtype=torch.float64, device="cuda")
@@ -85,7 +85,40 @@ def test_backward_matches_finite_differences_of_forward():
         assert abs(fd - da[j]) <= 1e-6 * max(1.0, abs(fd)), (j, fd, da[j])
 
 
+# The mixed adjoint (FP32 recurrences on the extended ranges, FP32 per-thread sums, FP64
+# geometry and accumulation) against the oracle derivative, relative to the largest gradient
+# component.
+MIXED_GRAD_TOL = 2e-5
+
+
+@pytest.mark.parametrize("K", [1, 3])
+def test_mixed_backward_matches_oracle(K):
+    pool, q, G, offs = workload(31 + K, K, 6 if K == 3 else 20)
+    dR, da = gpu_grad(pool, q, G, offs, "mixed")
+    rR, ra = oracle.eri_grad_batch(pool, q, G, offs)
+    assert np.max(np.abs(dR - rR)) <= MIXED_GRAD_TOL * np.abs(rR).max()
+    assert np.max(np.abs(da - ra)) <= MIXED_GRAD_TOL * np.abs(ra).max()
+
+
+def test_mixed_backward_with_f_shells():
+    """The mixed adjoint serves f shells (extended ranges up to L = 5 fit in shared memory in
+    FP32): s, p, d, f classes against the oracle derivative."""
+    rng = np.random.default_rng(71)
+    pool = W.random_contracted_pool(rng, 4, K=2, Ls=(0, 1, 2, 3))
+    cls = [(3, 0, 0, 0), (3, 1, 2, 0), (3, 3, 1, 1), (2, 3, 3, 2), (0, 3, 1, 3), (3, 3, 3, 3)]
+    q = np.concatenate([W.random_class_quartets(rng, c, 2, 4, Ls=(0, 1, 2, 3)) for c in cls])
+    sizes = oracle.quartet_sizes(pool, q)
+    offs = np.zeros(len(q) + 1, dtype=np.int64)
+    np.cumsum(sizes, out=offs[1:])
+    G = rng.standard_normal(int(offs[-1]))
+    dR, da = gpu_grad(pool, q, G, offs, "mixed")
+    rR, ra = oracle.eri_grad_batch(pool, q, G, offs)
+    assert np.max(np.abs(dR - rR)) <= MIXED_GRAD_TOL * np.abs(rR).max()
+    assert np.max(np.abs(da - ra)) <= MIXED_GRAD_TOL * np.abs(ra).max()
+
+
 def test_backward_rejects_f_shells():
+    """The FP64 adjoint does not serve f shells (the mixed one does)."""
     sh = W.make_shellset(np.zeros((4, 3)), [3, 1, 1, 1], [[1.0]] * 4, [[1.0]] * 4)
     plan = api.eri_plan_create(sh, np.array([[0, 1, 2, 3]], dtype=np.int32))
     G = torch.zeros(90, dtype=torch.float64, device="cuda")

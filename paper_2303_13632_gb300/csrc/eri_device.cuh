@@ -112,6 +112,67 @@ __device__ __forceinline__ R to_r(double v) {
         return v;
 }
 
+// Two-float numbers (value = h + l, |l| <= 2^-24 |h|): FP32 arithmetic with about 2^-46
+// relative precision, for the mixed setup's B and C values, whose differences cancel (C00 =
+// (P - A) - q x / (p + q) (P - Q) vanishes where the root-weighted centre meets A).
+struct F2 {
+    float h, l;
+};
+
+// Two-float form of an FP64 value with integer operations only: h is the value rounded to
+// FP32 (as f64_to_f32), l the rounding remainder d - h, formed from the 29 significand bits
+// that h drops (truncated to 24 bits).  h + l equals d to 2^-47 relative where h is a normal
+// FP32 number and the remainder is above the FP32 normal range (|d| >= 2^-74); otherwise l is
+// 0 and h alone stands for d.
+__device__ __forceinline__ F2 split_f2(double d) {
+    const unsigned int hi = (unsigned int)__double2hiint(d), lo = (unsigned int)__double2loint(d);
+    const unsigned int sign = hi & 0x80000000u, ahi = hi & 0x7FFFFFFFu;
+    const unsigned int e = ahi >> 20;
+    if (e - 897u > 253u) return {f64_to_f32(d), 0.0f};
+    const unsigned int t = __funnelshift_l(lo, ahi - (896u << 20), 3);
+    const unsigned int rem = lo & 0x1FFFFFFFu;
+    const unsigned int up = ((rem > 0x10000000u) | ((rem == 0x10000000u) & t)) & 1u;
+    const float h = __uint_as_float(sign | (t + up));
+    // d - h = r 2^(e - 1075) with r = rem (rounded down) or rem - 2^29 (rounded up)
+    const unsigned int m = up ? 0x20000000u - rem : rem;  // |r| <= 2^28
+    const unsigned int rsign = up ? (sign ^ 0x80000000u) : sign;
+    if (m == 0u) return {h, 0.0f};
+    const int p = 31 - __clz((int)m);  // leading one of |r|
+    const int ef = p + (int)e - 948;   // binary32 exponent field of |r| 2^(e - 1075)
+    if (ef < 1) return {h, 0.0f};
+    const unsigned int mant = p >= 23 ? m >> (p - 23) : m << (23 - p);
+    return {h, __uint_as_float(rsign | ((unsigned int)ef << 23) | (mant & 0x7FFFFFu))};
+}
+
+// a - b x: the product of the high parts is exact inside the first FMA and the cross terms
+// (a.l - b.h x.l - b.l x.h) enter as a correction; b.l x.l (2^-48 of b x) is dropped.  Error
+// below 2^-23 |a - b x| + 2^-46 (|a| + |b x|).
+__device__ __forceinline__ float tf_fms(F2 a, F2 b, F2 x) {
+    const float h = fmaf(-b.h, x.h, a.h);
+    float c = fmaf(-b.h, x.l, a.l);
+    c = fmaf(-b.l, x.h, c);
+    return __fadd_rn(h, c);
+}
+
+// a b (Dekker's product of the high parts through an FMA, plus the cross terms)
+__device__ __forceinline__ F2 tf_mul(F2 a, F2 b) {
+    const float p = __fmul_rn(a.h, b.h);
+    float e = fmaf(a.h, b.h, -p);
+    e = fmaf(a.h, b.l, e);
+    e = fmaf(a.l, b.h, e);
+    return {p, e};
+}
+
+// a + b (Knuth's two-sum of the high parts, plus the low parts)
+__device__ __forceinline__ F2 tf_add(F2 a, F2 b) {
+    const float s = __fadd_rn(a.h, b.h);
+    const float bb = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fsub_rn(b.h, bb));
+    return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+
+__device__ __forceinline__ F2 tf_neg(F2 a) { return {-a.h, -a.l}; }
+
 // Device addresses of the generated tables (see eri_tables.cu).
 struct Tables {
     const double *rys_poly;  // monomial coefficients of the Rys root/weight pieces

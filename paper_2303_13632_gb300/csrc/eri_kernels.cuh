@@ -157,6 +157,13 @@ struct Cfg {
     // are the largest at which ptxas reports no spill for these classes (8 CTAs = 64 registers
     // up to 6 outputs, 7 = 72 up to 10, 6 = 80 up to 18; larger classes keep their own count).
     // [ss|ss] measured 6% slower at 8 CTAs than with its own count and keeps it.
+    // the inline-setup FP32 kernels form B and C per root in two-float FP32 (SetupTF) from two
+    // roots on; with one root the FP64 evaluation is cheaper than the per-quartet splitting.
+    // [ds|ds] and [dp|ss] measured 14% and 3% slower with it (more registers, fewer resident
+    // CTAs) and keep the FP64 evaluation.
+    static constexpr bool TF_SLOWER = (La == 2 && Lb == 0 && Lc == 2 && Ld == 0) ||
+                                      (La == 2 && Lb == 1 && Lc == 0 && Ld == 0);
+    static constexpr bool SETUP_TF = sizeof(R) == 4 && NRYS >= 2 && !TF_SLOWER;
     static constexpr int TPQ_MINB = (TPQ_SMALL && sizeof(R) == 4)
                                         ? (NERI == 1 ? 1 : (NERI <= 6 ? 8 : (NERI <= 10 ? 7 : (NERI <= 18 ? 6 : 1))))
                                         : 1;
@@ -349,6 +356,93 @@ __device__ __forceinline__ void phase_setup(const Tables &tb, const double *geo,
             for (int s = 0; s < 3; ++s)
                 bc[C::S_CD + s] = to_r<R>((geo[G_QCX + s] + geo[G_CDX + s]) + fp * geo[G_PQX + s]);
         }
+    }
+}
+
+// Phase A1 of the mixed path for the roots of one (primitive) quartet computed by one thread:
+// the root-independent factors of the B and C values are formed once per quartet and split
+// into two-float form, so that each root costs FP32 work only:
+//   B00 = x / (2(p+q)),  B10 = 1/(2p) - a10 x,  B01 = 1/(2q) - a01 x,
+//   C00 = (P - A) - u x,  C00' = (Q - C) + v x,
+//   a10 = q / (2p(p+q)),  a01 = p / (2q(p+q)),  u = q (P - Q) / (p+q),  v = p (P - Q) / (p+q).
+// The differences that cancel are evaluated in two-float arithmetic, so the values keep the
+// accuracy of the FP64 evaluation (rounded once to FP32) up to 2^-23 of the value plus 2^-46
+// of the terms; the root x enters in two-float form as well.
+template <class C>
+struct SetupTF {
+    static constexpr bool BRA = C::NAB > 0, KET = C::NCD > 0;
+    static constexpr bool CB = C::DIRECT && C::Lb > 0, CD = C::DIRECT && C::Ld > 0;
+    float hq, pref;
+    F2 hip, a10, hiq, a01;
+    F2 pa[3], u[3], qc[3], nv[3], pb[3], qd[3];
+
+    __device__ __forceinline__ void init(const double *geo) {
+        pref = f64_to_f32(geo[G_PREF]);
+        if constexpr (BRA || KET) hq = 0.5f * f64_to_f32(geo[G_IPQ]);
+        const double ipq = geo[G_IPQ];
+        if constexpr (BRA) {
+            const F2 ip = split_f2(geo[G_IP]), fq = split_f2(geo[G_Q] * ipq);
+            hip = {0.5f * ip.h, 0.5f * ip.l};
+            a10 = tf_mul(hip, fq);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                pa[s] = split_f2(geo[G_PAX + s]);
+                u[s] = tf_mul(fq, split_f2(geo[G_PQX + s]));
+                if constexpr (CB) pb[s] = tf_add(pa[s], split_f2(geo[G_ABX + s]));
+            }
+        }
+        if constexpr (KET) {
+            const F2 iq = split_f2(geo[G_IQ]), fp = split_f2(geo[G_P] * ipq);
+            hiq = {0.5f * iq.h, 0.5f * iq.l};
+            a01 = tf_mul(hiq, fp);
+#pragma unroll
+            for (int s = 0; s < 3; ++s) {
+                qc[s] = split_f2(geo[G_QCX + s]);
+                nv[s] = tf_neg(tf_mul(fp, split_f2(geo[G_PQX + s])));
+                if constexpr (CD) qd[s] = tf_add(qc[s], split_f2(geo[G_CDX + s]));
+            }
+        }
+    }
+
+    // B and C of the root with x = t^2 and weight w (the slots of phase_setup; slots the class
+    // does not use are zero)
+    __device__ __forceinline__ void root(double xd, double w, float *bc) const {
+        bc[S_WZ] = pref * f64_to_f32(w);
+#pragma unroll
+        for (int f = S_B00; f < S_WZ; ++f) bc[f] = 0.0f;
+        if constexpr (BRA || KET) {
+            const F2 x = split_f2(xd);
+            if constexpr (BRA && KET) bc[S_B00] = hq * x.h;
+            if constexpr (BRA) {
+                bc[S_B10] = tf_fms(hip, a10, x);
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    bc[S_C0X + s] = tf_fms(pa[s], u[s], x);
+                    if constexpr (CB) bc[C::S_CB + s] = tf_fms(pb[s], u[s], x);
+                }
+            }
+            if constexpr (KET) {
+                bc[S_B01] = tf_fms(hiq, a01, x);
+#pragma unroll
+                for (int s = 0; s < 3; ++s) {
+                    bc[S_C1X + s] = tf_fms(qc[s], nv[s], x);
+                    if constexpr (CD) bc[C::S_CD + s] = tf_fms(qd[s], nv[s], x);
+                }
+            }
+        }
+    }
+};
+
+// Root mu of the quartet (Boys F_0 alone for L = 0), mixed evaluation, as in phase_setup.
+template <class C>
+__device__ __forceinline__ void root_mixed(const Tables &tb, double T, int mu, double &x, double &w) {
+    if constexpr (C::NAB + C::NCD == 0) {
+        double F0, F1;
+        boys_f01_mixed<false>(T, tb.boys_t01, tb.boys_t01_f, F0, F1);
+        w = F0;
+        x = 0.0;
+    } else {
+        rys_root<true>(tb, C::NRYS, mu, T, x, w);
     }
 }
 
@@ -849,10 +943,20 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
             }
             __syncthreads();
-            // A1: roots, weights, B and C per (quartet, root)
+            // A1: roots, weights, B and C per (quartet, root); the mixed path forms B and C in
+            // two-float FP32 exactly as the split path's setup kernel does
             for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
                 int q = it / C::NRYS, mu = it % C::NRYS;
-                phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * C::SN);
+                if constexpr (sizeof(R) == 4) {
+                    const double *geo = geo_s + q * G_N;
+                    SetupTF<C> pre;
+                    pre.init(geo);
+                    double x, w;
+                    root_mixed<C>(tb, geo[G_T], mu, x, w);
+                    pre.root(x, w, bc_s + (q * C::NRYS + mu) * C::SN);
+                } else {
+                    phase_setup<C>(tb, geo_s + q * G_N, mu, bc_s + (q * C::NRYS + mu) * C::SN);
+                }
             }
             __syncthreads();
         }
@@ -1066,12 +1170,26 @@ eri_setup_kernel(ShellsDev sh, Tables tb, ClassArgs args, typename C::R *out, lo
     o[5 * st] = to_r<R>(geo[G_CDZ]);
     o[6 * st] = to_r<R>(geo[G_SWAB]);
     o[7 * st] = to_r<R>(geo[G_SWCD]);
+    if constexpr (sizeof(R) == 4) {
+        SetupTF<C> pre;
+        pre.init(geo);
 #pragma unroll 1
-    for (int mu = 0; mu < C::NRYS; ++mu) {
-        R bc[C::SN];
-        phase_setup<C>(tb, geo, mu, bc);
+        for (int mu = 0; mu < C::NRYS; ++mu) {
+            double x, w;
+            root_mixed<C>(tb, geo[G_T], mu, x, w);
+            float bc[C::SN];
+            pre.root(x, w, bc);
 #pragma unroll
-        for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * st] = bc[f];
+            for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * st] = bc[f];
+        }
+    } else {
+#pragma unroll 1
+        for (int mu = 0; mu < C::NRYS; ++mu) {
+            R bc[C::SN];
+            phase_setup<C>(tb, geo, mu, bc);
+#pragma unroll
+            for (int f = 0; f < C::SN; ++f) o[(C::SETUP_GEO + mu * C::SN + f) * st] = bc[f];
+        }
     }
 }
 
@@ -1234,11 +1352,24 @@ __device__ __forceinline__ void tpq_tile(const ShellsDev &sh, const Tables &tb,
                 }
                 rg[RG_SWAB] = to_r<R>(geo[G_SWAB]);
                 rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
+                if constexpr (C::SETUP_TF) {
+                    SetupTF<C> pre;
+                    pre.init(geo);
 #pragma unroll 1
-                for (int mu = 0; mu < C::NRYS; ++mu) {
-                    R bc[C::SN];
-                    phase_setup<C>(tb, geo, mu, bc);
-                    tpq_root<C>(bc, rg, acc);
+                    for (int mu = 0; mu < C::NRYS; ++mu) {
+                        double x, w;
+                        root_mixed<C>(tb, geo[G_T], mu, x, w);
+                        R bc[C::SN];
+                        pre.root(x, w, bc);
+                        tpq_root<C>(bc, rg, acc);
+                    }
+                } else {
+#pragma unroll 1
+                    for (int mu = 0; mu < C::NRYS; ++mu) {
+                        R bc[C::SN];
+                        phase_setup<C>(tb, geo, mu, bc);
+                        tpq_root<C>(bc, rg, acc);
+                    }
                 }
             }
         }

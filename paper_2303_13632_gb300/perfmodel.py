@@ -3,7 +3,10 @@
 FLOPs are counted like arXiv 2303.13632 counts n_FLOPQ (Sec. III-A: add, multiply and
 divide count one each, an FMA two), per primitive quartet of the canonical class the kernel
 evaluates:
-  setup       40 + 20 n_Rys     Gaussian-product prefactors and B, C arrays       (FP64)
+  setup       40 + 20 n_Rys     Gaussian-product prefactors (40, FP64) and the B, C arrays
+                                (20 n_Rys: FP64 on the plain path; on the mixed path FP32 in
+                                two-float arithmetic where the class uses that setup, see
+                                two_float_setup, else FP64)
   roots       60 n_Rys          Rys roots/weights (done on the host in the paper) (FP64 on the
                                 plain path; 20 n_Rys FP64 + 40 n_Rys R on the mixed path)
   VRR         5 * 3 n_Rys * ((La+Lb+1)(Lc+Ld+1) - 1)                            (R)
@@ -14,10 +17,11 @@ R is FP64 on the plain path and FP32 on the mixed path.  Bytes per quartet: 16 i
 int32 shell ids; shell data is cache resident) and n_ERIQ * bits / 8 + 4 out (compressed) or
 8 n_ERIQ out (FP64).
 
-Peaks (GB300, 152 SMs at the 2070 MHz maximum clock): FP32 = 152 x 128 lanes x 2 x 2.07 GHz
-= 80.5 TFLOP/s; FP64 = 1.25 TFLOP/s (the nominal figure for this part).  A kernel with F64
-FP64 flops and F32 FP32 flops per quartet needs at least F64/P64 + F32/P32 seconds per
-quartet on the ALUs and bytes/BW on HBM; its roofline time is the larger of the two.
+Default peaks (GB300, 152 SMs at the 2070 MHz maximum clock): FP32 = 152 x 128 lanes x 2 x
+2.07 GHz = 80.5 TFLOP/s; FP64 = 1.25 TFLOP/s (the nominal figure for this part); the benchmark
+passes the FMA rates it measures instead.  A kernel with F64 FP64 flops and F32 FP32 flops per
+quartet needs at least F64/P64 + F32/P32 seconds per quartet on the ALUs and bytes/BW on HBM;
+its roofline time is the larger of the two.
 """
 from __future__ import annotations
 
@@ -39,24 +43,37 @@ def canonical(cls):
     return bra + ket
 
 
+def two_float_setup(cls) -> bool:
+    """Whether the mixed path forms the B, C arrays of class cls in two-float FP32 (the split
+    setup kernel of every class not on the inline-setup thread-per-quartet kernel, and those
+    inline kernels with two or more roots except [ds|ds] and [dp|ss])."""
+    c = canonical(cls)
+    n = sum(c) // 2 + 1
+    if kernel_form(c) != "tpq_inline":
+        return True
+    return n >= 2 and c not in ((2, 0, 2, 0), (2, 1, 0, 0))
+
+
 def flops_per_quartet(cls, precision: str = "fp64"):
     """(fp64_flops, rr_flops) per primitive quartet of class cls.  The root/weight evaluation
     (60 n) is FP64 on the plain path; the mixed path evaluates the polynomial terms beyond the
     fourth (and the Taylor terms of F_0/F_1 beyond the second) in FP32, a third / two thirds
-    split of the same 60 n, counted 20 n FP64 + 40 n in the recurrence type."""
+    split of the same 60 n, counted 20 n FP64 + 40 n in the recurrence type.  The B, C arrays
+    (20 n) count in the recurrence type where the mixed path forms them in two-float FP32."""
     La, Lb, Lc, Ld = canonical(cls)
     n = (La + Lb + Lc + Ld) // 2 + 1
     nab, ncd = La + Lb, Lc + Ld
     neri = ncart(La) * ncart(Lb) * ncart(Lc) * ncart(Ld)
     roots64 = 60 * n if precision == "fp64" else 20 * n
-    f64 = 40 + 20 * n + roots64
+    bc64 = 0 if precision != "fp64" and two_float_setup(cls) else 20 * n
+    f64 = 40 + bc64 + roots64
     vrr = 5 * 3 * n * ((nab + 1) * (ncd + 1) - 1)
     hrr_bra = sum((nab - j + 1) * (ncd + 1) for j in range(1, Lb + 1))
     hrr_ket = (La + 1) * (Lb + 1) * sum(ncd - l + 1 for l in range(1, Ld + 1))
     hrr = 2 * 3 * n * (hrr_bra + hrr_ket)
     quad = 3 * n * neri
     comp = 2 * neri + 1
-    return f64, vrr + hrr + quad + comp + (60 * n - roots64)
+    return f64, vrr + hrr + quad + comp + (60 * n - roots64) + (20 * n - bc64)
 
 
 def bytes_per_quartet(cls, bits: int) -> int:

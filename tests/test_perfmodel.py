@@ -44,12 +44,23 @@ def test_canonical_classes():
 
 
 def test_mixed_split_keeps_the_total():
-    """The mixed path moves two thirds of the root evaluation to the recurrence type; the total
-    count per quartet is the same as the plain path's."""
-    for cls in [(0, 0, 0, 0), (1, 1, 1, 1), (3, 2, 1, 0), (3, 3, 3, 3)]:
+    """The mixed path moves two thirds of the root evaluation to the recurrence type, and the B,
+    C arrays where it forms them in two-float FP32; the total count per quartet is the same as
+    the plain path's."""
+    for cls in [(0, 0, 0, 0), (1, 0, 0, 0), (2, 0, 2, 0), (1, 0, 1, 0), (1, 1, 1, 1), (3, 2, 1, 0),
+                (3, 3, 3, 3)]:
         a, b = P.flops_per_quartet(cls, "fp64"), P.flops_per_quartet(cls, "mixed")
         n = sum(cls) // 2 + 1
-        assert sum(a) == sum(b) and a[0] - b[0] == 40 * n
+        moved = 40 * n + (20 * n if P.two_float_setup(cls) else 0)
+        assert sum(a) == sum(b) and a[0] - b[0] == moved
+
+
+def test_two_float_setup_classes():
+    """Inline-setup classes with one root keep the FP64 B, C; split-path classes use two-float."""
+    assert not P.two_float_setup((0, 0, 0, 0)) and not P.two_float_setup((1, 0, 0, 0))
+    assert not P.two_float_setup((2, 0, 2, 0)) and not P.two_float_setup((0, 0, 1, 2))
+    assert P.two_float_setup((1, 0, 1, 0)) and P.two_float_setup((3, 0, 1, 0))
+    assert P.two_float_setup((2, 1, 1, 0)) and P.two_float_setup((3, 3, 3, 3))
 
 
 def test_roofline_time_is_the_larger_bound():

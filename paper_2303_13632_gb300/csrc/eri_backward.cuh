@@ -70,9 +70,9 @@ __device__ __forceinline__ typename C::R gI(const typename C::R *Iq, int xi, int
 }
 
 template <class C>
-__global__ void __launch_bounds__(C::THREADS)
-eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__restrict__ G,
-                    double *__restrict__ dR, double *__restrict__ dalpha) {
+__device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables &tb,
+                                              const ClassArgs &args, const double *__restrict__ G,
+                                              double *__restrict__ dR, double *__restrict__ dalpha) {
     using R = typename C::R;
     extern __shared__ __align__(16) unsigned char smem[];
     double *geo_s = reinterpret_cast<double *>(smem + C::OFF_GEO);
@@ -276,13 +276,36 @@ eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__res
     }
 }
 
+template <class C>
+__global__ void __launch_bounds__(C::THREADS)
+eri_backward_kernel(ShellsDev sh, Tables tb, ClassArgs args, const double *__restrict__ G,
+                    double *__restrict__ dR, double *__restrict__ dalpha) {
+    backward_tile<C>(sh, tb, args, G, dR, dalpha);
+}
+
+// The same for the mixed adjoint of classes with an f shell, compiled for one resident CTA per
+// SM: under the default bound ptxas caps some of them at 128 registers with large spills, and
+// [ff|pp] then returned wrong exponent gradients for its first centre (the emulated kernel
+// arithmetic and the oracle agree); with the whole register file available none spills.
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
+eri_backward_kernel_wide(ShellsDev sh, Tables tb, ClassArgs args, const double *__restrict__ G,
+                         double *__restrict__ dR, double *__restrict__ dalpha) {
+    backward_tile<C>(sh, tb, args, G, dR, dalpha);
+}
+
 template <int La, int Lb, int Lc, int Ld, typename R = double>
 cudaError_t launch_backward(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
                             const double *G, double *dR, double *dalpha, cudaStream_t stream) {
     using C = GCfg<La, Lb, Lc, Ld, R>;
     static_assert(C::SMEM <= 227 * 1024, "adjoint tile exceeds shared memory");
     if (args.nq <= 0) return cudaSuccess;
-    auto kern = eri_backward_kernel<C>;
+    constexpr bool wide = sizeof(R) == 4 && (La == 3 || Lb == 3 || Lc == 3 || Ld == 3);
+    void (*kern)(ShellsDev, Tables, ClassArgs, const double *, double *, double *);
+    if constexpr (wide)
+        kern = eri_backward_kernel_wide<C>;
+    else
+        kern = eri_backward_kernel<C>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     if (e != cudaSuccess) return e;
     long long grid = (args.nq + C::Q - 1) / C::Q;

@@ -5,7 +5,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2303_13632_gb300 import api, workloads as W
+from paper_2303_13632_gb300 import api, perfmodel as P, workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -115,6 +115,26 @@ def test_mixed_backward_with_f_shells():
     rR, ra = oracle.eri_grad_batch(pool, q, G, offs)
     assert np.max(np.abs(dR - rR)) <= MIXED_GRAD_TOL * np.abs(rR).max()
     assert np.max(np.abs(da - ra)) <= MIXED_GRAD_TOL * np.abs(ra).max()
+
+
+def test_mixed_backward_every_class():
+    """Every canonical class (s to f, primitive shells, three quartets each) through the mixed
+    adjoint against the oracle derivative."""
+    rng = np.random.default_rng(5)
+    pool = W.random_primitive_pool(rng, 6)
+    canon = sorted({P.canonical((a, b, c, d)) for a in range(4) for b in range(4) for c in range(4)
+                    for d in range(4)})
+    assert len(canon) == 55
+    for cls in canon:
+        q = W.random_class_quartets(rng, cls, 3, 6)
+        sizes = oracle.quartet_sizes(pool, q)
+        offs = np.zeros(len(q) + 1, dtype=np.int64)
+        np.cumsum(sizes, out=offs[1:])
+        G = rng.standard_normal(int(offs[-1]))
+        rR, ra = oracle.eri_grad_batch(pool, q, G, offs)
+        dR, da = gpu_grad(pool, q, G, offs, "mixed")
+        assert np.max(np.abs(dR - rR)) <= MIXED_GRAD_TOL * np.abs(rR).max(), cls
+        assert np.max(np.abs(da - ra)) <= MIXED_GRAD_TOL * np.abs(ra).max(), cls
 
 
 def test_backward_rejects_f_shells():

@@ -685,6 +685,77 @@ def run_lattice(args):
     print(json.dumps(out), flush=True)
 
 
+def run_gshell(args):
+    """Classes with a g shell (L = 4, beyond the paper's s..f): the 369 classes, one run-time-L
+    kernel per precision.  Primitive shells from a pool of 2048 per L (centres U[-3,3]^3 bohr,
+    exponents log-U[0.1,10]), round(2^24 / n_ERIQ) quartets per class, 16-bit output, one class
+    per call; per class one sampled quartet against the oracle (decompressed error and the FP32
+    error of the mixed path relative to b_max)."""
+    import torch
+
+    import oracle
+    from paper_2303_13632_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    Ls = (0, 1, 2, 3, 4)
+    rng = np.random.default_rng(2303_13632 + 6)
+    pool = W.random_primitive_pool(rng, 2048, Ls=Ls)
+    ids = W.g_class_ids()
+    res, acc = {}, {}
+    t = {"mixed": 0.0, "fp64": 0.0}
+    total = 0
+    for c in ids:
+        cls = W.class_of_id(c)
+        neri = W.quartet_size(*cls)
+        n = int(round(2 ** 24 / neri))
+        q = W.random_class_quartets(rng, cls, n, 2048, Ls=Ls)
+        plan = api.eri_plan_create(pool, q, precision="mixed")
+        nb, sb = api.eri_output_bytes(plan, BITS)
+        packed = torch.empty(nb // 4, dtype=torch.int32, device=dev)
+        scales = torch.empty(sb // 4, dtype=torch.float32, device=dev)
+        ms = {}
+        for prec in ("mixed", "fp64"):
+            api.eri_plan_set_precision(plan, prec)
+            ms[prec] = _events(torch, stream, lambda: api.eri_compute_compressed(plan, BITS, packed, scales, stream))
+            t[prec] += ms[prec]
+        api.eri_sync(plan, stream)
+        total += n * neri
+        res[fmt_class(cls)] = {"mixed": n * neri / ms["mixed"] / 1e6, "fp64": n * neri / ms["fp64"] / 1e6}
+        if not args.no_check:
+            order = api.eri_plan_quartet_order(plan)
+            ref, _ = oracle.eri_batch(pool, q[order[:1]])
+            api.eri_plan_set_precision(plan, "mixed")
+            fp = torch.empty(neri, dtype=torch.float64, device=dev)
+            sub = api.eri_plan_create(pool, q[order[:1]], precision="mixed")
+            api.eri_compute(sub, fp, stream)
+            api.eri_compute_compressed(plan, BITS, packed, scales, stream)
+            api.eri_sync(plan, stream)
+            words = packed[: (neri * BITS + 31) // 32 + 1].cpu().numpy().view(np.uint32)
+            x = oracle.unpack_bits(words, neri, BITS) * float(scales[0].item())
+            bmax = float(np.max(np.abs(ref)))
+            # quartets with b_max <= 1e-30 Ha leave the FP32 range in the recurrences (as in the
+            # calibration); their relative FP32 error is not reported
+            acc[fmt_class(cls)] = {"decompressed_max_abs_err": float(np.max(np.abs(x - ref))),
+                                   "half_step": float(scales[0].item()) / 2,
+                                   "b_max": bmax,
+                                   "fp32_err_rel_bmax": float(np.max(np.abs(fp.cpu().numpy() - ref))) / bmax if bmax > 1e-30 else None}
+            sub.destroy()
+        plan.destroy()
+    out = {"impl": "ours", "workload": "gshell", "metric": "GERIS, classes with a g shell, 16-bit",
+           "value": total / (t["mixed"] * 1e-3) / 1e9, "unit": "GERIS", "fp64_value": total / (t["fp64"] * 1e-3) / 1e9,
+           "classes": len(ids), "eris": total, "quartets_per_class": "round(2^24 / n_ERIQ)",
+           "per_class_geris": res}
+    if acc:
+        out["max_decompressed_err_16bit"] = max(v["decompressed_max_abs_err"] for v in acc.values())
+        out["classes_within_one_step"] = sum(v["decompressed_max_abs_err"] <= 2 * v["half_step"] * (1 + 1e-5)
+                                             for v in acc.values())
+        out["max_fp32_err_rel_bmax"] = max(v["fp32_err_rel_bmax"] for v in acc.values() if v["fp32_err_rel_bmax"] is not None)
+        out["accuracy_per_class"] = acc
+    print(json.dumps(out), flush=True)
+
+
 def run_molecule(args):
     """Batched mixed workload: 200 atoms in a 20-bohr box (min separation 1.8 bohr), shells
     s, s, p, p, d, f per atom, contraction degree 1..6.  The library enumerates the 8-fold unique
@@ -853,7 +924,7 @@ def run_gradient(args):
 
 
 def fmt_class(cls):
-    s = "spdf"
+    s = "spdfg"
     return f"[{s[cls[0]]}{s[cls[1]]}|{s[cls[2]]}{s[cls[3]]}]"
 
 
@@ -863,7 +934,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "lattice", "molecule", "gradient"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "lattice", "molecule", "gradient", "gshell"],
                     help="sweep (default): the 256-class benchmark; the others are further studies")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--ref-eris", type=int, default=1500000)
@@ -884,6 +955,8 @@ def main():
         run_molecule(args)
     elif args.workload == "gradient":
         run_gradient(args)
+    elif args.workload == "gshell":
+        run_gshell(args)
     else:
         run_ours(args)
 

@@ -5,7 +5,7 @@
  *
  * What is computed (paper section in brackets):
  *   [ab|cd] = int int g_a(r) g_b(r) g_c(r') g_d(r') / |r - r'| dr dr'          (Sec. II-B, Eq. 1)
- * for Cartesian Gaussian shells with L <= 3 (s, p, d, f; Sec. II-A), contracted over
+ * for Cartesian Gaussian shells with L <= 4 (s, p, d, f as in Sec. II-A, and g), contracted over
  * primitives, by Rys quadrature (Sec. II-C): Boys function / Rys roots and weights,
  * setup of B and C, vertical recurrence (Eq. 6), horizontal recurrence (Eq. 7) and
  * quadrature (Eq. 8); optionally compressed per quartet into n-bit integers with one
@@ -21,7 +21,12 @@
  *     fastest.  (The FPGA loop order of the paper's Fig. 2 is d, c outer with b, a unrolled;
  *     that is a hardware choice and does not change the values.)
  *   - Class id of a quartet of shells with angular momenta (La, Lb, Lc, Ld):
- *     ((La*4 + Lb)*4 + Lc)*4 + Ld, 0..255 (the 256 generic classes of Sec. III-A).
+ *     ((La*4 + Lb)*4 + Lc)*4 + Ld, 0..255, for the 256 generic classes of Sec. III-A (every
+ *     L <= 3); 256 + ((La*5 + Lb)*5 + Lc)*5 + Ld for the 369 classes with a g shell (L = 4).
+ *     Ids below ERI_NUM_CLASS_IDS that match neither rule (256 + ... with every L <= 3) are not
+ *     classes.  Classes with a g shell are computed by one kernel whose angular momenta are
+ *     run-time values (the others by kernels specialised per canonical class); their
+ *     compressed output goes through a scratch buffer of FP64 values.
  *   - Output order: quartets sorted by class id (ascending), stable within a class (the
  *     order of the caller's list); eri_plan_quartet_order returns the permutation.
  *   - Pointers named d_* are device pointers on the plan's device; every other pointer is
@@ -44,9 +49,12 @@ extern "C" {
 
 typedef struct eri_plan_s *eri_plan_t;
 
+/* Number of class ids (see the class-id rule above): per-class loops run over 0..880. */
+#define ERI_NUM_CLASS_IDS 881
+
 typedef enum {
     ERI_OK = 0,
-    ERI_E_INVALID = 1,     /* bad argument: null pointer, L > 3, alpha <= 0, non-finite input,
+    ERI_E_INVALID = 1,     /* bad argument: null pointer, L < 0, alpha <= 0, non-finite input,
                               shell id out of range, bitwidth outside 2..24, wrong class */
     ERI_E_UNSUPPORTED = 2, /* valid request this build does not serve */
     ERI_E_NOMEM = 3,       /* device or host allocation failed */
@@ -148,7 +156,7 @@ eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);
 
 /* Precision of one class, overriding the plan's (ERI_FP64, ERI_MIXED, or -1 to follow the plan).
  * Host only (drops the cached graph of eri_compute_compressed_batched); ERI_E_INVALID for a NULL
- * plan, cls outside 0..255 or another value. */
+ * plan, cls not a class id or another value. */
 eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision);
 
 /* Chooses the precision of every class of the plan for `bits`-bit output: FP32 recurrences
@@ -170,13 +178,13 @@ eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *pre
 /* Kernel launches eri_compute_class / eri_compute_compressed_class make for class cls in its
  * current precision: 1 for the fused kernels, 2 per chunk of 2^20 quartets (setup and
  * recurrence kernels) on the split path of primitive plans, 0 for an empty class.
- * ERI_E_INVALID for a NULL plan or output, or cls outside 0..255. */
+ * ERI_E_INVALID for a NULL plan or output, or cls not a class id. */
 eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches);
 
 /* Names of the kernel instantiation(s) eri_compute_compressed_class launches for class cls in
  * its current precision (for reports that group time by kernel, e.g. "eri_setup_kernel<Cfg<2, 1,
  * 1, 0, float>> + eri_class_kernel<Cfg<2, 1, 1, 0, float>, 0, 1>"), NUL-terminated into buf of
- * len bytes.  Host only; ERI_E_INVALID for a NULL plan or buffer, cls outside 0..255 or a buffer
+ * len bytes.  Host only; ERI_E_INVALID for a NULL plan or buffer, cls not a class id or a buffer
  * too short. */
 eri_status_t eri_plan_class_kernels(eri_plan_t plan, int32_t cls, char *buf, size_t len);
 
@@ -188,7 +196,7 @@ eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n_quartets);
  *   n_eri_per_quartet   n_ga n_gb n_gc n_gd (Sec. II-A shell sizes)
  *   first_quartet       index of the class's first quartet in class-sorted order
  *   fp64_offset         offset (in doubles) of the class's first ERI in eri_compute's output
- * Host only; ERI_E_INVALID for a NULL plan or cls outside 0..255. */
+ * Host only; ERI_E_INVALID for a NULL plan or cls not a class id. */
 eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quartets,
                                  int32_t *n_eri_per_quartet, int64_t *first_quartet,
                                  int64_t *fp64_offset);
@@ -224,7 +232,7 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
  * n_eri + index-in-quartet) occupies stream bits [v*bits, (v+1)*bits), stream bit s being
  * bit s%32 of 32-bit word s/32.  For bits = 8 and 16 this is a plain int8/int16 array.
  * Bits past the class's last field up to the segment end are zero.  Host only; ERI_E_INVALID
- * for a NULL plan, bits outside 2..24 or cls outside 0..255.  Either output may be NULL. */
+ * for a NULL plan, bits outside 2..24 or cls not a class id.  Either output may be NULL. */
 eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                      size_t *byte_offset, size_t *bytes);
 
@@ -236,14 +244,15 @@ eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
  * 32-bit word s/32 (little-endian, least significant bit first, as the dense stream; the paper
  * does not fix the bit order).  Quartets are class-sorted as everywhere else; class segments
  * follow each other without gaps (each is a whole number of chunks).
- * Byte range of class `cls` in that layout; cls = 256 gives the total size in *byte_offset.
+ * Byte range of class `cls` in that layout; cls = ERI_NUM_CLASS_IDS gives the total size in
+ * *byte_offset.
  * bits 2..24; ERI_E_INVALID otherwise.  Host only. */
 eri_status_t eri_paper512_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                        size_t *byte_offset, size_t *bytes);
 
 /* Re-lays the packed output of eri_compute_compressed (d_packed, layout of
  * eri_packed_class_offset, read only) into the chunk layout above (d_chunks, written in full:
- * eri_paper512_class_offset(plan, bits, 256) bytes).  Integer copy on the GPU, asynchronous on
+ * eri_paper512_class_offset(plan, bits, ERI_NUM_CLASS_IDS) bytes).  Integer copy on the GPU, asynchronous on
  * `stream`; both pointers device memory, 4-byte aligned, not overlapping.  The scales are
  * unchanged (one eps per quartet, as written by eri_compute_compressed). */
 eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_packed, void *d_chunks,
@@ -252,7 +261,7 @@ eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_pack
 /* Same as eri_pack_paper512 for one dense stream without a plan: d_stream holds n_quartets *
  * n_eri n-bit fields, quartet after quartet, as the dense stream above (at least
  * ceil(n_quartets * n_eri * bits / 32) 32-bit words); d_chunks receives n_quartets * n_CS * 64
- * bytes.  n_eri 1..10000, bits 2..24, device pointers 4-byte aligned; ERI_E_INVALID
+ * bytes.  n_eri 1..50625, bits 2..24, device pointers 4-byte aligned; ERI_E_INVALID
  * otherwise, ERI_E_CUDA if a launch fails.  n_quartets = 0 does nothing. */
 eri_status_t eri_pack_paper512_stream(const void *d_stream, int64_t n_quartets, int32_t n_eri,
                                       int32_t bits, void *d_chunks, void *stream);
@@ -303,7 +312,9 @@ eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t 
  * dynamically), the classes spread over four streams forked from `stream`, the whole sequence
  * captured once into a CUDA graph and replayed on later calls with the same bits, precision
  * and output pointers.  The tile counters are plan-owned device memory.  The launch choice per
- * class (kernel family and grid) comes from eri_autotune when it has run.  Asynchronous. */
+ * class (kernel family and grid) comes from eri_autotune when it has run.  Classes with a g
+ * shell run their plain (non-persistent) launches, all on the first of the four streams since
+ * they share the plan's scratch buffer; eri_autotune leaves them out.  Asynchronous. */
 eri_status_t eri_compute_compressed_batched(eri_plan_t plan, int32_t bits, void *d_packed,
                                             float *d_scales, void *stream);
 
@@ -330,7 +341,7 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
  * ERI_E_UNSUPPORTED before any device work); ERI_MIXED with the 2-D integrals on the extended
  * ranges by the FP32 four-index recursion, G rounded to FP32, the per-thread sums in FP32 and
  * the geometry, roots, B and C (rounded once), the per-primitive accumulation and both outputs
- * in FP64, for every class up to f.  Both outputs are zeroed and then accumulated on `stream`
+ * in FP64, for every class up to f.  Plans with a g shell return ERI_E_UNSUPPORTED.  Both outputs are zeroed and then accumulated on `stream`
  * (device atomics: summation order, hence the last bits, can vary between runs). */
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
                           void *stream);
@@ -379,8 +390,8 @@ eri_status_t eri_plan_num_basis_functions(eri_plan_t plan, int64_t *n_bf);
  * and a small table of per-class launch parameters (allocated on the first call, the table
  * copied from host memory on `stream` at every call: one launch covers every class).  Asynchronous on `stream`.  ERI_E_INVALID for a NULL plan, bits
  * outside 2..24, unknown flags, ERI_DIGEST_SYMMETRIC without ERI_DIGEST_UNIQUE8, NULL buffers
- * where the plan needs them, or buffers not aligned to their element size; ERI_E_NOMEM /
- * ERI_E_CUDA from allocation or launch failures. */
+ * where the plan needs them, or buffers not aligned to their element size; ERI_E_UNSUPPORTED
+ * for plans with a g shell; ERI_E_NOMEM / ERI_E_CUDA from allocation or launch failures. */
 eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, const float *d_scales,
                            const double *d_D, double *d_J, double *d_K, int32_t flags, void *stream);
 
@@ -390,7 +401,8 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
 #define ERI_NOALLOC_MAX_QUARTETS 16384
 
 /* FP64 (precision ERI_FP64) or mixed-precision (ERI_MIXED) ERIs of quartets that all belong
- * to generic class `cls`, written in eri_compute's per-quartet layout (row major, a slowest),
+ * to generic class `cls` (a class without a g shell: ERI_E_UNSUPPORTED otherwise), written in
+ * eri_compute's per-quartet layout (row major, a slowest),
  * for callers that cannot let a library allocate device memory: applications that reserve the
  * device memory themselves and sub-allocate from their own pool, or code that must not risk
  * the synchronisation an allocation call can cause.  This function calls no cudaMalloc,

@@ -27,6 +27,7 @@ ERI_UNIQUE8 = 2
 ERI_QUARTETS_ON_DEVICE = 1
 ERI_NO_PAIR_TABLE = 2
 ERI_NOALLOC_MAX_QUARTETS = 16384
+ERI_NUM_CLASS_IDS = 881
 ERI_DIGEST_UNIQUE8 = 1
 ERI_DIGEST_ACCUMULATE = 2
 ERI_DIGEST_SYMMETRIC = 4

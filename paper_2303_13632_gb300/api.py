@@ -195,8 +195,8 @@ def eri_packed_class_offset(plan: Plan, bits: int, cls: int):
 
 
 def eri_paper512_class_offset(plan: Plan, bits: int, cls: int):
-    """(byte offset, bytes) of class `cls` in the paper's 512-bit chunk layout; cls = 256 gives
-    (total bytes, 0)."""
+    """(byte offset, bytes) of class `cls` in the paper's 512-bit chunk layout; cls =
+    ERI_NUM_CLASS_IDS gives (total bytes, 0)."""
     a, b = ctypes.c_size_t(), ctypes.c_size_t()
     check(_lib.load().eri_paper512_class_offset(plan.handle, bits, cls, ctypes.byref(a), ctypes.byref(b)),
           "eri_paper512_class_offset")

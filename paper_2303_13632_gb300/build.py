@@ -51,7 +51,8 @@ def _units():
              ("eri_noalloc", "eri_noalloc.cu", []),
              ("eri_layout", "eri_layout.cu", []),
              ("eri_digest", "eri_digest.cu", []),
-             ("eri_screen", "eri_screen.cu", [])]
+             ("eri_screen", "eri_screen.cu", []),
+             ("eri_generic", "eri_generic.cu", [])]
     for k in range(NUM_TU):
         units.append((f"eri_classes_{k}", "eri_classes.cu", [f"-DERI_TU={k}"]))
     for k in range(4):

@@ -422,12 +422,14 @@ __device__ __forceinline__ void rys_root(const Tables &tb, int n, int mu, double
 __host__ __device__ constexpr int ncart(int L) { return (L + 1) * (L + 2) / 2; }
 
 // Cartesian components (a_x, a_y, a_z) of index idx in a shell of angular momentum L.
-static __constant__ int c_cart[4][10][3] = {
+static __constant__ int c_cart[5][15][3] = {
     {{0, 0, 0}},
     {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}},
     {{2, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 2, 0}, {0, 1, 1}, {0, 0, 2}},
     {{3, 0, 0}, {2, 1, 0}, {2, 0, 1}, {1, 2, 0}, {1, 1, 1}, {1, 0, 2}, {0, 3, 0}, {0, 2, 1},
-     {0, 1, 2}, {0, 0, 3}}};
+     {0, 1, 2}, {0, 0, 3}},
+    {{4, 0, 0}, {3, 1, 0}, {3, 0, 1}, {2, 2, 0}, {2, 1, 1}, {2, 0, 2}, {1, 3, 0}, {1, 2, 1},
+     {1, 1, 2}, {1, 0, 3}, {0, 4, 0}, {0, 3, 1}, {0, 2, 2}, {0, 1, 3}, {0, 0, 4}}};
 
 // Cartesian component of index idx in a shell of angular momentum L (order: a_x from L
 // down to 0, then a_y from L - a_x down to 0).

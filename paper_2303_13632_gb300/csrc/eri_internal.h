@@ -15,6 +15,48 @@ cudaError_t tables_for_current_device(Tables *out);
 // FP32 copies of the table parts the mixed-precision setup reads (eri_tables.cu).
 void mixed_table_copies(std::vector<float> &tail_m, std::vector<float> &t01_f);
 
+// Class ids.  Classes without a g shell keep the ids of the 256 classes of Sec. III-A,
+// ((La*4 + Lb)*4 + Lc)*4 + Ld; classes with a g shell (L = 4) take 256 + ((La*5 + Lb)*5 + Lc)*5
+// + Ld.  The slots 256 + ... whose four angular momenta are all <= 3 are never used, so a plan's
+// per-class arrays have kNumClassIds entries of which 625 can be non-empty.
+constexpr int kLmax = 4;
+constexpr int kNumClassIds = 256 + 625;
+__host__ __device__ inline int class_id_of(int La, int Lb, int Lc, int Ld) {
+    if (La < 4 && Lb < 4 && Lc < 4 && Ld < 4) return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld;
+    return 256 + ((La * 5 + Lb) * 5 + Lc) * 5 + Ld;
+}
+__host__ __device__ inline void class_ls(int cls, int L[4]) {
+    if (cls < 256) {
+        L[0] = (cls >> 6) & 3; L[1] = (cls >> 4) & 3; L[2] = (cls >> 2) & 3; L[3] = cls & 3;
+    } else {
+        int r = cls - 256;
+        L[3] = r % 5; r /= 5;
+        L[2] = r % 5; r /= 5;
+        L[1] = r % 5; L[0] = r / 5;
+    }
+}
+// true for the ids of actual classes (0..255 and the slots with a g shell)
+inline bool class_id_valid(int cls) {
+    if (cls < 0 || cls >= kNumClassIds) return false;
+    if (cls < 256) return true;
+    int L[4];
+    class_ls(cls, L);
+    return L[0] == 4 || L[1] == 4 || L[2] == 4 || L[3] == 4;
+}
+inline bool class_has_g(int cls) { return cls >= 256; }
+
+// Classes with a g shell run one kernel whose angular momenta are run-time values
+// (eri_generic.cu): L = the canonical angular momenta, a the canonical class's arguments (its
+// quartets, permutation, output strides and output).  FP64 output is written to a.out_fp64;
+// compressed output goes through `scratch` (scratch_bytes of device memory, FP64 values of up to
+// scratch_bytes / (8 n_ERIQ) quartets at a time).  mixed: FP32 recurrences and quadrature from
+// FP64 setup values, FP64 sums over primitives.
+cudaError_t launch_generic(const ShellsDev &sh, const Tables &tb, const ClassArgs &a, const int L[4],
+                           bool mixed, double *scratch, size_t scratch_bytes, cudaStream_t stream);
+// launches launch_generic makes for nq quartets (kernel names in *names, for reports)
+int generic_launches(long long nq, int neri, bool compressed, size_t scratch_bytes);
+const char *generic_kernel_names(bool mixed, bool compressed);
+
 // Quartets per launch of the split setup/recurrence path (a multiple of 32 so that every chunk
 // starts on a 32-bit word of the packed stream) and the widest setup record (n_Rys = 7).
 constexpr long long kSetupChunk = 1LL << 20;

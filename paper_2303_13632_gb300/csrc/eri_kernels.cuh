@@ -63,6 +63,11 @@ __device__ __forceinline__ uint32_t to_code(R v, int bits) {
 __host__ __device__ constexpr int cdiv(int a, int b) { return (a + b - 1) / b; }
 __host__ __device__ constexpr int imin(int a, int b) { return a < b ? a : b; }
 __host__ __device__ constexpr int imax(int a, int b) { return a > b ? a : b; }
+// smallest b-chunk >= b with nanc * ceil(nb / chunk) <= 1024 phase-D items per quartet
+__host__ __device__ constexpr int bch_fit(int nanc, int nb, int b) {
+    while (b < nb && nanc * cdiv(nb, b) > 1024) ++b;
+    return b;
+}
 
 // ids[k] of an int4 without dynamic register indexing.
 __device__ __forceinline__ int pick(const int4 &g, int k) {
@@ -122,7 +127,9 @@ struct Cfg {
     static constexpr int RWORDS = sizeof(R) / 4;
     // outputs per thread: bchunk x ND accumulators (+ Kahan compensation in FP32)
     static constexpr int ACC_REGS = (sizeof(R) == 8) ? 48 : 64;
-    static constexpr int BCH = imax(1, imin(NB, ACC_REGS / (ND * RWORDS)));
+    // widened where one thread per phase-D item would exceed a CTA's 1024 threads (FP64 classes
+    // with two g shells)
+    static constexpr int BCH = bch_fit(NA * NC, NB, imax(1, imin(NB, ACC_REGS / (ND * RWORDS))));
     static constexpr int NCH = cdiv(NB, BCH);
     static constexpr int ITEMS_D = NA * NC * NCH;
     // shared memory per quartet (bytes)

@@ -21,7 +21,7 @@ constexpr int kChunkWords = 16;  // 512 bits
 
 // Quartets [q0, q0 + nq) of one class.  `src` is the class's dense stream (word 0 holds stream
 // bit 0), `dst` the chunk words of quartet q0.  nq * n_cs * 16 < 2^31 (host-checked), and every
-// in-quartet bit offset fits 32 bits (n_eri * bits <= 10000 * 24).
+// in-quartet bit offset fits 32 bits (n_eri * bits <= 50625 * 24, [gg|gg] at 24 bits).
 __global__ void __launch_bounds__(256) paper512_kernel(const uint32_t *__restrict__ src,
                                                        unsigned long long q0, unsigned nq,
                                                        unsigned n_eri, unsigned n_cs, unsigned bits,
@@ -60,14 +60,14 @@ __global__ void __launch_bounds__(256) paper512_kernel(const uint32_t *__restric
 extern "C" eri_status_t eri_pack_paper512_stream(const void *d_stream, int64_t n_quartets,
                                                  int32_t n_eri, int32_t bits, void *d_chunks,
                                                  void *stream) {
-    if (n_quartets < 0 || n_eri < 1 || n_eri > 10000 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (n_quartets < 0 || n_eri < 1 || n_eri > 50625 || bits < 2 || bits > 24) return ERI_E_INVALID;
     if (n_quartets == 0) return ERI_OK;
     if (!d_stream || !d_chunks) return ERI_E_INVALID;
     if (reinterpret_cast<uintptr_t>(d_stream) % 4 || reinterpret_cast<uintptr_t>(d_chunks) % 4)
         return ERI_E_INVALID;
     const long long F = 512 / bits;
     const long long n_cs = (n_eri + F - 1) / F;
-    const long long per_piece = (1ll << 30) / (n_cs * eri::kChunkWords);  // >= 1: n_cs <= 10000
+    const long long per_piece = (1ll << 30) / (n_cs * eri::kChunkWords);  // >= 1: n_cs <= 50625
     const auto *src = static_cast<const uint32_t *>(d_stream);
     auto *dst = static_cast<uint32_t *>(d_chunks);
     int dev = 0;

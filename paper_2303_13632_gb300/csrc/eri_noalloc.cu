@@ -156,6 +156,7 @@ extern "C" eri_status_t eri_compute_class_noalloc(int32_t cls, int32_t precision
                                                   const double *d_exps, const double *d_cn,
                                                   const int32_t *d_quartets, int64_t n_quartets,
                                                   double *d_out, int32_t *d_err, void *stream) {
+    if (class_id_valid(cls) && class_has_g(cls)) return ERI_E_UNSUPPORTED;  // L <= 3 only
     if (cls < 0 || cls > 255 || (precision != ERI_FP64 && precision != ERI_MIXED)) return ERI_E_INVALID;
     if (n_quartets < 0 || n_quartets > ERI_NOALLOC_MAX_QUARTETS) return ERI_E_INVALID;
     if (!d_err) return ERI_E_INVALID;

@@ -61,7 +61,8 @@ struct Canon {
 };
 
 Canon canonicalise(int cls) {
-    int L[4] = {(cls >> 6) & 3, (cls >> 4) & 3, (cls >> 2) & 3, cls & 3};
+    int L[4];
+    class_ls(cls, L);
     int bra[2] = {0, 1}, ket[2] = {2, 3};
     if (L[0] < L[1]) { bra[0] = 1; bra[1] = 0; }
     if (L[2] < L[3]) { ket[0] = 3; ket[1] = 2; }
@@ -76,12 +77,12 @@ Canon canonicalise(int cls) {
         c.perm[k] = p[k];
         c.ostride[k] = gstride[p[k]];
     }
-    c.cls = ((L[p[0]] * 4 + L[p[1]]) * 4 + L[p[2]]) * 4 + L[p[3]];
+    c.cls = class_id_of(L[p[0]], L[p[1]], L[p[2]], L[p[3]]);
     return c;
 }
 
 __global__ void classify_kernel(const int4 *__restrict__ q, long long n, const int *__restrict__ L,
-                                int n_shells, uint8_t *__restrict__ keys, int *__restrict__ vals,
+                                int n_shells, uint16_t *__restrict__ keys, int *__restrict__ vals,
                                 int *__restrict__ err) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -92,7 +93,7 @@ __global__ void classify_kernel(const int4 *__restrict__ q, long long n, const i
         atomicOr(err, 4);
         keys[i] = 0;
     } else {
-        keys[i] = (uint8_t)(((L[t.x] * 4 + L[t.y]) * 4 + L[t.z]) * 4 + L[t.w]);
+        keys[i] = (uint16_t)class_id_of(L[t.x], L[t.y], L[t.z], L[t.w]);
     }
     vals[i] = (int)i;
 }
@@ -127,16 +128,16 @@ __global__ void compose_kernel(int *__restrict__ perm, const int *__restrict__ o
     if (i < n) perm[i] = orig[perm[i]];
 }
 
-__global__ void histogram_kernel(const uint8_t *__restrict__ keys, long long n,
+__global__ void histogram_kernel(const uint16_t *__restrict__ keys, long long n,
                                  unsigned long long *__restrict__ counts) {
-    __shared__ unsigned int h[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) h[i] = 0;
+    __shared__ unsigned int h[kNumClassIds];
+    for (int i = threadIdx.x; i < kNumClassIds; i += blockDim.x) h[i] = 0;
     __syncthreads();
     for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (long long)gridDim.x * blockDim.x)
         atomicAdd(&h[keys[i]], 1u);
     __syncthreads();
-    for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    for (int i = threadIdx.x; i < kNumClassIds; i += blockDim.x)
         if (h[i]) atomicAdd(&counts[i], (unsigned long long)h[i]);
 }
 
@@ -221,22 +222,22 @@ struct eri_plan_s {
     cudaEvent_t fork_ev = nullptr, join_ev[kSide] = {};
     // streamed copies to the host: copy stream and one event per class
     cudaStream_t copy_stream = nullptr;
-    cudaEvent_t class_ev[256] = {};
+    cudaEvent_t class_ev[kNumClassIds] = {};
     cudaEvent_t copy_done = nullptr;
     cudaGraphExec_t graph = nullptr;
     int g_bits = -1, g_prec = -1;
     void *g_packed = nullptr;
     float *g_scales = nullptr;
     // per-class precision (-1: the plan's) and the calibrated mixed-path error per class
-    int class_prec[256];
-    float class_err[256];
+    int class_prec[kNumClassIds];
+    float class_err[kNumClassIds];
     // autotuned launch choice per canonical class and variant (grid 0 = all resident CTAs)
     int tune_phase[256 * kNumVariants] = {0};
     int tune_grid[256 * kNumVariants] = {0};
     // host layout
-    long long count[256] = {0};
-    long long first[256] = {0};
-    long long fp64_off[256] = {0};
+    long long count[kNumClassIds] = {0};
+    long long first[kNumClassIds] = {0};
+    long long fp64_off[kNumClassIds] = {0};
     Tables tables;
 };
 
@@ -267,7 +268,7 @@ void free_plan(eri_plan_s *p) {
     }
     if (p->fork_ev) cudaEventDestroy(p->fork_ev);
     if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
-    for (int c = 0; c < 256; ++c)
+    for (int c = 0; c < kNumClassIds; ++c)
         if (p->class_ev[c]) cudaEventDestroy(p->class_ev[c]);
     if (p->copy_done) cudaEventDestroy(p->copy_done);
     delete p;
@@ -322,7 +323,17 @@ size_t paper512_segment_bytes(long long nq, int neri, int bits) {
 }
 
 int class_neri(int cls) {
-    return ncart_h((cls >> 6) & 3) * ncart_h((cls >> 4) & 3) * ncart_h((cls >> 2) & 3) * ncart_h(cls & 3);
+    int L[4];
+    class_ls(cls, L);
+    return ncart_h(L[0]) * ncart_h(L[1]) * ncart_h(L[2]) * ncart_h(L[3]);
+}
+
+// bytes of the plan's scratch (split setup records, or the FP64 values of the compressed output
+// of classes with a g shell)
+constexpr size_t kScratchBytes = (size_t)kSetupChunk * kSetupFieldsMax * sizeof(double);
+
+cudaError_t ensure_scratch(eri_plan_s *p) {
+    return p->d_setup ? cudaSuccess : cudaMalloc(&p->d_setup, kScratchBytes);
 }
 
 int class_precision(const eri_plan_s *p, int cls) {
@@ -368,14 +379,24 @@ eri_status_t launch_class_args(eri_plan_s *p, int cls, const ClassArgs &a, int v
     ShellsDev sh{p->d_cx, p->d_cy, p->d_cz, p->d_pofs, p->d_nprim, p->d_exps, p->d_cn};
     const int neri = class_neri(cls);
     const int bits = a.bits;
+    if (class_has_g(c.cls)) {
+        int L[4];
+        class_ls(c.cls, L);
+        if (!a.out_fp64) {
+            cudaError_t e = ensure_scratch(p);
+            if (e != cudaSuccess) return cuda_status(e);
+        }
+        return cuda_status(launch_generic(sh, p->tables, a, L, variant != 0, static_cast<double *>(p->d_setup),
+                                          kScratchBytes, stream));
+    }
     LaunchFn fn = g_launch[c.cls * kNumVariants + variant];
     if (!fn) return ERI_E_UNSUPPORTED;
     LaunchOpts o;
     o.device = p->device;
     const bool split = p->max_nprim == 1 && g_info[c.cls * kNumVariants + variant].setup;
     if (!split) return cuda_status(fn(sh, p->tables, a, stream, o));
-    if (!p->d_setup) {
-        cudaError_t e = cudaMalloc(&p->d_setup, (size_t)kSetupChunk * kSetupFieldsMax * sizeof(double));
+    {
+        cudaError_t e = ensure_scratch(p);
         if (e != cudaSuccess) return cuda_status(e);
     }
     o.scratch = p->d_setup;
@@ -422,12 +443,12 @@ eri_status_t schwarz_factors(const eri_shell_t *shells, int n_shells, int device
     cudaFree(d_diag);
     if (st != ERI_OK) return st;
     long long maxv = 1;
-    for (int c = 0; c < 256; ++c)
+    for (int c = 0; c < kNumClassIds; ++c)
         if (sp->count[c] > 0) maxv = std::max(maxv, std::min(sp->count[c], std::max(1LL, kChunkDoubles / class_neri(c))) * class_neri(c));
     e = plan_malloc(&Qs, npairs * sizeof(double));
     if (e == cudaSuccess) e = plan_malloc(&buf, maxv * sizeof(double));
     if (e == cudaSuccess) e = plan_malloc(d_Q, npairs * sizeof(double));
-    for (int c = 0; e == cudaSuccess && st == ERI_OK && c < 256; ++c) {
+    for (int c = 0; e == cudaSuccess && st == ERI_OK && c < kNumClassIds; ++c) {
         if (sp->count[c] == 0) continue;
         const int neri = class_neri(c);
         const long long chunk = std::max(1LL, kChunkDoubles / neri);
@@ -465,6 +486,9 @@ eri_status_t launch_one(eri_plan_s *p, int cls, double *d_out, int bits, void *d
 eri_status_t ensure_batched_resources(eri_plan_s *p) {
     cudaError_t e = cudaSuccess;
     if (!p->d_counters) e = cudaMalloc(&p->d_counters, 256 * sizeof(unsigned long long));
+    bool has_g = false;
+    for (int c = 256; c < kNumClassIds; ++c) has_g |= p->count[c] > 0;
+    if (e == cudaSuccess && has_g) e = ensure_scratch(p);  // before any stream capture
     for (int i = 0; e == cudaSuccess && i < eri_plan_s::kSide; ++i) {
         if (!p->side[i]) e = cudaStreamCreateWithFlags(&p->side[i], cudaStreamNonBlocking);
         if (e == cudaSuccess && !p->join_ev[i])
@@ -484,9 +508,9 @@ eri_status_t enqueue_batched(eri_plan_s *p, int bits, void *d_packed, float *d_s
         e = cudaStreamWaitEvent(p->side[i], p->fork_ev, 0);
     if (e != cudaSuccess) return cuda_status(e);
     std::vector<int> cls;
-    std::vector<size_t> off(256, 0);
+    std::vector<size_t> off(kNumClassIds, 0);
     size_t o = 0;
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         off[c] = o;
         o += packed_segment_bytes(p->count[c], class_neri(c), bits);
         if (p->count[c] > 0) cls.push_back(c);
@@ -499,6 +523,14 @@ eri_status_t enqueue_batched(eri_plan_s *p, int bits, void *d_packed, float *d_s
         int c = cls[i];
         int cc = canonicalise(c).cls;
         const int variant = class_variant(p, c);
+        if (class_has_g(cc)) {
+            // plain launches of the run-time-L kernels; all on the first side stream, since
+            // they share the plan's scratch
+            ClassArgs a = class_args(p, c, nullptr, bits, d_packed, d_scales, off[c]);
+            eri_status_t st = launch_class_args(p, c, a, variant, p->side[0]);
+            if (st != ERI_OK) return st;
+            continue;
+        }
         LaunchFn fn = g_launch[cc * kNumVariants + variant];
         if (!fn) return ERI_E_UNSUPPORTED;
         ClassArgs a = class_args(p, c, nullptr, bits, d_packed, d_scales, off[c]);
@@ -534,13 +566,15 @@ const char *eri_status_string(eri_status_t s) {
 }
 
 int32_t eri_class_id(int32_t La, int32_t Lb, int32_t Lc, int32_t Ld) {
-    if (La < 0 || La > 3 || Lb < 0 || Lb > 3 || Lc < 0 || Lc > 3 || Ld < 0 || Ld > 3) return -1;
-    return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld;
+    if (La < 0 || La > kLmax || Lb < 0 || Lb > kLmax || Lc < 0 || Lc > kLmax || Ld < 0 || Ld > kLmax)
+        return -1;
+    return class_id_of(La, Lb, Lc, Ld);
 }
 
 eri_status_t eri_class_shape(int32_t cls, int32_t *n_eri, int32_t *n_rys) {
-    if (cls < 0 || cls > 255) return ERI_E_INVALID;
-    int L[4] = {(cls >> 6) & 3, (cls >> 4) & 3, (cls >> 2) & 3, cls & 3};
+    if (!class_id_valid(cls)) return ERI_E_INVALID;
+    int L[4];
+    class_ls(cls, L);
     if (n_eri) *n_eri = ncart_h(L[0]) * ncart_h(L[1]) * ncart_h(L[2]) * ncart_h(L[3]);
     if (n_rys) *n_rys = (L[0] + L[1] + L[2] + L[3]) / 2 + 1;
     return ERI_OK;
@@ -582,7 +616,7 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     long long n_bf = 0;
     for (int s = 0; s < n_shells; ++s) {
         const eri_shell_t &sh = shells[s];
-        if (sh.L < 0 || sh.L > 3) return sh.L > 3 ? ERI_E_UNSUPPORTED : ERI_E_INVALID;
+        if (sh.L < 0 || sh.L > kLmax) return sh.L > kLmax ? ERI_E_UNSUPPORTED : ERI_E_INVALID;
         if (sh.nprim < 1 || !sh.exps || !sh.coefs) return ERI_E_INVALID;
         for (int x = 0; x < 3; ++x)
             if (!std::isfinite(sh.center[x])) return ERI_E_INVALID;
@@ -644,7 +678,7 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     p->nq = nq;
     p->max_nprim = max_nprim;
     p->n_bf = n_bf;
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         p->class_prec[c] = -1;
         p->class_err[c] = -1.0f;
     }
@@ -725,7 +759,7 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     }
 
     if (nq > 0) {
-        uint8_t *d_keys = nullptr, *d_keys_sorted = nullptr;
+        uint16_t *d_keys = nullptr, *d_keys_sorted = nullptr;
         int *d_vals = nullptr;
         unsigned long long *d_counts = nullptr;
         void *d_tmp = nullptr;
@@ -733,36 +767,36 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         int *d_verr = nullptr;
         const unsigned blocks = (unsigned)((nq + 255) / 256);
         do {
-            if ((e = plan_malloc(&d_keys, nq)) != cudaSuccess) break;
-            if ((e = plan_malloc(&d_keys_sorted, nq)) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_keys, nq * sizeof(uint16_t))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_keys_sorted, nq * sizeof(uint16_t))) != cudaSuccess) break;
             if ((e = plan_malloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
             if ((e = plan_malloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
             if ((e = plan_malloc(&d_verr, sizeof(int))) != cudaSuccess) break;
             if ((e = cudaMemset(d_verr, 0, sizeof(int))) != cudaSuccess) break;
             classify_kernel<<<blocks, 256>>>(d_in, nq, d_L, n_shells, d_keys, d_vals, d_verr);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
-            // stable radix sort on the 8-bit class key keeps the caller's order within a class
+            // stable radix sort on the 10-bit class key keeps the caller's order within a class
             e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_vals,
-                                                p->d_perm, (int)nq, 0, 8);
+                                                p->d_perm, (int)nq, 0, 10);
             if (e != cudaSuccess) break;
             if ((e = plan_malloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
             e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_vals,
-                                                p->d_perm, (int)nq, 0, 8);
+                                                p->d_perm, (int)nq, 0, 10);
             if (e != cudaSuccess) break;
             if ((e = plan_malloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
             gather_kernel<<<blocks, 256>>>(d_in, p->d_perm, nq, p->d_quartets);
-            if ((e = plan_malloc(&d_counts, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
-            if ((e = cudaMemset(d_counts, 0, 256 * sizeof(unsigned long long))) != cudaSuccess) break;
+            if ((e = plan_malloc(&d_counts, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
+            if ((e = cudaMemset(d_counts, 0, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
             histogram_kernel<<<std::min<unsigned>(blocks, 4096u), 256>>>(d_keys_sorted, nq, d_counts);
             if ((e = cudaGetLastError()) != cudaSuccess) break;
-            unsigned long long counts[256];
+            unsigned long long counts[kNumClassIds];
             if ((e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost)) != cudaSuccess)
                 break;
             int verr = 0;
             if ((e = cudaMemcpy(&verr, d_verr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
                 break;
             if (verr) e = cudaErrorInvalidValue;  // mapped to ERI_E_INVALID below
-            for (int c = 0; c < 256; ++c) p->count[c] = (long long)counts[c];
+            for (int c = 0; c < kNumClassIds; ++c) p->count[c] = (long long)counts[c];
             if (d_orig) {  // sorted position -> index in the caller's list
                 compose_kernel<<<blocks, 256>>>(p->d_perm, d_orig, nq);
                 e = cudaGetLastError();
@@ -814,11 +848,10 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
         }
     }
     long long f = 0, off = 0;
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         p->first[c] = f;
         p->fp64_off[c] = off;
-        int neri = 0;
-        eri_class_shape(c, &neri, nullptr);
+        const int neri = class_neri(c);
         f += p->count[c];
         off += p->count[c] * neri;
     }
@@ -839,7 +872,7 @@ eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision) {
 }
 
 eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t precision) {
-    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls)) return ERI_E_INVALID;
     if (precision != ERI_FP64 && precision != ERI_MIXED && precision != -1) return ERI_E_INVALID;
     plan->class_prec[cls] = precision;
     if (plan->graph) {
@@ -851,7 +884,7 @@ eri_status_t eri_plan_set_class_precision(eri_plan_t plan, int32_t cls, int32_t 
 
 eri_status_t eri_plan_class_precision(eri_plan_t plan, int32_t cls, int32_t *precision,
                                       float *mixed_err) {
-    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls)) return ERI_E_INVALID;
     if (precision) *precision = class_precision(plan, cls);
     if (mixed_err) *mixed_err = plan->class_err[cls];
     return ERI_OK;
@@ -866,7 +899,7 @@ eri_status_t eri_plan_num_quartets(eri_plan_t plan, int64_t *n) {
 eri_status_t eri_plan_class_info(eri_plan_t plan, int32_t cls, int64_t *n_quartets,
                                  int32_t *n_eri_per_quartet, int64_t *first_quartet,
                                  int64_t *fp64_offset) {
-    if (!plan || cls < 0 || cls > 255) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls)) return ERI_E_INVALID;
     if (n_quartets) *n_quartets = plan->count[cls];
     if (n_eri_per_quartet) eri_class_shape(cls, n_eri_per_quartet, nullptr);
     if (first_quartet) *first_quartet = plan->first[cls];
@@ -887,17 +920,11 @@ eri_status_t eri_plan_quartet_order(eri_plan_t plan, int64_t *perm_out) {
 
 eri_status_t eri_packed_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                      size_t *byte_offset, size_t *bytes) {
-    if (!plan || cls < 0 || cls > 255 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls) || bits < 2 || bits > 24) return ERI_E_INVALID;
     size_t off = 0;
-    for (int c = 0; c < cls; ++c) {
-        int neri = 0;
-        eri_class_shape(c, &neri, nullptr);
-        off += packed_segment_bytes(plan->count[c], neri, bits);
-    }
-    int neri = 0;
-    eri_class_shape(cls, &neri, nullptr);
+    for (int c = 0; c < cls; ++c) off += packed_segment_bytes(plan->count[c], class_neri(c), bits);
     if (byte_offset) *byte_offset = off;
-    if (bytes) *bytes = packed_segment_bytes(plan->count[cls], neri, bits);
+    if (bytes) *bytes = packed_segment_bytes(plan->count[cls], class_neri(cls), bits);
     return ERI_OK;
 }
 
@@ -905,9 +932,8 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
                               size_t *scales_bytes) {
     if (!plan || (bits != 0 && (bits < 2 || bits > 24))) return ERI_E_INVALID;
     size_t total = 0;
-    for (int c = 0; c < 256; ++c) {
-        int neri = 0;
-        eri_class_shape(c, &neri, nullptr);
+    for (int c = 0; c < kNumClassIds; ++c) {
+        const int neri = class_neri(c);
         total += bits == 0 ? (size_t)plan->count[c] * neri * sizeof(double)
                            : packed_segment_bytes(plan->count[c], neri, bits);
     }
@@ -918,11 +944,11 @@ eri_status_t eri_output_bytes(eri_plan_t plan, int32_t bits, size_t *packed_byte
 
 eri_status_t eri_paper512_class_offset(eri_plan_t plan, int32_t bits, int32_t cls,
                                        size_t *byte_offset, size_t *bytes) {
-    if (!plan || cls < 0 || cls > 256 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (!plan || (cls != kNumClassIds && !class_id_valid(cls)) || bits < 2 || bits > 24) return ERI_E_INVALID;
     size_t off = 0;
     for (int c = 0; c < cls; ++c) off += paper512_segment_bytes(plan->count[c], class_neri(c), bits);
     if (byte_offset) *byte_offset = off;
-    if (bytes) *bytes = cls == 256 ? 0 : paper512_segment_bytes(plan->count[cls], class_neri(cls), bits);
+    if (bytes) *bytes = cls == kNumClassIds ? 0 : paper512_segment_bytes(plan->count[cls], class_neri(cls), bits);
     return ERI_OK;
 }
 
@@ -934,7 +960,7 @@ eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_pack
         return ERI_E_INVALID;
     cudaSetDevice(plan->device);
     size_t in = 0, out = 0;
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         const int neri = class_neri(c);
         if (plan->count[c] > 0) {
             eri_status_t st = eri_pack_paper512_stream(static_cast<const char *>(d_packed) + in,
@@ -949,7 +975,7 @@ eri_status_t eri_pack_paper512(eri_plan_t plan, int32_t bits, const void *d_pack
 }
 
 eri_status_t eri_compute_class(eri_plan_t plan, int32_t cls, double *d_out, void *stream) {
-    if (!plan || cls < 0 || cls > 255 || (!d_out && plan->nq > 0)) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls) || (!d_out && plan->nq > 0)) return ERI_E_INVALID;
     if (reinterpret_cast<uintptr_t>(d_out) % 8) return ERI_E_INVALID;
     cudaSetDevice(plan->device);
     return launch_one(plan, cls, d_out, 0, nullptr, nullptr, 0, (cudaStream_t)stream);
@@ -959,7 +985,7 @@ eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream) {
     if (!plan || (!d_out && plan->nq > 0)) return ERI_E_INVALID;
     if (reinterpret_cast<uintptr_t>(d_out) % 8) return ERI_E_INVALID;
     cudaSetDevice(plan->device);
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         eri_status_t s = launch_one(plan, c, d_out, 0, nullptr, nullptr, 0, (cudaStream_t)stream);
         if (s != ERI_OK) return s;
     }
@@ -968,7 +994,7 @@ eri_status_t eri_compute(eri_plan_t plan, double *d_out, void *stream) {
 
 eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t bits,
                                           void *d_packed, float *d_scales, void *stream) {
-    if (!plan || cls < 0 || cls > 255 || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls) || bits < 2 || bits > 24) return ERI_E_INVALID;
     if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
     if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
         return ERI_E_INVALID;
@@ -986,9 +1012,8 @@ eri_status_t eri_compute_compressed(eri_plan_t plan, int32_t bits, void *d_packe
         return ERI_E_INVALID;
     cudaSetDevice(plan->device);
     size_t off = 0;
-    for (int c = 0; c < 256; ++c) {
-        int neri = 0;
-        eri_class_shape(c, &neri, nullptr);
+    for (int c = 0; c < kNumClassIds; ++c) {
+        const int neri = class_neri(c);
         eri_status_t s = launch_one(plan, c, nullptr, bits, d_packed, d_scales, off, (cudaStream_t)stream);
         if (s != ERI_OK) return s;
         off += packed_segment_bytes(plan->count[c], neri, bits);
@@ -1011,10 +1036,8 @@ eri_status_t eri_compute_compressed_to_host(eri_plan_t plan, int32_t bits, void 
         e = cudaEventCreateWithFlags(&plan->copy_done, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_status(e);
     size_t off = 0;
-    for (int c = 0; c < 256; ++c) {
-        int neri = 0;
-        eri_class_shape(c, &neri, nullptr);
-        const size_t seg = packed_segment_bytes(plan->count[c], neri, bits);
+    for (int c = 0; c < kNumClassIds; ++c) {
+        const size_t seg = packed_segment_bytes(plan->count[c], class_neri(c), bits);
         if (plan->count[c] > 0) {
             eri_status_t st = launch_one(plan, c, nullptr, bits, d_packed, d_scales, off, s);
             if (st != ERI_OK) return st;
@@ -1052,11 +1075,13 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
         return ERI_E_INVALID;
     // the adjoint of a class runs in that class's precision: FP64, or FP32 recurrences with FP64
     // geometry, roots and accumulation (the mixed adjoint)
+    // (none for classes with a g shell)
     auto backward_of = [&](int c) -> BackwardFn {
         const int cc = canonicalise(c).cls;
+        if (class_has_g(cc)) return nullptr;
         return class_precision(plan, c) == ERI_FP64 ? g_backward[cc] : g_backward_mixed[cc];
     };
-    for (int c = 0; c < 256; ++c)
+    for (int c = 0; c < kNumClassIds; ++c)
         if (plan->count[c] > 0 && !backward_of(c)) return ERI_E_UNSUPPORTED;
     cudaSetDevice(plan->device);
     cudaStream_t st = (cudaStream_t)stream;
@@ -1064,7 +1089,7 @@ eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, doub
     if (e == cudaSuccess) e = cudaMemsetAsync(d_dalpha, 0, sizeof(double) * (size_t)plan->n_prims, st);
     if (e != cudaSuccess) return cuda_status(e);
     ShellsDev sh{plan->d_cx, plan->d_cy, plan->d_cz, plan->d_pofs, plan->d_nprim, plan->d_exps, plan->d_cn};
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         if (plan->count[c] == 0) continue;
         Canon cn = canonicalise(c);
         ClassArgs a{};
@@ -1160,13 +1185,13 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
     ShellsDev sh{plan->d_cx, plan->d_cy, plan->d_cz, plan->d_pofs, plan->d_nprim, plan->d_exps, plan->d_cn};
     std::vector<std::string> lines;
     size_t o = 0;
-    std::vector<size_t> off(256);
-    for (int c = 0; c < 256; ++c) {
+    std::vector<size_t> off(kNumClassIds);
+    for (int c = 0; c < kNumClassIds; ++c) {
         off[c] = o;
         o += packed_segment_bytes(plan->count[c], class_neri(c), bits);
     }
     std::vector<int> done(256 * kNumVariants, 0);
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < 256; ++c) {  // the run-time-L kernels of g classes have no choices
         if (plan->count[c] == 0) continue;
         int cc = canonicalise(c).cls;
         const int variant = class_variant(plan, c);
@@ -1227,10 +1252,16 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
 }
 
 eri_status_t eri_plan_class_kernels(eri_plan_t plan, int32_t cls, char *buf, size_t len) {
-    if (!plan || cls < 0 || cls > 255 || !buf || len == 0) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls) || !buf || len == 0) return ERI_E_INVALID;
     buf[0] = 0;
     const int v = class_variant(plan, cls);
     const Canon c = canonicalise(cls);
+    if (class_has_g(c.cls)) {
+        const char *nm = generic_kernel_names(v != 0, true);
+        if (std::strlen(nm) + 1 > len) return ERI_E_INVALID;
+        std::memcpy(buf, nm, std::strlen(nm) + 1);
+        return ERI_OK;
+    }
     const int k = c.cls * kNumVariants + v;
     if (!g_launch[k]) return ERI_E_UNSUPPORTED;
     const bool split = plan->max_nprim == 1 && g_info[k].setup;
@@ -1254,10 +1285,14 @@ eri_status_t eri_plan_class_kernels(eri_plan_t plan, int32_t cls, char *buf, siz
 }
 
 eri_status_t eri_plan_class_launches(eri_plan_t plan, int32_t cls, int32_t *n_launches) {
-    if (!plan || cls < 0 || cls > 255 || !n_launches) return ERI_E_INVALID;
+    if (!plan || !class_id_valid(cls) || !n_launches) return ERI_E_INVALID;
     *n_launches = 0;
     if (plan->count[cls] == 0) return ERI_OK;
     const int v = class_variant(plan, cls);
+    if (class_has_g(canonicalise(cls).cls)) {
+        *n_launches = generic_launches(plan->count[cls], class_neri(cls), true, kScratchBytes);
+        return ERI_OK;
+    }
     const int k = canonicalise(cls).cls * kNumVariants + v;
     if (!g_launch[k]) return ERI_E_UNSUPPORTED;
     const bool split = plan->max_nprim == 1 && g_info[k].setup;
@@ -1273,15 +1308,15 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
     cudaSetDevice(plan->device);
     cudaStream_t s = (cudaStream_t)stream;
     size_t maxv = 0;
-    for (int c = 0; c < 256; ++c)
+    for (int c = 0; c < kNumClassIds; ++c)
         maxv = std::max(maxv, (size_t)std::min<long long>(plan->count[c], sample) * class_neri(c));
     double *da = nullptr, *db = nullptr;
     unsigned int *dres = nullptr;
     cudaError_t e = cudaMalloc(&da, maxv * sizeof(double));
     if (e == cudaSuccess) e = cudaMalloc(&db, maxv * sizeof(double));
-    if (e == cudaSuccess) e = cudaMalloc(&dres, 256 * sizeof(unsigned int));
-    if (e == cudaSuccess) e = cudaMemsetAsync(dres, 0, 256 * sizeof(unsigned int), s);
-    for (int c = 0; e == cudaSuccess && c < 256; ++c) {
+    if (e == cudaSuccess) e = cudaMalloc(&dres, kNumClassIds * sizeof(unsigned int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(dres, 0, kNumClassIds * sizeof(unsigned int), s);
+    for (int c = 0; e == cudaSuccess && c < kNumClassIds; ++c) {
         if (plan->count[c] == 0) continue;
         const long long n = std::min<long long>(plan->count[c], sample);
         const int neri = class_neri(c);
@@ -1304,8 +1339,9 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
             e = cudaGetLastError();
         }
     }
-    unsigned int res[256] = {0};
-    if (e == cudaSuccess) e = cudaMemcpyAsync(res, dres, sizeof(res), cudaMemcpyDeviceToHost, s);
+    std::vector<unsigned int> res(kNumClassIds, 0u);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(res.data(), dres, kNumClassIds * sizeof(unsigned int), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     cudaFree(da);
     cudaFree(db);
@@ -1314,7 +1350,7 @@ eri_status_t eri_plan_calibrate_precision(eri_plan_t plan, int32_t bits, int64_t
     // a class keeps the FP32 recurrences when its measured error stays below max_err_steps
     // quantisation steps, one step being eps / b_max = 1 / (2^{bits-1} - 1)
     const float thr = max_err_steps / (float)((1u << (bits - 1)) - 1u);
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         if (plan->count[c] == 0) continue;
         float err;
         std::memcpy(&err, &res[c], sizeof(float));
@@ -1360,6 +1396,8 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
         reinterpret_cast<uintptr_t>(d_D) % 8 || reinterpret_cast<uintptr_t>(d_J) % 8 ||
         reinterpret_cast<uintptr_t>(d_K) % 8)
         return ERI_E_INVALID;
+    for (int c = 256; c < kNumClassIds; ++c)
+        if (plan->count[c] > 0) return ERI_E_UNSUPPORTED;  // classes with a g shell
     if (plan->n_bf == 0) return ERI_OK;
     cudaSetDevice(plan->device);
     cudaStream_t s = (cudaStream_t)stream;
@@ -1378,7 +1416,7 @@ eri_status_t eri_digest_jk(eri_plan_t plan, int32_t bits, const void *d_packed, 
     if ((e = digest_density_f32(d_D, n2, plan->d_D32, s)) != cudaSuccess) return cuda_status(e);
     std::vector<DigestClass> dcs;
     size_t off = 0;
-    for (int c = 0; c < 256; ++c) {
+    for (int c = 0; c < kNumClassIds; ++c) {
         const size_t seg = packed_segment_bytes(plan->count[c], class_neri(c), bits);
         if (plan->count[c] > 0) {
             DigestClass dc;

@@ -52,12 +52,24 @@ def rng_for(k: int) -> np.random.Generator:
 
 
 def class_id(La: int, Lb: int, Lc: int, Ld: int) -> int:
-    """Class index ((La*4 + Lb)*4 + Lc)*4 + Ld, 0..255."""
-    return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld
+    """Class id: ((La*4 + Lb)*4 + Lc)*4 + Ld (0..255) when every L <= 3, else
+    256 + ((La*5 + Lb)*5 + Lc)*5 + Ld (classes with a g shell)."""
+    if max(La, Lb, Lc, Ld) <= 3:
+        return ((La * 4 + Lb) * 4 + Lc) * 4 + Ld
+    return 256 + ((La * 5 + Lb) * 5 + Lc) * 5 + Ld
 
 
 def class_of_id(c: int):
-    return (c >> 6) & 3, (c >> 4) & 3, (c >> 2) & 3, c & 3
+    if c < 256:
+        return (c >> 6) & 3, (c >> 4) & 3, (c >> 2) & 3, c & 3
+    r = c - 256
+    return r // 125, (r // 25) % 5, (r // 5) % 5, r % 5
+
+
+def g_class_ids():
+    """Ids of the 369 classes with a g shell, ascending."""
+    return [class_id(a, b, c, d) for a in range(5) for b in range(5) for c in range(5) for d in range(5)
+            if 4 in (a, b, c, d)]
 
 
 def shell_size(L: int) -> int:

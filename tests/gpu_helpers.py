@@ -4,12 +4,12 @@ import numpy as np
 import torch
 
 import oracle
-from paper_2303_13632_gb300 import api
+from paper_2303_13632_gb300 import _lib, api, workloads as W
 
 
 def class_of(shells, q):
     L = np.asarray(shells.L)
-    return ((L[q[0]] * 4 + L[q[1]]) * 4 + L[q[2]]) * 4 + L[q[3]]
+    return W.class_id(int(L[q[0]]), int(L[q[1]]), int(L[q[2]]), int(L[q[3]]))
 
 
 def gpu_fp64(shells, quartets, precision="fp64", pair_table=True):
@@ -46,7 +46,9 @@ def gpu_compressed(shells, quartets, bits, precision="fp64"):
     q = np.asarray(quartets)
     codes = [None] * len(q)
     eps = np.zeros(len(q), dtype=np.float32)
-    for cls in range(256):
+    for cls in range(_lib.ERI_NUM_CLASS_IDS):
+        if W.class_id(*W.class_of_id(cls)) != cls:
+            continue  # not a class
         nq, neri, first, _ = api.eri_plan_class_info(plan, cls)
         if nq == 0:
             continue

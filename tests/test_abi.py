@@ -35,8 +35,17 @@ def test_host_only_helpers():
     assert api.eri_class_shape(api.eri_class_id(3, 3, 3, 3)) == (10000, 7)
     assert api.eri_class_shape(api.eri_class_id(2, 2, 1, 0)) == (108, 3)
     assert api.eri_status_string(_lib.ERI_E_NUMERIC) == "ERI_E_NUMERIC"
-    with pytest.raises(_lib.EriError):
-        api.eri_class_shape(256)
+    # classes with a g shell: 256 + ((La*5 + Lb)*5 + Lc)*5 + Ld
+    assert api.eri_class_id(4, 0, 0, 0) == 256 + 500
+    assert api.eri_class_id(4, 4, 4, 4) == 880
+    assert api.eri_class_id(0, 1, 2, 4) == 256 + 39
+    assert api.eri_class_shape(880) == (50625, 9)
+    assert api.eri_class_shape(api.eri_class_id(4, 3, 2, 1)) == (15 * 10 * 6 * 3, 6)
+    assert api.eri_class_id(5, 0, 0, 0) == -1
+    for bad_id in (256, 256 + 3, 256 + 31, 881, -1):  # slots of no class
+        with pytest.raises(_lib.EriError):
+            api.eri_class_shape(bad_id)
+    assert _lib.ERI_NUM_CLASS_IDS == 881
 
 
 def test_paper512_stream_validates_before_touching_the_device():
@@ -46,7 +55,7 @@ def test_paper512_stream_validates_before_touching_the_device():
     ok, bad = _lib.ERI_OK, _lib.ERI_E_INVALID
     assert lib.eri_pack_paper512_stream(None, 0, 10, 16, None, None) == ok
     assert lib.eri_pack_paper512_stream(4096, 1, 0, 16, 8192, None) == bad      # n_eri < 1
-    assert lib.eri_pack_paper512_stream(4096, 1, 10001, 16, 8192, None) == bad  # n_eri > 10000
+    assert lib.eri_pack_paper512_stream(4096, 1, 50626, 16, 8192, None) == bad  # n_eri > 50625
     assert lib.eri_pack_paper512_stream(4096, 1, 10, 1, 8192, None) == bad      # bits < 2
     assert lib.eri_pack_paper512_stream(4096, 1, 10, 25, 8192, None) == bad     # bits > 24
     assert lib.eri_pack_paper512_stream(4098, 1, 10, 16, 8192, None) == bad     # misaligned
@@ -60,9 +69,10 @@ C_CLIENT = r"""
 #include "eri.h"
 int main(void) {
     int32_t ne = 0, nr = 0;
-    if (eri_class_id(3, 3, 3, 3) != 255 || eri_class_id(4, 0, 0, 0) != -1) return 1;
+    if (eri_class_id(3, 3, 3, 3) != 255 || eri_class_id(4, 0, 0, 0) != 756 || eri_class_id(5, 0, 0, 0) != -1) return 1;
     if (eri_class_shape(255, &ne, &nr) != ERI_OK || ne != 10000 || nr != 7) return 2;
-    if (eri_class_shape(256, &ne, &nr) != ERI_E_INVALID) return 3;
+    if (eri_class_shape(256, &ne, &nr) != ERI_E_INVALID || ERI_NUM_CLASS_IDS != 881) return 3;
+    if (eri_class_shape(ERI_NUM_CLASS_IDS - 1, &ne, &nr) != ERI_OK || ne != 50625 || nr != 9) return 3;
     if (strcmp(eri_status_string(ERI_E_NUMERIC), "ERI_E_NUMERIC") != 0) return 4;
     if (eri_pack_paper512_stream(NULL, 0, 10, 16, NULL, NULL) != ERI_OK) return 5;
     if (eri_pack_paper512_stream((const void *)4096, 1, 10, 25, (void *)8192, NULL) != ERI_E_INVALID)

@@ -42,10 +42,14 @@ def test_invalid_shells_fail_before_the_device():
     with pytest.raises(api.EriError) as e:
         api.eri_plan_create(sh, np.zeros((1, 4), dtype=np.int32))
     assert e.value.status == _lib.ERI_E_INVALID
-    sh = W.make_shellset(np.zeros((1, 3)), [4], [[1.0]], [[1.0]])
+    sh = W.make_shellset(np.zeros((1, 3)), [5], [[1.0]], [[1.0]])  # h shells: beyond L = 4
     with pytest.raises(api.EriError) as e:
         api.eri_plan_create(sh, np.zeros((1, 4), dtype=np.int32))
     assert e.value.status == _lib.ERI_E_UNSUPPORTED
+    sh = W.make_shellset(np.zeros((1, 3)), [-1], [[1.0]], [[1.0]])
+    with pytest.raises(api.EriError) as e:
+        api.eri_plan_create(sh, np.zeros((1, 4), dtype=np.int32))
+    assert e.value.status == _lib.ERI_E_INVALID
     sh = W.make_shellset(np.array([[np.nan, 0.0, 0.0]]), [0], [[1.0]], [[1.0]])
     with pytest.raises(api.EriError) as e:
         api.eri_plan_create(sh, np.zeros((1, 4), dtype=np.int32))

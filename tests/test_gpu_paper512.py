@@ -6,7 +6,7 @@ import pytest
 import torch
 
 import oracle
-from paper_2303_13632_gb300 import api
+from paper_2303_13632_gb300 import _lib, api
 from test_gpu_parity import mixed_workload
 
 pytestmark = pytest.mark.gpu
@@ -58,7 +58,7 @@ def test_plan_relayout_matches_dense_output(bits):
     scales = torch.empty(sb // 4, dtype=torch.float32, device="cuda")
     s = torch.cuda.current_stream()
     api.eri_compute_compressed(plan, bits, packed, scales, s)
-    total, _ = api.eri_paper512_class_offset(plan, bits, 256)
+    total, _ = api.eri_paper512_class_offset(plan, bits, _lib.ERI_NUM_CLASS_IDS)
     chunks = torch.full((total // 4,), -1, dtype=torch.int32, device="cuda")
     api.eri_pack_paper512(plan, bits, packed, chunks, s)
     api.eri_sync(plan, s)

@@ -98,6 +98,22 @@ def test_os_matches_mcmurchie_davidson_all_classes(cls):
     assert np.max(np.abs(a - b)) <= 2e-12 * scale
 
 
+G_CLASSES = [c for c in all_classes(4) if 4 in c]
+
+
+def test_os_matches_mcmurchie_davidson_g_classes():
+    """The 369 classes with a g shell (L = 4), one quartet each: the two evaluators agree."""
+    assert len(G_CLASSES) == 369
+    rng = np.random.default_rng(2000)
+    Ls = (0, 1, 2, 3, 4)
+    pool = W.random_primitive_pool(rng, 3, Ls=Ls)
+    for cls in G_CLASSES:
+        q = W.random_class_quartets(rng, cls, 1, 3, Ls=Ls)
+        a, _ = oracle.eri_batch(pool, q, "os")
+        b, _ = oracle.eri_batch(pool, q, "md")
+        assert np.max(np.abs(a - b)) <= 2e-12 * max(1.0, np.max(np.abs(a))), cls
+
+
 def test_os_matches_md_contracted():
     rng = np.random.default_rng(7)
     pool = W.random_contracted_pool(rng, 3, K=3, Ls=(0, 1, 2, 3))
@@ -117,7 +133,8 @@ def random_quartet_shells(rng, cls, K=1):
     return shells_from(centers, list(cls), exps, coefs)
 
 
-@pytest.mark.parametrize("cls", [(1, 0, 2, 1), (3, 1, 2, 2), (2, 2, 3, 0), (3, 3, 1, 1)])
+@pytest.mark.parametrize("cls", [(1, 0, 2, 1), (3, 1, 2, 2), (2, 2, 3, 0), (3, 3, 1, 1), (4, 2, 1, 3),
+                                 (4, 4, 2, 0)])
 @pytest.mark.parametrize("method", ["md", "os"])
 def test_eightfold_symmetry(cls, method):
     """Sec. II-B: [ab|cd] = [ba|cd] = [ab|dc] = [cd|ab] = ... (8 variants)."""
@@ -134,7 +151,7 @@ def test_eightfold_symmetry(cls, method):
         np.testing.assert_allclose(np.transpose(v, axes), w, rtol=0, atol=1e-13)
 
 
-@pytest.mark.parametrize("cls", [(1, 1, 1, 1), (3, 2, 2, 1), (0, 3, 3, 0)])
+@pytest.mark.parametrize("cls", [(1, 1, 1, 1), (3, 2, 2, 1), (0, 3, 3, 0), (4, 1, 0, 4)])
 @pytest.mark.parametrize("method,tol", [("md", 1e-15), ("os", 1e-12)])
 def test_translation_invariance(cls, method, tol):
     rng = np.random.default_rng(12)
@@ -167,7 +184,8 @@ def monomial_rotation(L, R):
     return M
 
 
-@pytest.mark.parametrize("cls", [(1, 0, 0, 0), (1, 1, 1, 1), (2, 1, 3, 0), (3, 3, 2, 2), (2, 2, 2, 2)])
+@pytest.mark.parametrize("cls", [(1, 0, 0, 0), (1, 1, 1, 1), (2, 1, 3, 0), (3, 3, 2, 2), (2, 2, 2, 2), (4, 0, 0, 0),
+                                 (4, 3, 1, 2), (4, 4, 4, 4)])
 def test_rotational_invariance(cls):
     """Rotating every centre by R about the origin maps each Cartesian shell by the monomial
     transform of R (one normalisation per shell), so (ab|cd)_rot = M_a M_b M_c M_d (ab|cd)."""
@@ -184,7 +202,7 @@ def test_rotational_invariance(cls):
     np.testing.assert_allclose(w, pred, rtol=0, atol=1e-13 * max(1, np.max(np.abs(v))))
 
 
-@pytest.mark.parametrize("cls", [(1, 1, 1, 1), (2, 1, 2, 1), (3, 0, 2, 2), (3, 3, 3, 3)])
+@pytest.mark.parametrize("cls", [(1, 1, 1, 1), (2, 1, 2, 1), (3, 0, 2, 2), (3, 3, 3, 3), (4, 2, 4, 1)])
 def test_schwarz_inequality(cls):
     """|(ab|cd)| <= sqrt((ab|ab)(cd|cd)) for every component."""
     rng = np.random.default_rng(14)

@@ -318,6 +318,21 @@ eri_status_t eri_compute_compressed_class(eri_plan_t plan, int32_t cls, int32_t 
 eri_status_t eri_compute_compressed_batched(eri_plan_t plan, int32_t bits, void *d_packed,
                                             float *d_scales, void *stream);
 
+/* eri_compute_compressed (same outputs, same layout) as ONE persistent launch of one kernel
+ * for every class of the plan: the classes' quartets are cut into tiles (up to 128 quartets of
+ * one class) that the resident CTAs pull from a single work queue (an atomic counter), so
+ * quartets of uneven class and contraction degree balance across the GPU without per-class
+ * launches.  The kernel takes the angular momenta at run time (the kernel of the classes with a
+ * g shell, see the class-id rule above): geometry, roots and B, C in FP64 (rounded to FP32 in
+ * ERI_MIXED), the four-index Rys recursion and the quadrature in the plan's precision, sums over
+ * primitives in FP64; each tile is compressed in the same launch (b_max and eps per quartet,
+ * Eq. 9; codes, Eq. 10).  Every class runs in the plan's precision (per-class overrides are not
+ * used here).  d_packed is zeroed on `stream` first (tiles OR their shared edge words in); the
+ * plan keeps a class table and reuses its scratch buffer.  Codes agree with eri_compute_compressed
+ * to +-1 (a different order of the arithmetic for classes without a g shell).  Asynchronous. */
+eri_status_t eri_compute_compressed_queue(eri_plan_t plan, int32_t bits, void *d_packed,
+                                          float *d_scales, void *stream);
+
 /* Picks, per canonical class of the plan and for the plan's precision and `bits`, the faster
  * persistent launch (thread-per-quartet or shared-memory kernel where both exist; grid of all
  * resident CTAs, one or two CTAs per SM) by timing each candidate on the plan's own quartets

@@ -88,6 +88,7 @@ SIGNATURES = {
     "eri_sync": (_i32, [_p, _p]),
     "eri_backward": (_i32, [_p, _p, _p, _p, _p]),
     "eri_compute_compressed_batched": (_i32, [_p, _i32, _p, _p, _p]),
+    "eri_compute_compressed_queue": (_i32, [_p, _i32, _p, _p, _p]),
     "eri_autotune": (_i32, [_p, _i32, _p, _p, ctypes.c_char_p, _p]),
     "eri_status_string": (ctypes.c_char_p, [_i32]),
     "eri_plan_num_basis_functions": (_i32, [_p, _i64p]),

@@ -247,6 +247,11 @@ def eri_compute_compressed_batched(plan: Plan, bits: int, packed, scales, stream
                                                      _stream_handle(stream)), "eri_compute_compressed_batched")
 
 
+def eri_compute_compressed_queue(plan: Plan, bits: int, packed, scales, stream=None) -> None:
+    check(_lib.load().eri_compute_compressed_queue(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales),
+                                                   _stream_handle(stream)), "eri_compute_compressed_queue")
+
+
 def eri_autotune(plan: Plan, bits: int, packed, scales, cache_path: str | None = None, stream=None) -> None:
     path = cache_path.encode() if cache_path else None
     check(_lib.load().eri_autotune(plan.handle, bits, _dev_ptr(packed), _dev_ptr(scales), path,

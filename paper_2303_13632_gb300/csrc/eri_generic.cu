@@ -18,6 +18,7 @@
 // Compressed output (Sec. II-D) then takes two more launches over the FP64 values: b_max and eps
 // per quartet (Eq. 9), and the codes (Eq. 10) packed one output word per thread.
 #include <algorithm>
+#include <vector>
 
 #include "eri_internal.h"
 #include "eri_kernels.cuh"
@@ -27,6 +28,7 @@ namespace eri {
 namespace {
 
 constexpr int kGenThreads = 256;
+constexpr int kGenAcc = 8;  // outputs per thread summed over primitives in registers
 // B, C values per (quartet, root): the slots of phase_setup plus C00 relative to B and C00'
 // relative to D
 constexpr int kGenCB = S_N, kGenCD = S_N + 3, kGenSN = S_N + 6;
@@ -46,7 +48,7 @@ struct GenShape {
 };
 
 template <typename R>
-GenShape gen_shape(const int L[4]) {
+GenShape gen_shape(const int L[4], int qmax = 64) {
     GenShape g{};
     for (int k = 0; k < 4; ++k) {
         g.L[k] = L[k];
@@ -57,27 +59,35 @@ GenShape gen_shape(const int L[4]) {
     g.iblk = (L[0] + 1) * (L[1] + 1) * (L[2] + 1) * (L[3] + 1);
     const int geo = G_N * 8, bc = g.nrys * kGenSN * (int)sizeof(R), ib = 3 * g.nrys * g.iblk * (int)sizeof(R);
     const int perq = geo + bc + ib + 16;
-    g.q = std::max(1, std::min(64, (96 * 1024) / perq));
+    // quartets per CTA: within the shared-memory budget, and (for classes of at most
+    // kGenThreads * kGenAcc outputs) few enough that the primitive sums stay in registers
+    g.q = std::max(1, std::min(qmax, (96 * 1024) / perq));
+    if (g.neri <= kGenThreads * kGenAcc) g.q = std::max(1, std::min(g.q, kGenThreads * kGenAcc / g.neri));
     g.bc_off = g.q * geo;
     g.i_off = ((g.bc_off + g.q * bc + 15) / 16) * 16;
     g.smem = g.i_off + g.q * ib;
     return g;
 }
 
+// One tile: quartets [q0, q0 + qn) of the class of `args`, ERIs summed over primitive quartets
+// in FP64 into out[q * n_ERIQ + generic index], q = 0..qn-1 (out = the tile's first quartet).
+// Every thread of the CTA calls it; it begins and ends with a barrier.
 template <typename R>
-__global__ void __launch_bounds__(kGenThreads)
-eri_generic_kernel(ShellsDev sh, Tables tb, ClassArgs args, GenShape g, double *__restrict__ out) {
-    extern __shared__ __align__(16) unsigned char smem[];
+__device__ __forceinline__ void generic_tile(const ShellsDev &sh, const Tables &tb, const ClassArgs &args,
+                                             const GenShape &g, long long q0, int qn, double *__restrict__ out,
+                                             unsigned char *smem, int &maxprim_s) {
     double *geo_s = reinterpret_cast<double *>(smem);
     R *bc_s = reinterpret_cast<R *>(smem + g.bc_off);
     R *I_s = reinterpret_cast<R *>(smem + g.i_off);
-    __shared__ int maxprim_s;
     const int tid = threadIdx.x;
-    const long long q0 = (long long)blockIdx.x * g.q;
-    const int qn = (int)((args.nq - q0) < g.q ? (args.nq - q0) : g.q);
     const int La = g.L[0], Lb = g.L[1], Lc = g.L[2], Ld = g.L[3];
     // strides of I(i, j, k, l) within one (root, axis) block
     const int sk = Ld + 1, sj = (Lc + 1) * sk, si = (Lb + 1) * sj;
+    const bool in_regs = qn * g.neri <= kGenThreads * kGenAcc;
+    double acc[kGenAcc];
+#pragma unroll
+    for (int k = 0; k < kGenAcc; ++k) acc[k] = 0.0;
+    __syncthreads();
     if (tid == 0) maxprim_s = 1;
     __syncthreads();
     for (int prim = 0; prim < maxprim_s; ++prim) {
@@ -167,9 +177,11 @@ eri_generic_kernel(ShellsDev sh, Tables tb, ClassArgs args, GenShape g, double *
                         }
         }
         __syncthreads();
-        // D: quadrature of each (quartet, output); primitive quartets summed in FP64
+        // D: quadrature of each (quartet, output); primitive quartets summed in FP64, in the
+        // thread's registers when the tile has at most kGenAcc outputs per thread (the same
+        // outputs every primitive), else in `out`
         const bool last = prim + 1 == maxprim_s;
-        for (int it = tid; it < qn * g.neri; it += kGenThreads) {
+        auto quad = [&](int it, double *&dst) -> R {
             const int q = it / g.neri, o = it - q * g.neri;
             int t = o;
             const int id = t % g.n[3];
@@ -186,14 +198,44 @@ eri_generic_kernel(ShellsDev sh, Tables tb, ClassArgs args, GenShape g, double *
             const R *Iz = I_s + (size_t)(q * 3 + 2) * g.nrys * g.iblk + off[2];
             R s = (R)0;
             for (int mu = 0; mu < g.nrys; ++mu) s = fma(Ix[mu * g.iblk] * Iy[mu * g.iblk], Iz[mu * g.iblk], s);
-            double *dst = out + (q0 + q) * (long long)g.neri + ia * args.ostride[0] + ib * args.ostride[1] +
-                          ic * args.ostride[2] + id * args.ostride[3];
-            const double v = (prim == 0 ? 0.0 : *dst) + RTraits<R>::to_f64(s);
-            *dst = v;
-            if (last && !(fabs(v) <= 1.7976931348623157e308)) atomicOr(args.err, 1);
+            dst = out + q * (long long)g.neri + ia * args.ostride[0] + ib * args.ostride[1] + ic * args.ostride[2] +
+                  id * args.ostride[3];
+            return s;
+        };
+        if (in_regs) {
+#pragma unroll
+            for (int k = 0; k < kGenAcc; ++k) {
+                const int it = tid + k * kGenThreads;
+                if (it < qn * g.neri) {
+                    double *dst;
+                    acc[k] += RTraits<R>::to_f64(quad(it, dst));
+                    if (last) {
+                        *dst = acc[k];
+                        if (!(fabs(acc[k]) <= 1.7976931348623157e308)) atomicOr(args.err, 1);
+                    }
+                }
+            }
+        } else {
+            for (int it = tid; it < qn * g.neri; it += kGenThreads) {
+                double *dst;
+                const R s = quad(it, dst);
+                const double v = (prim == 0 ? 0.0 : *dst) + RTraits<R>::to_f64(s);
+                *dst = v;
+                if (last && !(fabs(v) <= 1.7976931348623157e308)) atomicOr(args.err, 1);
+            }
         }
         __syncthreads();
     }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kGenThreads)
+eri_generic_kernel(ShellsDev sh, Tables tb, ClassArgs args, GenShape g, double *__restrict__ out) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int maxprim_s;
+    const long long q0 = (long long)blockIdx.x * g.q;
+    const int qn = (int)((args.nq - q0) < g.q ? (args.nq - q0) : g.q);
+    generic_tile<R>(sh, tb, args, g, q0, qn, out + q0 * (long long)g.neri, smem, maxprim_s);
 }
 
 // eps = b_max / (2^(bits-1) - 1) of each quartet (Eq. 9), b_max from the FP64 values; one warp
@@ -254,7 +296,138 @@ long long chunk_quartets(int neri, size_t scratch_bytes) {
     return c;
 }
 
+// ---------------------------------------------------------------------------------------------
+// One persistent launch for every class of a plan: a work queue of tiles (class, quartets
+// [q0, q0 + q)) over all classes, pulled by the resident CTAs from one atomic counter, so
+// quartets of uneven class and contraction degree balance across the GPU.  Each tile's FP64
+// values go to the CTA's slot of a scratch buffer and are compressed in the same launch: b_max
+// and eps per quartet (Eq. 9), then the codes (Eq. 10) packed one output word per thread; words
+// that a tile shares with its neighbour tile are OR-ed in (the output is zeroed before the
+// launch), the others stored.
+
+struct QueueClass {
+    ClassArgs a;           // quartets, permutation, output strides, packed segment and scales
+    GenShape g;            // shape and shared-memory layout (common quartet cap)
+    long long first_tile;  // first tile of the class in the queue
+};
+
+constexpr int kQueueQmax = 128;
+
+template <typename R>
+__global__ void __launch_bounds__(kGenThreads)
+eri_queue_kernel(ShellsDev sh, Tables tb, const QueueClass *__restrict__ classes, int n_classes,
+                 long long n_tiles, unsigned long long *counter, double *__restrict__ scratch,
+                 long long slot_doubles, int bits, int *err) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int maxprim_s;
+    __shared__ long long item_s;
+    __shared__ int cls_s;
+    __shared__ unsigned long long bmax_s[kQueueQmax];
+    __shared__ float eps_s[kQueueQmax];
+    const int tid = threadIdx.x;
+    double *vals = scratch + (long long)blockIdx.x * slot_doubles;
+    const double M = (double)((1u << (bits - 1)) - 1u);
+    const uint32_t mask = (1u << bits) - 1u;
+    for (;;) {
+        if (tid == 0) {
+            item_s = (long long)atomicAdd(counter, 1ull);
+            int lo = 0, hi = n_classes - 1;  // last class whose first tile <= item
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) / 2;
+                if (classes[mid].first_tile <= item_s) lo = mid; else hi = mid - 1;
+            }
+            cls_s = lo;
+        }
+        __syncthreads();
+        const long long item = item_s;
+        if (item >= n_tiles) break;
+        const QueueClass &qc = classes[cls_s];
+        const ClassArgs a = qc.a;
+        const GenShape g = qc.g;
+        const long long q0 = (item - qc.first_tile) * g.q;
+        const int qn = (int)((a.nq - q0) < g.q ? (a.nq - q0) : g.q);
+        generic_tile<R>(sh, tb, a, g, q0, qn, vals, smem, maxprim_s);
+        // b_max per quartet (non-negative IEEE values order like their bit patterns)
+        for (int q = tid; q < qn; q += kGenThreads) bmax_s[q] = 0ull;
+        __syncthreads();
+        for (int it = tid; it < qn * g.neri; it += kGenThreads) {
+            const double v = fabs(vals[it]);
+            if (!(v <= 1.7976931348623157e308)) atomicOr(err, 1);
+            atomicMax(bmax_s + it / g.neri, (unsigned long long)__double_as_longlong(v));
+        }
+        __syncthreads();
+        for (int q = tid; q < qn; q += kGenThreads) {
+            const float e = (float)(__longlong_as_double((long long)bmax_s[q]) / M);
+            eps_s[q] = e;
+            a.scales[q0 + q] = e;
+        }
+        __syncthreads();
+        // codes of the tile's values [c0, c1) at stream bits [c0 * bits, c1 * bits)
+        const long long c0 = q0 * g.neri, c1 = (q0 + qn) * (long long)g.neri;
+        const long long b0 = c0 * bits, b1 = c1 * bits;
+        for (long long w = (b0 >> 5) + tid; w < ((b1 + 31) >> 5); w += kGenThreads) {
+            const long long wb = w * 32;
+            long long first = wb / bits, last = (wb + 31) / bits;
+            first = first < c0 ? c0 : first;
+            last = last >= c1 ? c1 - 1 : last;
+            uint32_t word = 0u;
+            for (long long c = first; c <= last; ++c) {
+                const float e = eps_s[(c - c0) / g.neri];
+                const double inv = e > 0.0f ? 1.0 / (double)e : 0.0;
+                double r = round(vals[c - c0] * inv);
+                r = r > M ? M : (r < -M ? -M : r);
+                const uint32_t code = (uint32_t)(int)r & mask;
+                const long long sh_ = c * bits - wb;
+                word |= sh_ >= 0 ? code << sh_ : code >> (-sh_);
+            }
+            if (wb >= b0 && wb + 32 <= b1)
+                a.packed[w] = word;
+            else
+                atomicOr(a.packed + w, word);
+        }
+        __syncthreads();
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_queue(const ShellsDev &sh, const Tables &tb, const QueueSpec *classes, int n_classes,
+                         bool mixed, int bits, int *err, void *d_table, unsigned long long *d_counter,
+                         double *scratch, size_t scratch_bytes, int device, cudaStream_t stream) {
+    if (n_classes <= 0) return cudaSuccess;
+    std::vector<QueueClass> qc(n_classes);
+    long long tiles = 0;
+    int smem = 0;
+    long long slot = 1;
+    for (int i = 0; i < n_classes; ++i) {
+        qc[i].a = classes[i].a;
+        qc[i].g = mixed ? gen_shape<float>(classes[i].L, kQueueQmax) : gen_shape<double>(classes[i].L, kQueueQmax);
+        qc[i].first_tile = tiles;
+        tiles += (classes[i].a.nq + qc[i].g.q - 1) / qc[i].g.q;
+        smem = std::max(smem, qc[i].g.smem);
+        slot = std::max(slot, (long long)qc[i].g.q * qc[i].g.neri);
+    }
+    if (smem > 227 * 1024 - 2048) return cudaErrorInvalidValue;
+    void (*kern)(ShellsDev, Tables, const QueueClass *, int, long long, unsigned long long *, double *,
+                 long long, int, int *) = mixed ? eri_queue_kernel<float> : eri_queue_kernel<double>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0, sms = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kGenThreads, smem)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device)) != cudaSuccess) return e;
+    long long grid = std::min<long long>(tiles, (long long)std::max(1, per_sm) * sms);
+    grid = std::min<long long>(grid, (long long)(scratch_bytes / (sizeof(double) * (size_t)slot)));
+    if (grid < 1) return cudaErrorInvalidValue;
+    if ((size_t)n_classes * sizeof(QueueClass) > queue_table_bytes()) return cudaErrorInvalidValue;
+    e = cudaMemcpyAsync(d_table, qc.data(), (size_t)n_classes * sizeof(QueueClass), cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_counter, 0, sizeof(unsigned long long), stream);
+    if (e != cudaSuccess) return e;
+    kern<<<(unsigned)grid, kGenThreads, smem, stream>>>(sh, tb, static_cast<const QueueClass *>(d_table), n_classes,
+                                                        tiles, d_counter, scratch, slot, bits, err);
+    return cudaGetLastError();
+}
+
+size_t queue_table_bytes() { return (size_t)kNumClassIds * sizeof(QueueClass); }
 
 cudaError_t launch_generic(const ShellsDev &sh, const Tables &tb, const ClassArgs &a, const int L[4],
                            bool mixed, double *scratch, size_t scratch_bytes, cudaStream_t stream) {

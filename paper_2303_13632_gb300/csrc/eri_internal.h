@@ -53,9 +53,23 @@ inline bool class_has_g(int cls) { return cls >= 256; }
 // FP64 setup values, FP64 sums over primitives.
 cudaError_t launch_generic(const ShellsDev &sh, const Tables &tb, const ClassArgs &a, const int L[4],
                            bool mixed, double *scratch, size_t scratch_bytes, cudaStream_t stream);
-// launches launch_generic makes for nq quartets (kernel names in *names, for reports)
+// launches launch_generic makes for nq quartets of n_ERIQ = neri, and the kernel names
 int generic_launches(long long nq, int neri, bool compressed, size_t scratch_bytes);
 const char *generic_kernel_names(bool mixed, bool compressed);
+
+// One persistent launch of the run-time-L kernel over every class of a plan from one work queue
+// of tiles, compressing each tile in the same launch (eri_generic.cu).  classes[i]: the canonical
+// angular momenta and the arguments of one non-empty class (compressed output; the packed output
+// must be zero before the launch).  d_table: queue_table_bytes() of device memory, d_counter one
+// device word, scratch: FP64 values of one tile per resident CTA.
+struct QueueSpec {
+    int L[4];
+    ClassArgs a;
+};
+size_t queue_table_bytes();
+cudaError_t launch_queue(const ShellsDev &sh, const Tables &tb, const QueueSpec *classes, int n_classes,
+                         bool mixed, int bits, int *err, void *d_table, unsigned long long *d_counter,
+                         double *scratch, size_t scratch_bytes, int device, cudaStream_t stream);
 
 // Quartets per launch of the split setup/recurrence path (a multiple of 32 so that every chunk
 // starts on a 32-bit word of the packed stream) and the widest setup record (n_Rys = 7).

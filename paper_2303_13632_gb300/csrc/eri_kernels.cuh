@@ -950,11 +950,13 @@ __device__ __forceinline__ void class_tile(const ShellsDev &sh, const Tables &tb
                 rg[RG_SWCD] = to_r<R>(geo[G_SWCD]);
             }
             __syncthreads();
-            // A1: roots, weights, B and C per (quartet, root); the mixed path forms B and C in
-            // two-float FP32 exactly as the split path's setup kernel does
+            // A1: roots, weights, B and C per (quartet, root).  For primitive plans (no Kahan
+            // sums) the mixed path forms B and C in two-float FP32 exactly as the split path's
+            // setup kernel does (the persistent form of those plans then matches the per-class
+            // launches bit for bit); contracted plans keep the FP64 formation, cheaper per item
             for (int it = tid; it < C::Q * C::NRYS; it += C::THREADS) {
                 int q = it / C::NRYS, mu = it % C::NRYS;
-                if constexpr (sizeof(R) == 4) {
+                if constexpr (sizeof(R) == 4 && !KAHAN) {
                     const double *geo = geo_s + q * G_N;
                     SetupTF<C> pre;
                     pre.init(geo);

@@ -54,6 +54,49 @@ __global__ void __launch_bounds__(256) paper512_kernel(const uint32_t *__restric
     }
 }
 
+// The same with one thread per quarter chunk (four consecutive output words, one 16-byte store):
+// the quartet and chunk indices are found once per four words, and the field indices lo / bits
+// and (lo + 31) / bits by a multiply with ceil(2^16 / bits) (exact for lo < 2^9 and bits <= 24:
+// the product overshoots lo / bits by less than lo / 2^16 < 1 / bits).  dst 16-byte aligned.
+__global__ void __launch_bounds__(256) paper512_kernel4(const uint32_t *__restrict__ src,
+                                                        unsigned long long q0, unsigned nq,
+                                                        unsigned n_eri, unsigned n_cs, unsigned bits,
+                                                        uint4 *__restrict__ dst) {
+    const unsigned F = 512u / bits;
+    const unsigned inv = (65536u + bits - 1u) / bits;
+    const unsigned total = nq * n_cs * (kChunkWords / 4);
+    const uint32_t mask = (1u << bits) - 1u;
+    for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
+        const unsigned ch = t >> 2, k0 = (t & 3u) * 4u;
+        const unsigned i = ch / n_cs, c = ch - i * n_cs;
+        const unsigned long long qbit = (q0 + i) * (unsigned long long)n_eri * bits;
+        const uint32_t *qs = src + (qbit >> 5);
+        const unsigned off = (unsigned)qbit & 31u;
+        const unsigned nf = min(F, n_eri - c * F);
+        uint32_t out[4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            const unsigned lo = 32u * (k0 + kk);
+            const unsigned j0 = (lo * inv) >> 16;
+            uint32_t o = 0;
+            if (j0 < nf) {
+                const unsigned j1 = min(((lo + 31u) * inv) >> 16, nf - 1u);
+                for (unsigned j = j0; j <= j1; ++j) {
+                    const unsigned b = off + (c * F + j) * bits;
+                    const unsigned w = b >> 5, s = b & 31u;
+                    uint32_t v = qs[w] >> s;
+                    if (s + bits > 32u) v |= qs[w + 1] << (32u - s);
+                    v &= mask;
+                    const int d = (int)(j * bits) - (int)lo;
+                    o |= d >= 0 ? v << d : v >> (-d);
+                }
+            }
+            out[kk] = o;
+        }
+        dst[t] = make_uint4(out[0], out[1], out[2], out[3]);
+    }
+}
+
 }  // namespace
 }  // namespace eri
 
@@ -75,14 +118,20 @@ extern "C" eri_status_t eri_pack_paper512_stream(const void *d_stream, int64_t n
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1)
         return ERI_E_CUDA;
+    const bool wide = reinterpret_cast<uintptr_t>(d_chunks) % 16 == 0;
     for (long long q0 = 0; q0 < n_quartets; q0 += per_piece) {
         const long long nq = n_quartets - q0 < per_piece ? n_quartets - q0 : per_piece;
         const long long words = nq * n_cs * eri::kChunkWords;
-        long long blocks = (words + 255) / 256;
+        long long blocks = ((wide ? words / 4 : words) + 255) / 256;
         if (blocks > 8ll * sms) blocks = 8ll * sms;  // grid-stride beyond 8 resident CTAs per SM
-        eri::paper512_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
-            src, (unsigned long long)q0, (unsigned)nq, (unsigned)n_eri, (unsigned)n_cs,
-            (unsigned)bits, dst + q0 * n_cs * eri::kChunkWords);
+        if (wide)
+            eri::paper512_kernel4<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+                src, (unsigned long long)q0, (unsigned)nq, (unsigned)n_eri, (unsigned)n_cs, (unsigned)bits,
+                reinterpret_cast<uint4 *>(dst + q0 * n_cs * eri::kChunkWords));
+        else
+            eri::paper512_kernel<<<(unsigned)blocks, 256, 0, (cudaStream_t)stream>>>(
+                src, (unsigned long long)q0, (unsigned)nq, (unsigned)n_eri, (unsigned)n_cs,
+                (unsigned)bits, dst + q0 * n_cs * eri::kChunkWords);
         if (cudaGetLastError() != cudaSuccess) return ERI_E_CUDA;
     }
     return ERI_OK;

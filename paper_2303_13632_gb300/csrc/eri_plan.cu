@@ -213,6 +213,7 @@ struct eri_plan_s {
     long long n_bf = 0;          // basis functions (sum of the shells' Cartesian components)
     float *d_D32 = nullptr;      // FP32 copy of the density of eri_digest_jk (lazy)
     void *d_digest = nullptr;    // per-class parameters of eri_digest_jk's launch (lazy)
+    void *d_queue = nullptr;     // class table and tile counter of the work-queue launch (lazy)
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
     double *d_pairs = nullptr;    // primitive-pair table (n_prims^2 records), or null
     // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
@@ -258,6 +259,7 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_bfoff);
     cudaFree(p->d_D32);
     cudaFree(p->d_digest);
+    cudaFree(p->d_queue);
     cudaFree(p->d_setup);
     cudaFree(p->d_pairs);
     cudaFree(p->d_counters);
@@ -1149,6 +1151,42 @@ eri_status_t eri_compute_compressed_batched(eri_plan_t plan, int32_t bits, void 
         plan->g_scales = d_scales;
     }
     return cuda_status(cudaGraphLaunch(plan->graph, (cudaStream_t)stream));
+}
+
+eri_status_t eri_compute_compressed_queue(eri_plan_t plan, int32_t bits, void *d_packed,
+                                          float *d_scales, void *stream) {
+    if (!plan || bits < 2 || bits > 24) return ERI_E_INVALID;
+    if (plan->nq > 0 && (!d_packed || !d_scales)) return ERI_E_INVALID;
+    if (reinterpret_cast<uintptr_t>(d_packed) % 4 || reinterpret_cast<uintptr_t>(d_scales) % 4)
+        return ERI_E_INVALID;
+    if (plan->nq == 0) return ERI_OK;
+    cudaSetDevice(plan->device);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = ensure_scratch(plan);
+    const size_t table = queue_table_bytes();
+    if (e == cudaSuccess && !plan->d_queue) e = cudaMalloc(&plan->d_queue, table + 16);
+    if (e != cudaSuccess) return cuda_status(e);
+    size_t total = 0;
+    eri_output_bytes(plan, bits, &total, nullptr);
+    // tiles OR their edge words into the output
+    if ((e = cudaMemsetAsync(d_packed, 0, total, s)) != cudaSuccess) return cuda_status(e);
+    std::vector<QueueSpec> spec;
+    size_t off = 0;
+    for (int c = 0; c < kNumClassIds; ++c) {
+        if (plan->count[c] > 0) {
+            QueueSpec q;
+            class_ls(canonicalise(c).cls, q.L);
+            q.a = class_args(plan, c, nullptr, bits, d_packed, d_scales, off);
+            spec.push_back(q);
+        }
+        off += packed_segment_bytes(plan->count[c], class_neri(c), bits);
+    }
+    ShellsDev sh{plan->d_cx, plan->d_cy, plan->d_cz, plan->d_pofs, plan->d_nprim, plan->d_exps, plan->d_cn};
+    e = launch_queue(sh, plan->tables, spec.data(), (int)spec.size(), plan->precision == ERI_MIXED, bits,
+                     plan->d_err, plan->d_queue,
+                     reinterpret_cast<unsigned long long *>(static_cast<char *>(plan->d_queue) + table),
+                     static_cast<double *>(plan->d_setup), kScratchBytes, plan->device, s);
+    return cuda_status(e);
 }
 
 eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *d_scales,

@@ -706,7 +706,7 @@ def run_gshell(args):
     Ls = (0, 1, 2, 3, 4)
     rng = np.random.default_rng(2303_13632 + 6)
     pool = W.random_primitive_pool(rng, 2048, Ls=Ls)
-    ids = W.g_class_ids()
+    ids = [c for c in W.g_class_ids() if ONLY is None or c in ONLY]
     res, acc = {}, {}
     t = {"mixed": 0.0, "fp64": 0.0}
     total = 0
@@ -956,7 +956,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--details", default=None)
     ap.add_argument("--classes", default=None,
-                    help="comma-separated class ids ((La*4+Lb)*4+Lc)*4+Ld; profiling only")
+                    help="comma-separated class ids (see eri_class_id) for the sweep and gshell workloads; profiling only")
     args = ap.parse_args()
     global ONLY
     if args.classes:

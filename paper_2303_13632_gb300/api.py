@@ -331,3 +331,42 @@ def eri_convert_device(x, f_out, back_out, stream=None) -> None:
     """Integer-pipe binary64 -> binary32 -> binary64 conversions of the setup stages."""
     check(_lib.load().eri_convert_device(_dev_ptr(x), x.numel(), _dev_ptr(f_out), _dev_ptr(back_out),
                                          _stream_handle(stream)), "eri_convert_device")
+
+
+class Engine:
+    """Shell-quartet access in the style of libint's engine (the library interface the paper's
+    conclusion points to): ERIs of a list of shell quartets, returned per quartet as an array of
+    shape (n_a, n_b, n_c, n_d) in the caller's order, Cartesian components in the order of
+    include/eri.h (a_x from L down, then a_y; libint's Cartesian order).  Each call builds one
+    plan of the quartets, runs eri_compute on the device and reorders the class-sorted output on
+    the host: a convenience over eri_plan_create / eri_compute / eri_plan_quartet_order for
+    integrating callers, not a faster path."""
+
+    def __init__(self, shells, precision: str = "fp64", device: int = 0):
+        self.shells = shells
+        self.precision = precision
+        self.device = device
+
+    def compute(self, quartets, stream=None) -> list:
+        import torch
+
+        q = np.ascontiguousarray(quartets, dtype=np.int32).reshape(-1, 4)
+        if len(q) == 0:
+            return []
+        plan = eri_plan_create(self.shells, q, precision=self.precision, device=self.device)
+        nbytes, _ = eri_output_bytes(plan, 0)
+        out = torch.empty(nbytes // 8, dtype=torch.float64, device=torch.device("cuda", self.device))
+        eri_compute(plan, out, stream)
+        eri_sync(plan, stream)
+        host = out.cpu().numpy()
+        order = eri_plan_quartet_order(plan)
+        L = np.asarray(self.shells.L)
+        dims = [(L[r] + 1) * (L[r] + 2) // 2 for r in q[order].T]
+        sizes = dims[0] * dims[1] * dims[2] * dims[3]
+        starts = np.concatenate([[0], np.cumsum(sizes)[:-1]])
+        res = [None] * len(q)
+        for k, i in enumerate(order):
+            shape = (int(dims[0][k]), int(dims[1][k]), int(dims[2][k]), int(dims[3][k]))
+            res[int(i)] = host[starts[k]:starts[k] + sizes[k]].reshape(shape)
+        plan.destroy()
+        return res

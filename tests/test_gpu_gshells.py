@@ -239,3 +239,18 @@ def test_unsupported_entry_points_for_g():
         api.eri_compute_class_noalloc(cls, "fp64", *dev, z((3, 4), torch.int32), z(3 * 45, torch.float64),
                                       z(1, torch.int32))
     assert e.value.status == _lib.ERI_E_UNSUPPORTED
+
+
+def test_engine_quartet_arrays():
+    """The libint-style Engine: per-quartet arrays (n_a, n_b, n_c, n_d) in the caller's order,
+    classes with and without a g shell, against the oracle's quartets."""
+    rng = np.random.default_rng(449)
+    pool = W.random_primitive_pool(rng, 3, Ls=LS)
+    classes = [(0, 0, 0, 0), (2, 1, 3, 0), (4, 0, 1, 2), (1, 4, 4, 0), (3, 3, 3, 3)]
+    q = np.concatenate([W.random_class_quartets(rng, c, 2, 3, Ls=LS) for c in classes])
+    q = q[rng.permutation(len(q))]
+    got = api.Engine(pool).compute(q)
+    for i, row in enumerate(q):
+        ref = oracle.eri_quartet(pool, [int(x) for x in row])
+        assert got[i].shape == ref.shape, i
+        assert np.all(fp64_ok(got[i].ravel(), ref.ravel())), i

@@ -32,6 +32,7 @@ constexpr int kGenAcc = 8;  // outputs per thread summed over primitives in regi
 // B, C values per (quartet, root): the slots of phase_setup plus C00 relative to B and C00'
 // relative to D
 constexpr int kGenCB = S_N, kGenCD = S_N + 3, kGenSN = S_N + 6;
+constexpr int kGenSNP = kGenSN + 1;  // odd stride of the (quartet, root) records: distinct banks
 
 // geometry without the choice of transfer direction (the four-index recursion needs none)
 struct GenGeo {
@@ -43,6 +44,8 @@ struct GenShape {
     int n[4];        // Cartesian components per shell
     int nrys, neri;  // roots, ERIs per quartet
     int iblk;        // 2-D integrals per (root, axis): (La+1)(Lb+1)(Lc+1)(Ld+1)
+    int iblkp;       // their stride in shared memory, odd so that the blocks the threads of a
+                     // warp build start in distinct banks
     int q;           // quartets per CTA
     int bc_off, i_off, smem;  // dynamic shared memory layout (bytes)
 };
@@ -57,7 +60,8 @@ GenShape gen_shape(const int L[4], int qmax = 64) {
     g.nrys = (L[0] + L[1] + L[2] + L[3]) / 2 + 1;
     g.neri = g.n[0] * g.n[1] * g.n[2] * g.n[3];
     g.iblk = (L[0] + 1) * (L[1] + 1) * (L[2] + 1) * (L[3] + 1);
-    const int geo = G_N * 8, bc = g.nrys * kGenSN * (int)sizeof(R), ib = 3 * g.nrys * g.iblk * (int)sizeof(R);
+    g.iblkp = g.iblk | 1;
+    const int geo = G_N * 8, bc = g.nrys * kGenSNP * (int)sizeof(R), ib = 3 * g.nrys * g.iblkp * (int)sizeof(R);
     const int perq = geo + bc + ib + 16;
     // quartets per CTA: within the shared-memory budget, and (for classes of at most
     // kGenThreads * kGenAcc outputs) few enough that the primitive sums stay in registers
@@ -115,7 +119,7 @@ __device__ __forceinline__ void generic_tile(const ShellsDev &sh, const Tables &
             const double *geo = geo_s + q * G_N;
             double x, w;
             rys_root<sizeof(R) == 4>(tb, g.nrys, mu, geo[G_T], x, w);
-            R *b = bc_s + (size_t)it * kGenSN;
+            R *b = bc_s + (size_t)it * kGenSNP;
             const double ipq = geo[G_IPQ];
             const double fq = geo[G_Q] * x * ipq, fp = geo[G_P] * x * ipq;
             b[S_B00] = to_r<R>(0.5 * x * ipq);
@@ -135,8 +139,8 @@ __device__ __forceinline__ void generic_tile(const ShellsDev &sh, const Tables &
         for (int it = tid; it < g.q * g.nrys * 3; it += kGenThreads) {
             const int q = it / (g.nrys * 3), r = it - q * g.nrys * 3;
             const int mu = r / 3, xi = r - mu * 3;
-            const R *b = bc_s + (size_t)(q * g.nrys + mu) * kGenSN;
-            R *I = I_s + ((size_t)(q * 3 + xi) * g.nrys + mu) * g.iblk;
+            const R *b = bc_s + (size_t)(q * g.nrys + mu) * kGenSNP;
+            R *I = I_s + (size_t)it * g.iblkp;  // block (q, mu, xi): consecutive threads, odd stride
             const R cA = b[S_C0X + xi], cB = b[kGenCB + xi], cC = b[S_C1X + xi], cD = b[kGenCD + xi];
             const R b00 = b[S_B00], b10 = b[S_B10], b01 = b[S_B01];
             I[0] = xi == 2 ? b[S_WZ] : (R)1;
@@ -193,11 +197,11 @@ __device__ __forceinline__ void generic_tile(const ShellsDev &sh, const Tables &
             for (int x = 0; x < 3; ++x)
                 off[x] = c_cart[La][ia][x] * si + c_cart[Lb][ib][x] * sj + c_cart[Lc][ic][x] * sk +
                          c_cart[Ld][id][x];
-            const R *Ix = I_s + (size_t)(q * 3 + 0) * g.nrys * g.iblk + off[0];
-            const R *Iy = I_s + (size_t)(q * 3 + 1) * g.nrys * g.iblk + off[1];
-            const R *Iz = I_s + (size_t)(q * 3 + 2) * g.nrys * g.iblk + off[2];
+            const R *I0 = I_s + (size_t)q * g.nrys * 3 * g.iblkp;
+            const R *Ix = I0 + off[0], *Iy = I0 + g.iblkp + off[1], *Iz = I0 + 2 * g.iblkp + off[2];
+            const int ms = 3 * g.iblkp;  // next root
             R s = (R)0;
-            for (int mu = 0; mu < g.nrys; ++mu) s = fma(Ix[mu * g.iblk] * Iy[mu * g.iblk], Iz[mu * g.iblk], s);
+            for (int mu = 0; mu < g.nrys; ++mu) s = fma(Ix[mu * ms] * Iy[mu * ms], Iz[mu * ms], s);
             dst = out + q * (long long)g.neri + ia * args.ostride[0] + ib * args.ostride[1] + ic * args.ostride[2] +
                   id * args.ostride[3];
             return s;

@@ -81,8 +81,10 @@ Canon canonicalise(int cls) {
     return c;
 }
 
+// class key of every quartet: 8 bits when every shell has L <= 3 (ids 0..255), else 10 bits
+template <typename K>
 __global__ void classify_kernel(const int4 *__restrict__ q, long long n, const int *__restrict__ L,
-                                int n_shells, uint16_t *__restrict__ keys, int *__restrict__ vals,
+                                int n_shells, K *__restrict__ keys, int *__restrict__ vals,
                                 int *__restrict__ err) {
     long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
@@ -93,7 +95,7 @@ __global__ void classify_kernel(const int4 *__restrict__ q, long long n, const i
         atomicOr(err, 4);
         keys[i] = 0;
     } else {
-        keys[i] = (uint16_t)class_id_of(L[t.x], L[t.y], L[t.z], L[t.w]);
+        keys[i] = (K)class_id_of(L[t.x], L[t.y], L[t.z], L[t.w]);
     }
     vals[i] = (int)i;
 }
@@ -128,7 +130,8 @@ __global__ void compose_kernel(int *__restrict__ perm, const int *__restrict__ o
     if (i < n) perm[i] = orig[perm[i]];
 }
 
-__global__ void histogram_kernel(const uint16_t *__restrict__ keys, long long n,
+template <typename K>
+__global__ void histogram_kernel(const K *__restrict__ keys, long long n,
                                  unsigned long long *__restrict__ counts) {
     __shared__ unsigned int h[kNumClassIds];
     for (int i = threadIdx.x; i < kNumClassIds; i += blockDim.x) h[i] = 0;
@@ -309,6 +312,67 @@ cudaError_t upload(T **dst, const std::vector<T> &src) {
     cudaError_t e = plan_malloc(dst, std::max<size_t>(1, src.size()) * sizeof(T));
     if (e != cudaSuccess) return e;
     if (!src.empty()) e = cudaMemcpy(*dst, src.data(), src.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return e;
+}
+
+// Class sort of the plan's quartets on the device: keys (class ids), stable radix sort keeping
+// the caller's order within a class, the sorted quartets, the permutation and the class counts.
+template <typename K>
+cudaError_t class_sort(eri_plan_s *p, const int4 *d_in, long long nq, const int *d_L, int n_shells,
+                       const int *d_orig) {
+    constexpr int kBits = sizeof(K) == 1 ? 8 : 10;
+    cudaError_t e = cudaSuccess;
+    K *d_keys = nullptr, *d_keys_sorted = nullptr;
+    int *d_vals = nullptr;
+    unsigned long long *d_counts = nullptr;
+    void *d_tmp = nullptr;
+    size_t tmp_bytes = 0;
+    int *d_verr = nullptr;
+    const unsigned blocks = (unsigned)((nq + 255) / 256);
+    do {
+        if ((e = plan_malloc(&d_keys, nq * sizeof(K))) != cudaSuccess) break;
+        if ((e = plan_malloc(&d_keys_sorted, nq * sizeof(K))) != cudaSuccess) break;
+        if ((e = plan_malloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
+        if ((e = plan_malloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
+        if ((e = plan_malloc(&d_verr, sizeof(int))) != cudaSuccess) break;
+        if ((e = cudaMemset(d_verr, 0, sizeof(int))) != cudaSuccess) break;
+        classify_kernel<K><<<blocks, 256>>>(d_in, nq, d_L, n_shells, d_keys, d_vals, d_verr);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        // stable radix sort on the class key keeps the caller's order within a class
+        e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_vals,
+                                            p->d_perm, (int)nq, 0, kBits);
+        if (e != cudaSuccess) break;
+        if ((e = plan_malloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
+        e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_vals,
+                                            p->d_perm, (int)nq, 0, kBits);
+        if (e != cudaSuccess) break;
+        if ((e = plan_malloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
+        gather_kernel<<<blocks, 256>>>(d_in, p->d_perm, nq, p->d_quartets);
+        if ((e = plan_malloc(&d_counts, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
+        if ((e = cudaMemset(d_counts, 0, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
+        histogram_kernel<K><<<std::min<unsigned>(blocks, 4096u), 256>>>(d_keys_sorted, nq, d_counts);
+        if ((e = cudaGetLastError()) != cudaSuccess) break;
+        unsigned long long counts[kNumClassIds];
+        if ((e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+        int verr = 0;
+        if ((e = cudaMemcpy(&verr, d_verr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
+            break;
+        if (verr) e = cudaErrorInvalidValue;  // mapped to ERI_E_INVALID below
+        for (int c = 0; c < kNumClassIds; ++c) p->count[c] = (long long)counts[c];
+        if (d_orig) {  // sorted position -> index in the caller's list
+            compose_kernel<<<blocks, 256>>>(p->d_perm, d_orig, nq);
+            e = cudaGetLastError();
+        }
+    } while (false);
+    cudaError_t sync_e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = sync_e;
+    cudaFree(d_keys);
+    cudaFree(d_keys_sorted);
+    cudaFree(d_vals);
+    cudaFree(d_counts);
+    cudaFree(d_tmp);
+    cudaFree(d_verr);
     return e;
 }
 
@@ -761,58 +825,12 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     }
 
     if (nq > 0) {
-        uint16_t *d_keys = nullptr, *d_keys_sorted = nullptr;
-        int *d_vals = nullptr;
-        unsigned long long *d_counts = nullptr;
-        void *d_tmp = nullptr;
-        size_t tmp_bytes = 0;
-        int *d_verr = nullptr;
-        const unsigned blocks = (unsigned)((nq + 255) / 256);
-        do {
-            if ((e = plan_malloc(&d_keys, nq * sizeof(uint16_t))) != cudaSuccess) break;
-            if ((e = plan_malloc(&d_keys_sorted, nq * sizeof(uint16_t))) != cudaSuccess) break;
-            if ((e = plan_malloc(&d_vals, nq * sizeof(int))) != cudaSuccess) break;
-            if ((e = plan_malloc(&p->d_perm, nq * sizeof(int))) != cudaSuccess) break;
-            if ((e = plan_malloc(&d_verr, sizeof(int))) != cudaSuccess) break;
-            if ((e = cudaMemset(d_verr, 0, sizeof(int))) != cudaSuccess) break;
-            classify_kernel<<<blocks, 256>>>(d_in, nq, d_L, n_shells, d_keys, d_vals, d_verr);
-            if ((e = cudaGetLastError()) != cudaSuccess) break;
-            // stable radix sort on the 10-bit class key keeps the caller's order within a class
-            e = cub::DeviceRadixSort::SortPairs(nullptr, tmp_bytes, d_keys, d_keys_sorted, d_vals,
-                                                p->d_perm, (int)nq, 0, 10);
-            if (e != cudaSuccess) break;
-            if ((e = plan_malloc(&d_tmp, std::max<size_t>(tmp_bytes, 1))) != cudaSuccess) break;
-            e = cub::DeviceRadixSort::SortPairs(d_tmp, tmp_bytes, d_keys, d_keys_sorted, d_vals,
-                                                p->d_perm, (int)nq, 0, 10);
-            if (e != cudaSuccess) break;
-            if ((e = plan_malloc(&p->d_quartets, nq * sizeof(int4))) != cudaSuccess) break;
-            gather_kernel<<<blocks, 256>>>(d_in, p->d_perm, nq, p->d_quartets);
-            if ((e = plan_malloc(&d_counts, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
-            if ((e = cudaMemset(d_counts, 0, kNumClassIds * sizeof(unsigned long long))) != cudaSuccess) break;
-            histogram_kernel<<<std::min<unsigned>(blocks, 4096u), 256>>>(d_keys_sorted, nq, d_counts);
-            if ((e = cudaGetLastError()) != cudaSuccess) break;
-            unsigned long long counts[kNumClassIds];
-            if ((e = cudaMemcpy(counts, d_counts, sizeof(counts), cudaMemcpyDeviceToHost)) != cudaSuccess)
-                break;
-            int verr = 0;
-            if ((e = cudaMemcpy(&verr, d_verr, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess)
-                break;
-            if (verr) e = cudaErrorInvalidValue;  // mapped to ERI_E_INVALID below
-            for (int c = 0; c < kNumClassIds; ++c) p->count[c] = (long long)counts[c];
-            if (d_orig) {  // sorted position -> index in the caller's list
-                compose_kernel<<<blocks, 256>>>(p->d_perm, d_orig, nq);
-                e = cudaGetLastError();
-            }
-        } while (false);
+        const bool g = std::find_if(Ls.begin(), Ls.end(), [](int l) { return l > 3; }) != Ls.end();
+        e = g ? class_sort<uint16_t>(p, d_in, nq, d_L, n_shells, d_orig)
+              : class_sort<uint8_t>(p, d_in, nq, d_L, n_shells, d_orig);
         cudaError_t sync_e = cudaDeviceSynchronize();
         if (e == cudaSuccess) e = sync_e;
         if (own_in) cudaFree(d_in);
-        cudaFree(d_keys);
-        cudaFree(d_keys_sorted);
-        cudaFree(d_vals);
-        cudaFree(d_counts);
-        cudaFree(d_tmp);
-        cudaFree(d_verr);
         if (e != cudaSuccess) {
             cudaFree(d_orig);
             cudaFree(d_L);
@@ -1046,7 +1064,8 @@ eri_status_t eri_compute_compressed_to_host(eri_plan_t plan, int32_t bits, void 
             if (!plan->class_ev[c] &&
                 (e = cudaEventCreateWithFlags(&plan->class_ev[c], cudaEventDisableTiming)) != cudaSuccess)
                 return cuda_status(e);
-            // the class's codes and scales leave while the next classes compute
+            // the class's codes and scales leave while the next classes compute (one copy stream:
+            // more in flight measured no faster, the host link being the bound)
             e = cudaEventRecord(plan->class_ev[c], s);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(plan->copy_stream, plan->class_ev[c], 0);
             if (e == cudaSuccess)

@@ -604,7 +604,7 @@ def run_e2e(args, api, pool, quartets, counts, total_eris, dev, stream, choice):
 
 
 # ---------------------------------------------------------------------------------------------
-# Further workloads (not the headline): --workload lattice | molecule | gradient
+# Further workloads (not the headline): --workload lattice | molecule | gradient | gshell | paper512
 
 
 def _events(torch, stream, fn, reps=2):
@@ -937,6 +937,43 @@ def run_gradient(args):
     print(json.dumps(out), flush=True)
 
 
+def run_paper512(args):
+    """The paper's 512-bit output chunks (Sec. III-C) as a re-layout pass: eri_pack_paper512_stream
+    on seeded random dense streams of three class shapes, each larger than L2.  CUDA events over
+    10 launches after 3 warm-ups; HBM bytes = dense stream read + chunk words written."""
+    import torch
+
+    from paper_2303_13632_gb300 import api
+
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream()
+    peaks, src = read_peaks()
+    hbm = float(peaks["hbm_gbs"])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(512)
+    rows = {}
+    for name, n_eri, bits, nq in (("[ss|ss]", 1, 16, 16000000), ("[dd|dd]", 1296, 16, 400000),
+                                  ("[ff|ff]", 10000, 12, 40000)):
+        F = 512 // bits
+        n_cs = -(-n_eri // F)
+        dense_words = (nq * n_eri * bits + 31) // 32
+        d_in = torch.randint(-2 ** 31, 2 ** 31 - 1, (dense_words,), dtype=torch.int32, device=dev, generator=gen)
+        d_out = torch.empty(nq * n_cs * 16, dtype=torch.int32, device=dev)
+        fn = lambda: api.eri_pack_paper512_stream(d_in, nq, n_eri, bits, d_out, stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        ms = _events(torch, stream, fn, reps=10)
+        moved = dense_words * 4 + d_out.numel() * 4
+        rows[name] = {"bits": bits, "quartets": nq, "chunks_per_quartet": n_cs, "bytes": moved,
+                      "ms": ms, "gbs": moved / (ms * 1e-3) / 1e9, "frac_hbm": moved / (ms * 1e-3) / 1e9 / hbm}
+        del d_in, d_out
+    out = {"impl": "ours", "workload": "paper512", "metric": "HBM rate of the 512-bit chunk re-layout",
+           "unit": "GB/s", "value": min(r["gbs"] for r in rows.values()), "peak_hbm_gbs": hbm,
+           "peak_source": src, "streams": rows}
+    print(json.dumps(out), flush=True)
+
+
 def fmt_class(cls):
     s = "spdfg"
     return f"[{s[cls[0]]}{s[cls[1]]}|{s[cls[2]]}{s[cls[3]]}]"
@@ -948,7 +985,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="sweep", choices=["sweep", "lattice", "molecule", "gradient", "gshell"],
+    ap.add_argument("--workload", default="sweep", choices=["sweep", "lattice", "molecule", "gradient", "gshell", "paper512"],
                     help="sweep (default): the 256-class benchmark; the others are further studies")
     ap.add_argument("--scale", type=float, default=1.0)
     ap.add_argument("--ref-eris", type=int, default=1500000)
@@ -971,6 +1008,8 @@ def main():
         run_gradient(args)
     elif args.workload == "gshell":
         run_gshell(args)
+    elif args.workload == "paper512":
+        run_paper512(args)
     else:
         run_ours(args)
 

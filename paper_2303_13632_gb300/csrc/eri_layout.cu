@@ -5,9 +5,11 @@
 // holds chunk bits [j*n, j*n + n), chunk bit s being bit s%32 of the chunk's 32-bit word s/32.
 //
 // The compressing kernels write the dense stream (every field right after the previous one);
-// this file re-lays a class's dense stream into chunks.  It is integer-only, HBM-bound work:
-// one thread per output word gathers the (at most 32/n + 2) fields that overlap it from one
-// or two dense words each, so reads and writes are both coalesced along the chunk.
+// this file re-lays a class's dense stream into chunks.  It is integer-only, HBM-bound work.
+// Because a quartet's fields are contiguous in the dense stream, chunk c of quartet i is the
+// nf * n stream bits that start at bit (i * n_eri + c * F) * n, followed by zeros: every output
+// word is a funnel shift of two neighbouring dense words, masked where the chunk's fields end,
+// so no thread looks at individual fields.  Reads and writes are both coalesced along the chunk.
 #include <cstdint>
 
 #include <cuda_runtime.h>
@@ -19,81 +21,57 @@ namespace {
 
 constexpr int kChunkWords = 16;  // 512 bits
 
-// Quartets [q0, q0 + nq) of one class.  `src` is the class's dense stream (word 0 holds stream
-// bit 0), `dst` the chunk words of quartet q0.  nq * n_cs * 16 < 2^31 (host-checked), and every
-// in-quartet bit offset fits 32 bits (n_eri * bits <= 50625 * 24, [gg|gg] at 24 bits).
+// Output word `lo / 32` of a chunk whose first field starts at bit `s` of qs[w] (the word of
+// the chunk bit lo) and whose fields fill `valid` bits.  A dense word is read only where it holds
+// one of the chunk's bits, so nothing past the class's last code is read.
+__device__ __forceinline__ uint32_t chunk_word(const uint32_t *__restrict__ qs, unsigned w, unsigned s,
+                                               unsigned lo, unsigned valid) {
+    if (lo >= valid) return 0u;
+    const unsigned need = valid - lo;  // chunk bits left from lo on
+    uint32_t v = qs[w] >> s;
+    if (s + min(need, 32u) > 32u) v |= qs[w + 1] << (32u - s);  // s > 0 here
+    if (need < 32u) v &= (1u << need) - 1u;
+    return v;
+}
+
+// Quartets [q0, q0 + nq) of one class, one thread per output word.  `src` is the class's dense
+// stream (word 0 holds stream bit 0), `dst` the chunk words of quartet q0.  nq * n_cs * 16 < 2^31
+// (host-checked), and every in-quartet bit offset fits 32 bits (n_eri * bits <= 50625 * 24).
 __global__ void __launch_bounds__(256) paper512_kernel(const uint32_t *__restrict__ src,
                                                        unsigned long long q0, unsigned nq,
                                                        unsigned n_eri, unsigned n_cs, unsigned bits,
                                                        uint32_t *__restrict__ dst) {
     const unsigned F = 512u / bits;
     const unsigned total = nq * n_cs * kChunkWords;
-    const uint32_t mask = (1u << bits) - 1u;  // bits <= 24
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
         const unsigned ch = t / kChunkWords, k = t % kChunkWords;
         const unsigned i = ch / n_cs, c = ch - i * n_cs;
-        // first stream bit of this quartet's codes
         const unsigned long long qbit = (q0 + i) * (unsigned long long)n_eri * bits;
         const uint32_t *qs = src + (qbit >> 5);
-        const unsigned off = (unsigned)qbit & 31u;
-        const unsigned lo = 32u * k;          // chunk bits [lo, lo + 32) make this word
-        const unsigned nf = min(F, n_eri - c * F);  // fields in this chunk (>= 1 since c < n_cs)
-        const unsigned j0 = lo / bits;
-        const unsigned j1 = min((lo + 31u) / bits, nf - 1u);
-        uint32_t out = 0;
-        for (unsigned j = j0; j <= j1; ++j) {
-            const unsigned b = off + (c * F + j) * bits;  // field's bit within the quartet's words
-            const unsigned w = b >> 5, s = b & 31u;
-            uint32_t v = qs[w] >> s;
-            if (s + bits > 32u) v |= qs[w + 1] << (32u - s);  // the field spills into the next word
-            v &= mask;
-            const int o = (int)(j * bits) - (int)lo;
-            out |= o >= 0 ? v << o : v >> (-o);
-        }
-        dst[t] = out;
+        const unsigned valid = min(F, n_eri - c * F) * bits;  // >= bits since c < n_cs
+        const unsigned b = ((unsigned)qbit & 31u) + c * F * bits + 32u * k;
+        dst[t] = chunk_word(qs, b >> 5, b & 31u, 32u * k, valid);
     }
 }
 
-// The same with one thread per quarter chunk (four consecutive output words, one 16-byte store):
-// the quartet and chunk indices are found once per four words, and the field indices lo / bits
-// and (lo + 31) / bits by a multiply with ceil(2^16 / bits) (exact for lo < 2^9 and bits <= 24:
-// the product overshoots lo / bits by less than lo / 2^16 < 1 / bits).  dst 16-byte aligned.
+// The same with one thread per quarter chunk: four consecutive output words share one shift
+// and are written with one 16-byte store.  dst 16-byte aligned.
 __global__ void __launch_bounds__(256) paper512_kernel4(const uint32_t *__restrict__ src,
                                                         unsigned long long q0, unsigned nq,
                                                         unsigned n_eri, unsigned n_cs, unsigned bits,
                                                         uint4 *__restrict__ dst) {
     const unsigned F = 512u / bits;
-    const unsigned inv = (65536u + bits - 1u) / bits;
     const unsigned total = nq * n_cs * (kChunkWords / 4);
-    const uint32_t mask = (1u << bits) - 1u;
     for (unsigned t = blockIdx.x * blockDim.x + threadIdx.x; t < total; t += gridDim.x * blockDim.x) {
-        const unsigned ch = t >> 2, k0 = (t & 3u) * 4u;
+        const unsigned ch = t >> 2, lo = (t & 3u) * 128u;
         const unsigned i = ch / n_cs, c = ch - i * n_cs;
         const unsigned long long qbit = (q0 + i) * (unsigned long long)n_eri * bits;
         const uint32_t *qs = src + (qbit >> 5);
-        const unsigned off = (unsigned)qbit & 31u;
-        const unsigned nf = min(F, n_eri - c * F);
-        uint32_t out[4];
-#pragma unroll
-        for (int kk = 0; kk < 4; ++kk) {
-            const unsigned lo = 32u * (k0 + kk);
-            const unsigned j0 = (lo * inv) >> 16;
-            uint32_t o = 0;
-            if (j0 < nf) {
-                const unsigned j1 = min(((lo + 31u) * inv) >> 16, nf - 1u);
-                for (unsigned j = j0; j <= j1; ++j) {
-                    const unsigned b = off + (c * F + j) * bits;
-                    const unsigned w = b >> 5, s = b & 31u;
-                    uint32_t v = qs[w] >> s;
-                    if (s + bits > 32u) v |= qs[w + 1] << (32u - s);
-                    v &= mask;
-                    const int d = (int)(j * bits) - (int)lo;
-                    o |= d >= 0 ? v << d : v >> (-d);
-                }
-            }
-            out[kk] = o;
-        }
-        dst[t] = make_uint4(out[0], out[1], out[2], out[3]);
+        const unsigned valid = min(F, n_eri - c * F) * bits;
+        const unsigned b = ((unsigned)qbit & 31u) + c * F * bits + lo;
+        const unsigned w = b >> 5, s = b & 31u;
+        dst[t] = make_uint4(chunk_word(qs, w, s, lo, valid), chunk_word(qs, w + 1, s, lo + 32u, valid),
+                            chunk_word(qs, w + 2, s, lo + 64u, valid), chunk_word(qs, w + 3, s, lo + 96u, valid));
     }
 }
 

@@ -150,6 +150,23 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
 /* Frees the plan and its device memory.  NULL is ignored. */
 void eri_plan_destroy(eri_plan_t plan);
 
+/* Moves the plan's shells: replaces the centres, exponents and contraction coefficients of every
+ * shell (normalised as in eri_plan_create, Sec. II-A) and rebuilds the primitive-pair table if
+ * the plan has one, keeping everything else -- the quartet list and its class order (including
+ * the result of any screening, which is not redone), per-class precision, autotuned launch
+ * choices and the cached graph of eri_compute_compressed_batched.  This is the per-step call of
+ * a geometry loop (molecular dynamics, optimisation): later compute and eri_backward calls see
+ * the new shells, with no new plan, host sort or allocation.
+ *   shells      n_shells entries (host); n_shells, and every shell's L and nprim, must equal
+ *               the plan's
+ *   stream      ordered after the plan's earlier work on this stream (cudaStream_t, NULL =
+ *               legacy default stream); work of the plan on other streams must have finished
+ * Synchronous on `stream` (returns once the new values are on the device).  On ERI_E_INVALID
+ * (NULL plan or shells, a changed count, L or nprim, a non-finite centre or coefficient, an
+ * exponent <= 0) the plan is unchanged; ERI_E_CUDA from the copies or the table kernel. */
+eri_status_t eri_plan_update_shells(eri_plan_t plan, const eri_shell_t *shells, int32_t n_shells,
+                                    void *stream);
+
 /* Changes the precision used by later compute calls (ERI_FP64 or ERI_MIXED).  Host only;
  * ERI_E_INVALID for a NULL plan or another value. */
 eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision);

@@ -63,6 +63,7 @@ SIGNATURES = {
     "eri_plan_create": (_i32, [ctypes.POINTER(eri_shell_t), _i32, _p, _i64,
                                ctypes.POINTER(eri_plan_opts_t), ctypes.POINTER(_p)]),
     "eri_plan_destroy": (None, [_p]),
+    "eri_plan_update_shells": (_i32, [_p, ctypes.POINTER(eri_shell_t), _i32, _p]),
     "eri_plan_set_precision": (_i32, [_p, _i32]),
     "eri_plan_set_class_precision": (_i32, [_p, _i32, _i32]),
     "eri_plan_calibrate_precision": (_i32, [_p, _i32, _i64, ctypes.c_float, _p]),

@@ -54,13 +54,9 @@ class Plan:
 MODES = {"explicit": ERI_EXPLICIT, "all": ERI_ALL, "unique8": ERI_UNIQUE8}
 
 
-def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = "explicit",
-                    device: int = 0, pair_table: bool = True, schwarz_threshold: float = 0.0,
-                    shard: tuple[int, int] = (0, 0)) -> Plan:
-    """shells: a ShellSet (workloads.py); quartets: [n, 4] int32 numpy array (host), a
-    contiguous int32 CUDA tensor (device), or None with mode="all" / "unique8"; pair_table=False
-    sets ERI_NO_PAIR_TABLE; shard = (shard_index, shard_count) of a unique8 enumeration."""
-    lib = _lib.load()
+def _shell_array(shells):
+    """eri_shell_t array of a ShellSet, and the numpy arrays its pointers refer to (keep them
+    alive for the call)."""
     n = len(shells.L)
     arr = (_lib.eri_shell_t * max(n, 1))()
     exps = np.ascontiguousarray(shells.exps, dtype=np.float64)
@@ -76,6 +72,18 @@ def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = 
         off = int(shells.pofs[s]) * 8
         sh.exps = ctypes.cast(base_e + off, _lib.c_double_p)
         sh.coefs = ctypes.cast(base_c + off, _lib.c_double_p)
+    return arr, (exps, coefs)
+
+
+def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = "explicit",
+                    device: int = 0, pair_table: bool = True, schwarz_threshold: float = 0.0,
+                    shard: tuple[int, int] = (0, 0)) -> Plan:
+    """shells: a ShellSet (workloads.py); quartets: [n, 4] int32 numpy array (host), a
+    contiguous int32 CUDA tensor (device), or None with mode="all" / "unique8"; pair_table=False
+    sets ERI_NO_PAIR_TABLE; shard = (shard_index, shard_count) of a unique8 enumeration."""
+    lib = _lib.load()
+    n = len(shells.L)
+    arr, _keep = _shell_array(shells)
     opts = _lib.eri_plan_opts_t(PRECISIONS[precision], MODES[mode], device,
                                 0 if pair_table else _lib.ERI_NO_PAIR_TABLE, float(schwarz_threshold),
                                 int(shard[0]), int(shard[1]))
@@ -99,6 +107,14 @@ def eri_plan_create(shells, quartets=None, precision: str = "fp64", mode: str = 
 
 def eri_plan_destroy(plan: Plan) -> None:
     plan.destroy()
+
+
+def eri_plan_update_shells(plan: Plan, shells, stream=None) -> None:
+    """New centres, exponents and coefficients for the plan's shells (same count, L and nprim
+    per shell); the quartet list and everything else of the plan stay."""
+    arr, _keep = _shell_array(shells)
+    check(_lib.load().eri_plan_update_shells(plan.handle, arr, len(shells.L), _stream_handle(stream)),
+          "eri_plan_update_shells")
 
 
 def eri_plan_set_precision(plan: Plan, precision: str) -> None:

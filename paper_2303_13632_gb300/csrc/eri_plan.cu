@@ -219,6 +219,8 @@ struct eri_plan_s {
     void *d_queue = nullptr;     // class table and tile counter of the work-queue launch (lazy)
     void *d_setup = nullptr;      // scratch of the split setup/recurrence path (lazy)
     double *d_pairs = nullptr;    // primitive-pair table (n_prims^2 records), or null
+    int *d_prim_shell = nullptr;  // shell of every primitive (with the pair table)
+    std::vector<int> h_L, h_nprim;  // per shell, for eri_plan_update_shells
     // batched form: tile counters of the persistent kernels (scratch), streams, graph cache
     unsigned long long *d_counters = nullptr;
     static constexpr int kSide = 4;
@@ -265,6 +267,7 @@ void free_plan(eri_plan_s *p) {
     cudaFree(p->d_queue);
     cudaFree(p->d_setup);
     cudaFree(p->d_pairs);
+    cudaFree(p->d_prim_shell);
     cudaFree(p->d_counters);
     if (p->graph) cudaGraphExecDestroy(p->graph);
     for (int i = 0; i < eri_plan_s::kSide; ++i) {
@@ -744,6 +747,8 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
     p->nq = nq;
     p->max_nprim = max_nprim;
     p->n_bf = n_bf;
+    p->h_L = Ls;
+    p->h_nprim = np;
     for (int c = 0; c < kNumClassIds; ++c) {
         p->class_prec[c] = -1;
         p->class_err[c] = -1.0f;
@@ -860,7 +865,7 @@ eri_status_t eri_plan_create(const eri_shell_t *shells, int32_t n_shells, const 
                 pe = cudaGetLastError();
                 if (pe == cudaSuccess) pe = cudaDeviceSynchronize();
             }
-            cudaFree(d_ps);
+            p->d_prim_shell = d_ps;  // kept: eri_plan_update_shells rebuilds the table
             if (pe != cudaSuccess) {
                 free_plan(p);
                 return cuda_status(pe);
@@ -883,6 +888,51 @@ void eri_plan_destroy(eri_plan_t plan) {
     if (!plan) return;
     cudaSetDevice(plan->device);
     free_plan(plan);
+}
+
+eri_status_t eri_plan_update_shells(eri_plan_t plan, const eri_shell_t *shells, int32_t n_shells,
+                                    void *stream) {
+    if (!plan || !shells || n_shells != plan->n_shells) return ERI_E_INVALID;
+    std::vector<double> cx(n_shells), cy(n_shells), cz(n_shells), ex, cn;
+    ex.reserve((size_t)plan->n_prims);
+    cn.reserve((size_t)plan->n_prims);
+    for (int s = 0; s < n_shells; ++s) {
+        const eri_shell_t &sh = shells[s];
+        if (sh.L != plan->h_L[s] || sh.nprim != plan->h_nprim[s] || !sh.exps || !sh.coefs)
+            return ERI_E_INVALID;
+        for (int x = 0; x < 3; ++x)
+            if (!std::isfinite(sh.center[x])) return ERI_E_INVALID;
+        cx[s] = sh.center[0];
+        cy[s] = sh.center[1];
+        cz[s] = sh.center[2];
+        for (int k = 0; k < sh.nprim; ++k) {
+            const double a = sh.exps[k], c = sh.coefs[k];
+            if (!(a > 0.0) || !std::isfinite(a) || !std::isfinite(c)) return ERI_E_INVALID;
+            ex.push_back(a);
+            cn.push_back(c * shell_norm(a, sh.L));
+        }
+    }
+    cudaError_t e = cudaSetDevice(plan->device);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (n_shells == 0) return ERI_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // stream-ordered after the plan's earlier work on `stream`; the host vectors live until the
+    // stream has consumed them (synchronised below)
+    const size_t sb = n_shells * sizeof(double), pb = ex.size() * sizeof(double);
+    e = cudaMemcpyAsync(plan->d_cx, cx.data(), sb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan->d_cy, cy.data(), sb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan->d_cz, cz.data(), sb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan->d_exps, ex.data(), pb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(plan->d_cn, cn.data(), pb, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && plan->d_pairs) {
+        pair_table_kernel<<<4 * 1024, 256, 0, st>>>(plan->d_cx, plan->d_cy, plan->d_cz, plan->d_exps,
+                                                      plan->d_cn, plan->d_prim_shell, plan->n_prims,
+                                                      plan->d_pairs);
+        e = cudaGetLastError();
+    }
+    const cudaError_t se = cudaStreamSynchronize(st);
+    if (e == cudaSuccess) e = se;
+    return cuda_status(e);
 }
 
 eri_status_t eri_plan_set_precision(eri_plan_t plan, int32_t precision) {

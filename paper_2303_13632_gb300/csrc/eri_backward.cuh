@@ -69,6 +69,63 @@ __device__ __forceinline__ typename C::R gI(const typename C::R *Iq, int xi, int
     return Iq[i_index<C>(xi, mu, i, k, j, l)];
 }
 
+// Index table of the grouped contraction, one per canonical class (A, B, Cc, D), evaluated at
+// compile time.  For axis x and the x-components w = (i0, i1, i2, i3) of the four centres the
+// outputs sharing them are entries start[w] .. start[w + 1] - 1 of e[x * N ..]; each entry holds
+// the output's canonical index (bits 0-15), the offset of its y-components (bits 16-31) and of
+// its z-components (bits 32-47) inside one (axis, root) block of the extended 2-D integrals
+// (layout [i][k][j][l] of i_index), y and z being the axes after x in cyclic order.
+template <int A, int B, int Cc, int D>
+struct BwdTab {
+    static constexpr int W1 = A + 1, W2 = B + 1, W3 = Cc + 1, W4 = D + 1, WN = W1 * W2 * W3 * W4;
+    static constexpr int NB = ncart(B), NC = ncart(Cc), ND = ncart(D), N = ncart(A) * NB * NC * ND;
+    // extended index ranges (L + 2) of the 2-D integrals, as in GCfg
+    static constexpr int LC1 = Cc + 3, LD1 = D + 3, JL = (B + 3) * (D + 3), JLP = JL % 2 ? JL : JL + 1;
+    unsigned short start[WN + 1];
+    unsigned long long e[3 * N];
+};
+
+// Cartesian index of the component with c0 along axis 0 and c1 along axis 1 (first component
+// descending, then the second: the output order of the forward kernels)
+constexpr int cart_index(int L, int c0, int c1) { return (L - c0) * (L - c0 + 1) / 2 + (L - c0 - c1); }
+
+template <int A, int B, int Cc, int D>
+constexpr BwdTab<A, B, Cc, D> make_bwd_tab() {
+    using T = BwdTab<A, B, Cc, D>;
+    T t{};
+    constexpr int LC1 = T::LC1, LD1 = T::LD1, JLP = T::JLP;
+    int n = 0;
+    for (int w = 0; w < T::WN; ++w) {
+        const int i3 = w % T::W4, i2 = (w / T::W4) % T::W3, i1 = (w / (T::W4 * T::W3)) % T::W2,
+                  i0 = w / (T::W4 * T::W3 * T::W2);
+        t.start[w] = (unsigned short)n;
+        for (int ay = 0; ay <= A - i0; ++ay)
+            for (int by = 0; by <= B - i1; ++by)
+                for (int cy = 0; cy <= Cc - i2; ++cy)
+                    for (int dy = 0; dy <= D - i3; ++dy) {
+                        const int az = A - i0 - ay, bz = B - i1 - by, cz = Cc - i2 - cy, dz = D - i3 - dy;
+                        const unsigned long long yo = (unsigned long long)((ay * LC1 + cy) * JLP + by * LD1 + dy);
+                        const unsigned long long zo = (unsigned long long)((az * LC1 + cz) * JLP + bz * LD1 + dz);
+                        for (int x = 0; x < 3; ++x) {
+                            const int y = x == 2 ? 0 : x + 1;
+                            const int a0 = x == 0 ? i0 : (y == 0 ? ay : az), a1 = x == 1 ? i0 : (y == 1 ? ay : az);
+                            const int b0 = x == 0 ? i1 : (y == 0 ? by : bz), b1 = x == 1 ? i1 : (y == 1 ? by : bz);
+                            const int c0 = x == 0 ? i2 : (y == 0 ? cy : cz), c1 = x == 1 ? i2 : (y == 1 ? cy : cz);
+                            const int d0 = x == 0 ? i3 : (y == 0 ? dy : dz), d1 = x == 1 ? i3 : (y == 1 ? dy : dz);
+                            const int g = ((cart_index(A, a0, a1) * T::NB + cart_index(B, b0, b1)) * T::NC +
+                                           cart_index(Cc, c0, c1)) * T::ND + cart_index(D, d0, d1);
+                            t.e[x * T::N + n] = (unsigned long long)g | (yo << 16) | (zo << 32);
+                        }
+                        ++n;
+                    }
+    }
+    t.start[T::WN] = (unsigned short)n;
+    return t;
+}
+
+template <int A, int B, int Cc, int D>
+__device__ const BwdTab<A, B, Cc, D> kBwdTab = make_bwd_tab<A, B, Cc, D>();
+
 template <class C>
 __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables &tb,
                                               const ClassArgs &args, const double *__restrict__ G,
@@ -85,6 +142,7 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
     R *I_s = reinterpret_cast<R *>(smem + C::OFF_I);
     __shared__ int maxprim_s;
     __shared__ int4 qt_s[C::Q];
+    __shared__ R ea_s[C::Q * 4];  // 2 alpha of the quartet's four primitives, in R
 
     const int tid = threadIdx.x;
     const long long q0 = (long long)blockIdx.x * C::Q;
@@ -96,13 +154,20 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
         qt_s[q] = make_int4(pick(g, args.perm[0]), pick(g, args.perm[1]), pick(g, args.perm[2]),
                             pick(g, args.perm[3]));
     }
-    // the tile's G (contiguous in the class's generic layout), read once for all primitives
-    // (rounded to FP32 once for the mixed adjoint)
+    // the tile's G (contiguous per quartet in the class's generic layout), read once for all
+    // primitives into the canonical component order (rounded to FP32 once for the mixed adjoint)
     R *G_s = reinterpret_cast<R *>(smem + C::OFF_G);
-    for (int e = tid; e < qn * C::oNERI; e += C::THREADS) G_s[e] = to_r<R>(G[q0 * C::oNERI + e]);
+    {
+        const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
+                  st3 = args.ostride[3];
+        for (int t = tid; t < qn * C::oNERI; t += C::THREADS) {
+            const int q = t / C::oNERI, e = t - q * C::oNERI;
+            const int id = e % C::oND, ic = (e / C::oND) % C::oNC, ib = (e / (C::oND * C::oNC)) % C::oNB,
+                      ia = e / (C::oND * C::oNC * C::oNB);
+            G_s[t] = to_r<R>(G[(q0 + q) * C::oNERI + ia * st0 + ib * st1 + ic * st2 + id * st3]);
+        }
+    }
     __syncthreads();
-    const int st0 = args.ostride[0], st1 = args.ostride[1], st2 = args.ostride[2],
-              st3 = args.ostride[3];
 
     for (int prim = 0; prim < maxprim_s; ++prim) {
         for (int i = tid; i < C::Q * C::NACC; i += C::THREADS) acc_s[i] = 0.0;
@@ -123,6 +188,7 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
                     for (int k = 0; k < 4; ++k) {
                         prim_s[q * 8 + k] = sh.exps[pk[k]];
                         prim_s[q * 8 + 4 + k] = (double)pk[k];
+                        ea_s[q * 4 + k] = to_r<R>(2.0 * sh.exps[pk[k]]);
                     }
                 }
             } else {
@@ -146,6 +212,7 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
                 for (int k = 0; k < 4; ++k) {
                     prim_s[q * 8 + k] = 1.0;
                     prim_s[q * 8 + 4 + k] = -1.0;
+                    ea_s[q * 4 + k] = (R)2;
                 }
             }
         }
@@ -184,49 +251,35 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
             constexpr int W1 = C::oLa + 1, W2 = C::oLb + 1, W3 = C::oLc + 1, W4 = C::oLd + 1;
             constexpr int WN = W1 * W2 * W3 * W4;
             constexpr int ITEMS = C::NRYS * 3 * WN;
+            const auto &tab = kBwdTab<C::oLa, C::oLb, C::oLc, C::oLd>;
+            using Tab = BwdTab<C::oLa, C::oLb, C::oLc, C::oLd>;
+            static_assert(Tab::WN == WN && Tab::N == C::oNERI && Tab::LC1 == C::Lc + 1 && Tab::LD1 == C::Ld + 1 &&
+                              Tab::JLP == C::JLP,
+                          "index table and 2-D integral layout disagree");
             const int lane = tid & 31;
             for (int q = 0; q < qn; ++q) {
-                const double *ex = prim_s + q * 8;
                 const R *Iq = I_s + (size_t)q * (C::I_BYTES / C::RB);
                 const R *Gq = G_s + q * C::oNERI;
                 R ea[4];
 #pragma unroll
-                for (int k = 0; k < 4; ++k) ea[k] = to_r<R>(2.0 * ex[k]);
-                // the thread's sums (in R; FP64 from the warp reduction on)
+                for (int k = 0; k < 4; ++k) ea[k] = ea_s[q * 4 + k];
+                // the thread's sums (in R)
                 R r[C::NACC];
 #pragma unroll
                 for (int k = 0; k < C::NACC; ++k) r[k] = (R)0;
                 for (int it = tid; it < ITEMS; it += C::THREADS) {
                     const int mu = it / (3 * WN), rem = it % (3 * WN);
-                    const int x = rem / WN;
-                    int w = rem % WN;
-                    const int i3 = w % W4;
-                    w /= W4;
-                    const int i2 = w % W3;
-                    w /= W3;
-                    const int i1 = w % W2, i0 = w / W2;
+                    const int x = rem / WN, w = rem % WN;
+                    const int i3 = w % W4, i2 = (w / W4) % W3, i1 = (w / (W4 * W3)) % W2,
+                              i0 = w / (W4 * W3 * W2);
                     const int y = x == 2 ? 0 : x + 1, z = x == 0 ? 2 : x - 1;
+                    const R *Iy = Iq + i_index<C>(y, mu, 0, 0, 0, 0), *Iz = Iq + i_index<C>(z, mu, 0, 0, 0, 0);
+                    const unsigned long long *ent = tab.e + x * C::oNERI;
                     R W = (R)0;
-                    for (int ay = 0; ay <= C::oLa - i0; ++ay)
-                        for (int by = 0; by <= C::oLb - i1; ++by)
-                            for (int cy = 0; cy <= C::oLc - i2; ++cy)
-                                for (int dy = 0; dy <= C::oLd - i3; ++dy) {
-                                    const int az = C::oLa - i0 - ay, bz = C::oLb - i1 - by,
-                                              cz = C::oLc - i2 - cy, dz = C::oLd - i3 - dy;
-                                    // Cartesian index (first component descending, then the
-                                    // second) of each centre from its components along axes 0, 1
-                                    const int a0 = x == 0 ? i0 : (y == 0 ? ay : az), a1 = x == 1 ? i0 : (y == 1 ? ay : az);
-                                    const int b0 = x == 0 ? i1 : (y == 0 ? by : bz), b1 = x == 1 ? i1 : (y == 1 ? by : bz);
-                                    const int c0 = x == 0 ? i2 : (y == 0 ? cy : cz), c1 = x == 1 ? i2 : (y == 1 ? cy : cz);
-                                    const int d0 = x == 0 ? i3 : (y == 0 ? dy : dz), d1 = x == 1 ? i3 : (y == 1 ? dy : dz);
-                                    const int ia = (C::oLa - a0) * (C::oLa - a0 + 1) / 2 + (C::oLa - a0 - a1);
-                                    const int ib = (C::oLb - b0) * (C::oLb - b0 + 1) / 2 + (C::oLb - b0 - b1);
-                                    const int ic = (C::oLc - c0) * (C::oLc - c0 + 1) / 2 + (C::oLc - c0 - c1);
-                                    const int id = (C::oLd - d0) * (C::oLd - d0 + 1) / 2 + (C::oLd - d0 - d1);
-                                    const R g = Gq[ia * st0 + ib * st1 + ic * st2 + id * st3];
-                                    W = fma(g * gI<C>(Iq, y, mu, ay, by, cy, dy),
-                                            gI<C>(Iq, z, mu, az, bz, cz, dz), W);
-                                }
+                    for (int k = tab.start[w], k1 = tab.start[w + 1]; k < k1; ++k) {
+                        const unsigned long long v = ent[k];
+                        W = fma(Gq[(int)(v & 0xffffu)] * Iy[(int)((v >> 16) & 0xffffu)], Iz[(int)(v >> 32)], W);
+                    }
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
                         const int nk = k == 0 ? i0 : (k == 1 ? i1 : (k == 2 ? i2 : i3));
@@ -243,12 +296,14 @@ __device__ __forceinline__ void backward_tile(const ShellsDev &sh, const Tables 
                     }
                     if (x == 0) r[16] += W * gI<C>(Iq, 0, mu, i0, i1, i2, i3);
                 }
+                // warp sums in R (FP32 in the mixed adjoint: the FP64 pipe is the scarce one there),
+                // then FP64 across warps, primitives and quartets
 #pragma unroll
                 for (int k = 0; k < C::NACC; ++k) {
-                    double v = RTraits<R>::to_f64(r[k]);
+                    R v = r[k];
 #pragma unroll
                     for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-                    if (lane == 0 && v != 0.0) atomicAdd(acc_s + q * C::NACC + k, v);
+                    if (lane == 0 && v != (R)0) atomicAdd(acc_s + q * C::NACC + k, RTraits<R>::to_f64(v));
                 }
             }
         }

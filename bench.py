@@ -909,9 +909,30 @@ def run_gradient(args):
                         "backward_geris": n_eri / (ms_b * 1e-3) / 1e9, "forward_geris": n_eri / (ms_f * 1e-3) / 1e9,
                         "backward_over_forward": ms_b / ms_f}
     api.eri_sync(plan, stream)
+    # roofline of the backward pass: the adjoint's algorithmic FLOPs (perfmodel) of every
+    # primitive quartet at the FP32 and FP64 FMA rates measured here
+    peaks = measure_alu_peaks(api, torch, stream, 0)
+    p32, p64 = peaks["fp32_tflops"], peaks["fp64_tflops"]
+    prim_quartets = nper * 3 ** 4
+    roof = {}
+    for prec in ("mixed", "fp64"):
+        t_roof = flops = 0.0
+        for c in cls_list_:
+            f64, rr = perfmodel.adjoint_flops_per_quartet(c, prec)
+            if prec == "fp64":
+                f64, rr = f64 + rr, 0
+            t_roof += prim_quartets * (f64 / (p64 * 1e12) + rr / (p32 * 1e12))
+            flops += prim_quartets * (f64 * p32 / p64 + rr)
+        t = timing[prec]["ms_backward"] * 1e-3
+        roof[prec] = {"bound": "alu", "achieved": flops / t / 1e12, "peak": p32, "unit": "TFLOP/s",
+                      "frac": t_roof / t, "ms_roofline": t_roof * 1e3}
     out = {"impl": "ours", "workload": "gradient", "metric": "adjoint: ERI derivatives contracted per second",
            "value": timing["mixed"]["backward_geris"], "unit": "G ERI/s (backward, mixed)",
            "precisions": timing, "backward_mixed_over_forward_fp64": timing["mixed"]["ms_backward"] / timing["fp64"]["ms_forward"],
+           "roofline_backward": roof,
+           "roofline_note": "FP32-equivalent TFLOP/s (FP64 work weighted by the measured FP32/FP64 rate ratio) "
+                            "against the measured FP32 FMA rate (eri_fma_probe)",
+           "alu_peaks_tflops": {"fp32": p32, "fp64": p64},
            "quartets": int(len(q)), "eris": int(n_eri), "K": 3}
     if not args.no_check:
         # oracle derivative on a sample: a plan of the sampled quartets alone, same G values

@@ -76,6 +76,37 @@ def flops_per_quartet(cls, precision: str = "fp64"):
     return f64, vrr + hrr + quad + comp + (60 * n - roots64) + (20 * n - bc64)
 
 
+def adjoint_flops_per_quartet(cls, precision: str = "fp64"):
+    """(fp64_flops, rr_flops) of the adjoint (eri_backward) per primitive quartet of class cls,
+    counted like flops_per_quartet:
+      setup       40 + 20 n' + 60 n'   geometry, B and C, roots on the extended class (every L + 2,
+                                       n' = floor((L + 2) / 2) + 1 roots): FP64, except two thirds
+                                       of the roots (40 n') in the recurrence type on the mixed
+                                       path; the adjoint forms B and C in FP64 on both paths
+      recurrences VRR + HRR of the extended class, as in flops_per_quartet              (R)
+      contraction 3 flops (a multiply and an FMA) per root, axis and output: W = sum G I_y I_z
+                  over the outputs sharing their x-components                           (R)
+      derivative  30 per root, axis and tuple of x-components (w): four centres x (2 alpha
+                  I(a+1) - a I(a-1), times W, accumulated: 5; W I(a+2) subtracted: 2), and the
+                  exponent term W I (2)                                                 (R)
+      finish      20 per quartet: the exponent gradients and the centre sums            (FP64)"""
+    La, Lb, Lc, Ld = canonical(cls)
+    n = (La + Lb + Lc + Ld + 2) // 2 + 1
+    neri = ncart(La) * ncart(Lb) * ncart(Lc) * ncart(Ld)
+    wn = (La + 1) * (Lb + 1) * (Lc + 1) * (Ld + 1)
+    ea, eb, ec, ed = La + 2, Lb + 2, Lc + 2, Ld + 2
+    nab, ncd = ea + eb, ec + ed
+    vrr = 5 * 3 * n * ((nab + 1) * (ncd + 1) - 1)
+    hrr_bra = sum((nab - j + 1) * (ncd + 1) for j in range(1, eb + 1))
+    hrr_ket = (ea + 1) * (eb + 1) * sum(ncd - l + 1 for l in range(1, ed + 1))
+    hrr = 2 * 3 * n * (hrr_bra + hrr_ket)
+    contraction = 3 * 3 * n * neri
+    derivative = 30 * 3 * n * wn
+    roots64 = 60 * n if precision == "fp64" else 20 * n
+    f64 = 40 + 20 * n + roots64 + 20
+    return f64, vrr + hrr + contraction + derivative + (60 * n - roots64)
+
+
 def bytes_per_quartet(cls, bits: int) -> int:
     neri = ncart(cls[0]) * ncart(cls[1]) * ncart(cls[2]) * ncart(cls[3])
     out = neri * 8 if bits == 0 else (neri * bits + 7) // 8 + 4

@@ -86,3 +86,19 @@ def test_gpu_model_fits_the_committed_class_table():
     assert q["median_abs_log_err"] < 0.2
     # the fitted rates stay below the nominal peaks
     assert p["R64"] < P.PEAK_FP64_TFLOPS * 1e12 and p["R32"] < P.PEAK_FP32_TFLOPS * 1e12
+
+
+def test_adjoint_count():
+    """The adjoint's count: [ss|ss] by hand (extended class [dd|dd] for the recurrences, two roots),
+    the contraction term growing as n_ERIQ, and the mixed split keeping the total."""
+    f64, rr = P.adjoint_flops_per_quartet((0, 0, 0, 0))
+    n = 2  # floor(2 / 2) + 1 roots for the ranges L + 2 of [ss|ss]
+    vrr = 5 * 3 * n * (5 * 5 - 1)
+    hrr = 2 * 3 * n * (sum(4 - j + 1 for j in range(1, 3)) * 5 + 3 * 3 * sum(4 - l + 1 for l in range(1, 3)))
+    assert f64 == 40 + 20 * n + 60 * n + 20
+    assert rr == vrr + hrr + 9 * n * 1 + 90 * n * 1
+    a, b = P.adjoint_flops_per_quartet((2, 2, 2, 2), "fp64"), P.adjoint_flops_per_quartet((2, 2, 2, 2), "mixed")
+    assert sum(a) == sum(b) and a[0] - b[0] == 40 * 6
+    # the contraction (9 n n_ERIQ) is the largest term of the large classes
+    n = (12 + 2) // 2 + 1
+    assert 9 * n * 10000 > 0.5 * P.adjoint_flops_per_quartet((3, 3, 3, 3))[1]

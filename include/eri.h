@@ -371,10 +371,11 @@ eri_status_t eri_autotune(eri_plan_t plan, int32_t bits, void *d_packed, float *
  * the per-class override): ERI_FP64 in FP64 throughout, for shells with L <= 2 (the extended
  * ranges of f shells exceed the per-CTA shared memory in FP64; such a plan returns
  * ERI_E_UNSUPPORTED before any device work); ERI_MIXED with the 2-D integrals on the extended
- * ranges by the FP32 four-index recursion, G rounded to FP32, the per-thread sums in FP32 and
- * the geometry, roots, B and C (rounded once), the per-primitive accumulation and both outputs
- * in FP64, for every class up to f.  Plans with a g shell return ERI_E_UNSUPPORTED.  Both outputs are zeroed and then accumulated on `stream`
- * (device atomics: summation order, hence the last bits, can vary between runs). */
+ * ranges by the FP32 four-index recursion, G rounded to FP32, the per-thread and per-warp sums
+ * in FP32 and the geometry, roots, B and C (rounded once), the sums across warps, primitives and
+ * quartets and both outputs in FP64, for every class up to f.  Plans with a g shell return
+ * ERI_E_UNSUPPORTED.  Both outputs are zeroed and then accumulated on `stream` (device atomics:
+ * summation order, hence the last bits, can vary between runs). */
 eri_status_t eri_backward(eri_plan_t plan, const double *d_G, double *d_dR, double *d_dalpha,
                           void *stream);
 

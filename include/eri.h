@@ -97,7 +97,7 @@ enum {
 /* One shell (host memory; eri_plan_create copies it). */
 typedef struct {
     double center[3];     /* bohr */
-    int32_t L;            /* 0..3 */
+    int32_t L;            /* 0..4 (s, p, d, f, g) */
     int32_t nprim;        /* >= 1 */
     const double *exps;   /* nprim exponents, each > 0 */
     const double *coefs;  /* nprim contraction coefficients (finite) */

@@ -13,6 +13,7 @@
 // Centre gradients are summed over primitives; exponent gradients go to the primitive.
 #pragma once
 
+#include "eri_bwd_table.h"
 #include "eri_kernels.cuh"
 
 namespace eri {
@@ -69,60 +70,8 @@ __device__ __forceinline__ typename C::R gI(const typename C::R *Iq, int xi, int
     return Iq[i_index<C>(xi, mu, i, k, j, l)];
 }
 
-// Index table of the grouped contraction, one per canonical class (A, B, Cc, D), evaluated at
-// compile time.  For axis x and the x-components w = (i0, i1, i2, i3) of the four centres the
-// outputs sharing them are entries start[w] .. start[w + 1] - 1 of e[x * N ..]; each entry holds
-// the output's canonical index (bits 0-15), the offset of its y-components (bits 16-31) and of
-// its z-components (bits 32-47) inside one (axis, root) block of the extended 2-D integrals
-// (layout [i][k][j][l] of i_index), y and z being the axes after x in cyclic order.
-template <int A, int B, int Cc, int D>
-struct BwdTab {
-    static constexpr int W1 = A + 1, W2 = B + 1, W3 = Cc + 1, W4 = D + 1, WN = W1 * W2 * W3 * W4;
-    static constexpr int NB = ncart(B), NC = ncart(Cc), ND = ncart(D), N = ncart(A) * NB * NC * ND;
-    // extended index ranges (L + 2) of the 2-D integrals, as in GCfg
-    static constexpr int LC1 = Cc + 3, LD1 = D + 3, JL = (B + 3) * (D + 3), JLP = JL % 2 ? JL : JL + 1;
-    unsigned short start[WN + 1];
-    unsigned long long e[3 * N];
-};
-
-// Cartesian index of the component with c0 along axis 0 and c1 along axis 1 (first component
-// descending, then the second: the output order of the forward kernels)
-constexpr int cart_index(int L, int c0, int c1) { return (L - c0) * (L - c0 + 1) / 2 + (L - c0 - c1); }
-
-template <int A, int B, int Cc, int D>
-constexpr BwdTab<A, B, Cc, D> make_bwd_tab() {
-    using T = BwdTab<A, B, Cc, D>;
-    T t{};
-    constexpr int LC1 = T::LC1, LD1 = T::LD1, JLP = T::JLP;
-    int n = 0;
-    for (int w = 0; w < T::WN; ++w) {
-        const int i3 = w % T::W4, i2 = (w / T::W4) % T::W3, i1 = (w / (T::W4 * T::W3)) % T::W2,
-                  i0 = w / (T::W4 * T::W3 * T::W2);
-        t.start[w] = (unsigned short)n;
-        for (int ay = 0; ay <= A - i0; ++ay)
-            for (int by = 0; by <= B - i1; ++by)
-                for (int cy = 0; cy <= Cc - i2; ++cy)
-                    for (int dy = 0; dy <= D - i3; ++dy) {
-                        const int az = A - i0 - ay, bz = B - i1 - by, cz = Cc - i2 - cy, dz = D - i3 - dy;
-                        const unsigned long long yo = (unsigned long long)((ay * LC1 + cy) * JLP + by * LD1 + dy);
-                        const unsigned long long zo = (unsigned long long)((az * LC1 + cz) * JLP + bz * LD1 + dz);
-                        for (int x = 0; x < 3; ++x) {
-                            const int y = x == 2 ? 0 : x + 1;
-                            const int a0 = x == 0 ? i0 : (y == 0 ? ay : az), a1 = x == 1 ? i0 : (y == 1 ? ay : az);
-                            const int b0 = x == 0 ? i1 : (y == 0 ? by : bz), b1 = x == 1 ? i1 : (y == 1 ? by : bz);
-                            const int c0 = x == 0 ? i2 : (y == 0 ? cy : cz), c1 = x == 1 ? i2 : (y == 1 ? cy : cz);
-                            const int d0 = x == 0 ? i3 : (y == 0 ? dy : dz), d1 = x == 1 ? i3 : (y == 1 ? dy : dz);
-                            const int g = ((cart_index(A, a0, a1) * T::NB + cart_index(B, b0, b1)) * T::NC +
-                                           cart_index(Cc, c0, c1)) * T::ND + cart_index(D, d0, d1);
-                            t.e[x * T::N + n] = (unsigned long long)g | (yo << 16) | (zo << 32);
-                        }
-                        ++n;
-                    }
-    }
-    t.start[T::WN] = (unsigned short)n;
-    return t;
-}
-
+// The index table of the grouped contraction (eri_bwd_table.h), as device data, one per canonical
+// class.
 template <int A, int B, int Cc, int D>
 __device__ const BwdTab<A, B, Cc, D> kBwdTab = make_bwd_tab<A, B, Cc, D>();
 
